@@ -1,0 +1,215 @@
+"""ctypes front end of the CPU oracle (oracle/pic_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg use this module; the library under test never imports it.
+
+The oracle is a plain, slow, FP64, -ffp-contract=off restatement of the
+paper's particle steps (Gassmoeller et al., arXiv 1612.03369, Sec. 2.2-2.7).
+Every function here only marshals numpy arrays into the C code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = C.CDLL(_LIB)
+    P = C.c_void_p
+    i64, u64, u32, f64 = C.c_int64, C.c_uint64, C.c_uint32, C.c_double
+    lib.orc_mesh_create.restype = P
+    lib.orc_mesh_create.argtypes = [C.c_int, P, P]
+    lib.orc_mesh_set_velocity.argtypes = [P, P]
+    lib.orc_mesh_destroy.argtypes = [P]
+    lib.orc_phi.argtypes = [P, i64, P, P]
+    lib.orc_newton.restype = C.c_int
+    lib.orc_newton.argtypes = [P, i64, P, P, P, P]
+    lib.orc_inside.restype = C.c_int
+    lib.orc_inside.argtypes = [P, i64, P, P]
+    lib.orc_owner.restype = i64
+    lib.orc_owner.argtypes = [P, P, P]
+    lib.orc_owner_brute.restype = i64
+    lib.orc_owner_brute.argtypes = [P, P, P]
+    lib.orc_q2_eval.argtypes = [P, i64, P, P]
+    lib.orc_splitmix64.restype = u64
+    lib.orc_splitmix64.argtypes = [u64, u64]
+    lib.orc_seed.restype = i64
+    lib.orc_seed.argtypes = [P, P, u32, u64, u64, P, P, P, P]
+    lib.orc_advect.restype = i64
+    lib.orc_advect.argtypes = [P, i64, P, P, P, P, P, C.c_int, f64, C.c_int, C.c_int, P]
+    lib.orc_locate_points.argtypes = [P, i64, P, P, P, C.c_int]
+    lib.orc_cell_average.argtypes = [i64, i64, P, P, f64, P, P]
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Mesh:
+    """Structured mesh of (bi/tri)linear cells with a Q2 nodal velocity."""
+
+    def __init__(self, n, X, U=None):
+        lib = _load()
+        self.dim = len(n)
+        self.n = tuple(int(v) for v in n)
+        nn = np.array(list(self.n) + [1] * (3 - self.dim), dtype=np.int64)
+        self.X = np.ascontiguousarray(X, dtype=np.float64)
+        assert self.X.shape == (self.dim, int(np.prod([v + 1 for v in self.n])))
+        self._h = lib.orc_mesh_create(self.dim, _p(nn), _p(self.X))
+        self.ncells = int(np.prod(self.n))
+        if U is not None:
+            self.set_velocity(U)
+
+    def set_velocity(self, U):
+        self.U = np.ascontiguousarray(U, dtype=np.float64)
+        assert self.U.shape == (self.dim, int(np.prod([2 * v + 1 for v in self.n])))
+        _load().orc_mesh_set_velocity(self._h, _p(self.U))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.orc_mesh_destroy(self._h)
+            self._h = None
+
+    # single-point primitives --------------------------------------------
+    def phi(self, K: int, xhat) -> np.ndarray:
+        t = np.ascontiguousarray(xhat, dtype=np.float64)
+        out = np.zeros(self.dim)
+        _load().orc_phi(self._h, int(K), _p(t), _p(out))
+        return out
+
+    def newton(self, K: int, x, start=None):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        s = np.full(self.dim, 0.5) if start is None else np.ascontiguousarray(start, dtype=np.float64)
+        t = np.zeros(self.dim)
+        it = C.c_int(0)
+        conv = _load().orc_newton(self._h, int(K), _p(x), _p(s), _p(t), C.byref(it))
+        return bool(conv), t, int(it.value)
+
+    def inside(self, K: int, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.zeros(self.dim)
+        r = _load().orc_inside(self._h, int(K), _p(x), _p(t))
+        return bool(r), t
+
+    def owner(self, x, brute: bool = False):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        t = np.zeros(self.dim)
+        f = _load().orc_owner_brute if brute else _load().orc_owner
+        K = f(self._h, _p(x), _p(t))
+        return int(K), t
+
+    def q2(self, K: int, xhat) -> np.ndarray:
+        t = np.ascontiguousarray(xhat, dtype=np.float64)
+        out = np.zeros(self.dim)
+        _load().orc_q2_eval(self._h, int(K), _p(t), _p(out))
+        return out
+
+    # batched ----------------------------------------------------------------
+    def locate(self, x, brute: bool = False):
+        """x [n][dim] -> (cell [n] int64, -1 = outside; xhat [n][dim])."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, self.dim)
+        n = x.shape[0]
+        cell = np.zeros(n, dtype=np.int64)
+        xh = np.zeros((n, self.dim))
+        _load().orc_locate_points(self._h, n, _p(x), _p(cell), _p(xh), int(brute))
+        return cell, xh
+
+
+def splitmix64(seed: int, n: int) -> int:
+    return int(_load().orc_splitmix64(C.c_uint64(seed & (2**64 - 1)), C.c_uint64(n)))
+
+
+class Particles:
+    """Particle-major arrays in (cell, id) order."""
+
+    def __init__(self, x, xhat, cell, id, props):
+        self.x = np.ascontiguousarray(x, dtype=np.float64)
+        self.xhat = np.ascontiguousarray(xhat, dtype=np.float64)
+        self.cell = np.ascontiguousarray(cell, dtype=np.int64)
+        self.id = np.ascontiguousarray(id, dtype=np.uint64)
+        self.props = np.ascontiguousarray(props, dtype=np.float64)
+        self.n_lost = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.cell.shape[0])
+
+    def copy(self) -> "Particles":
+        p = Particles(self.x.copy(), self.xhat.copy(), self.cell.copy(), self.id.copy(), self.props.copy())
+        p.n_lost = self.n_lost
+        return p
+
+    def subset(self, mask) -> "Particles":
+        return Particles(self.x[mask], self.xhat[mask], self.cell[mask], self.id[mask], self.props[mask])
+
+
+def seed_particles(mesh: Mesh, per_cell=None, uniform_count: int = 0, seed: int = 0, first_id: int = 0,
+                   n_props: int = 0) -> Particles:
+    """Local-coordinate generation, ids in creation order (R11)."""
+    if per_cell is not None:
+        pc = np.ascontiguousarray(per_cell, dtype=np.uint32)
+        N = int(pc.sum())
+        pcp = _p(pc)
+    else:
+        pc = None
+        N = mesh.ncells * int(uniform_count)
+        pcp = None
+    d = mesh.dim
+    x = np.zeros((N, d))
+    xh = np.zeros((N, d))
+    cell = np.zeros(N, dtype=np.int64)
+    ids = np.zeros(N, dtype=np.uint64)
+    n = _load().orc_seed(mesh._h, pcp, int(uniform_count), C.c_uint64(seed & (2**64 - 1)), C.c_uint64(first_id),
+                         _p(x), _p(xh), _p(cell), _p(ids))
+    assert n == N
+    return Particles(x, xh, cell, ids, np.zeros((N, n_props)))
+
+
+def advect(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int) -> Particles:
+    """n_steps of (advance all particles with stage locates; drop lost; sort
+    by (cell, id)).  Returns a new Particles."""
+    p = parts.copy()
+    d = mesh.dim
+    nprops = p.props.shape[1] if p.props.ndim == 2 else 0
+    lost = C.c_int64(0)
+    n = _load().orc_advect(mesh._h, p.n, _p(p.x), _p(p.xhat), _p(p.cell), _p(p.id), _p(p.props), nprops,
+                           float(dt), int(integrator), int(n_steps), C.byref(lost))
+    out = Particles(p.x[:n], p.xhat[:n], p.cell[:n], p.id[:n], p.props[:n])
+    out.n_lost = parts.n_lost + int(lost.value)
+    return out
+
+
+def cell_average(ncells: int, cell, value, empty_fill: float = 0.0):
+    """Arithmetic per-cell average, left fold in store order (Sec. 2.7 (ii))."""
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    value = np.ascontiguousarray(value, dtype=np.float64)
+    avg = np.zeros(ncells)
+    cnt = np.zeros(ncells, dtype=np.int64)
+    _load().orc_cell_average(int(ncells), int(cell.shape[0]), _p(cell), _p(value), float(empty_fill), _p(avg),
+                             _p(cnt))
+    return avg, cnt

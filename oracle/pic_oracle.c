@@ -1,0 +1,574 @@
+/*
+ * pic_oracle.c -- plain, slow, obviously-correct CPU oracle for the particle
+ * hot path of Gassmoeller, Heien, Puckett & Bangerth, "Flexible and scalable
+ * particle-in-cell methods for massively parallel computations" (arXiv
+ * 1612.03369).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline leg use it.  It shares no code, header, table or helper with the
+ * CUDA library; the two meet only through the seeded input generators.
+ *
+ * Everything is IEEE binary64, compiled with -ffp-contract=off, with no
+ * blocking, fusion or reordering: each function follows the paper's
+ * statement of the step it computes, and its comment names the section or
+ * equation.  Where the paper is silent or its printed formulas are garbled,
+ * the reading taken is named R1..R13 (the list of readings is kept with the
+ * design notes of the repository).
+ *
+ * Layouts (chosen for the oracle alone):
+ *   vertices X[dim][nverts], vertex (i,j,k) at i + (nx+1)*(j + (ny+1)*k)
+ *   Q2 nodal values U[dim][nnodes], node (I,J,K) at I + (2nx+1)*(J + (2ny+1)*K)
+ *   cell (i,j,k) at i + nx*(j + ny*k)
+ *   particles: array of structs, one struct per particle (Sec. 2.1 listing)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_NEWTON_TOL 1e-14   /* R2: stop when max|delta| <= 1e-14          */
+#define ORC_NEWTON_MAXIT 30    /* R2: or after 30 iterations (= not inside)  */
+#define ORC_INSIDE_EPS 1e-10   /* R3: x-hat in [-eps, 1+eps]^d means inside  */
+
+typedef struct {
+  int dim;
+  int64_t n[3];   /* cells per axis; n[2] = 1 in 2D */
+  int64_t nv[3];  /* vertices per axis */
+  int64_t nq[3];  /* Q2 nodes per axis */
+  int64_t ncells, nverts, nnodes;
+  double *X; /* [dim][nverts] */
+  double *U; /* [dim][nnodes], NULL until set */
+  /* exact bounding-box filter for the owner search: a cell can only contain
+   * x if its (padded) bounding box contains x, so testing only those cells is
+   * the brute-force search of Sec. 2.2 (prescribed positions) with a filter
+   * that cannot drop a true owner. */
+  double *bb_lo, *bb_hi; /* [ncells][3] */
+  double org[3], bs[3];
+  int64_t nb[3];
+  int64_t *bin_start; /* [nbins+1] */
+  int64_t *bin_cells;
+} orc_mesh;
+
+typedef struct {
+  uint64_t id;
+  int64_t cell; /* owner cell, -1 = lost */
+  double x[3];
+  double xhat[3];
+  double *props;
+} orc_particle;
+
+/* ---------------------------------------------------------------- mesh --- */
+
+static int64_t cell_index(const orc_mesh *m, int64_t i, int64_t j, int64_t k) {
+  return i + m->n[0] * (j + m->n[1] * k);
+}
+
+static void cell_ijk(const orc_mesh *m, int64_t c, int64_t *i, int64_t *j, int64_t *k) {
+  *i = c % m->n[0];
+  *j = (c / m->n[0]) % m->n[1];
+  *k = c / (m->n[0] * m->n[1]);
+}
+
+/* Vertex v (v = a + 2b + 4c, lexicographic) of cell K, coordinate comp. */
+static double cell_vertex(const orc_mesh *m, int64_t K, int v, int comp) {
+  int64_t i, j, k;
+  cell_ijk(m, K, &i, &j, &k);
+  int64_t a = v & 1, b = (v >> 1) & 1, c = (v >> 2) & 1;
+  int64_t gv = (i + a) + m->nv[0] * ((j + b) + m->nv[1] * (k + c));
+  return m->X[(int64_t)comp * m->nverts + gv];
+}
+
+static void build_bins(orc_mesh *m);
+
+orc_mesh *orc_mesh_create(int dim, const int64_t *n, const double *X) {
+  orc_mesh *m = (orc_mesh *)calloc(1, sizeof(orc_mesh));
+  m->dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    m->n[a] = a < dim ? n[a] : 1;
+    m->nv[a] = a < dim ? n[a] + 1 : 1;
+    m->nq[a] = a < dim ? 2 * n[a] + 1 : 1;
+  }
+  m->ncells = m->n[0] * m->n[1] * m->n[2];
+  m->nverts = m->nv[0] * m->nv[1] * m->nv[2];
+  m->nnodes = m->nq[0] * m->nq[1] * m->nq[2];
+  m->X = (double *)malloc(sizeof(double) * dim * m->nverts);
+  memcpy(m->X, X, sizeof(double) * dim * m->nverts);
+  build_bins(m);
+  return m;
+}
+
+void orc_mesh_set_velocity(orc_mesh *m, const double *U) {
+  if (!m->U) m->U = (double *)malloc(sizeof(double) * m->dim * m->nnodes);
+  memcpy(m->U, U, sizeof(double) * m->dim * m->nnodes);
+}
+
+void orc_mesh_destroy(orc_mesh *m) {
+  if (!m) return;
+  free(m->X);
+  free(m->U);
+  free(m->bb_lo);
+  free(m->bb_hi);
+  free(m->bin_start);
+  free(m->bin_cells);
+  free(m);
+}
+
+int64_t orc_mesh_ncells(const orc_mesh *m) { return m->ncells; }
+
+static int64_t clampi(int64_t v, int64_t lo, int64_t hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static void build_bins(orc_mesh *m) {
+  int d = m->dim, nvc = 1 << d;
+  m->bb_lo = (double *)malloc(sizeof(double) * 3 * m->ncells);
+  m->bb_hi = (double *)malloc(sizeof(double) * 3 * m->ncells);
+  double glo[3] = {0, 0, 0}, ghi[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    glo[a] = INFINITY;
+    ghi[a] = -INFINITY;
+  }
+  for (int64_t K = 0; K < m->ncells; ++K) {
+    for (int a = 0; a < d; ++a) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int v = 0; v < nvc; ++v) {
+        double xv = cell_vertex(m, K, v, a);
+        if (xv < lo) lo = xv;
+        if (xv > hi) hi = xv;
+      }
+      /* pad by 1e-6 of the cell's extent: far wider than the eps band of R3 */
+      double pad = 1e-6 * (hi - lo);
+      m->bb_lo[3 * K + a] = lo - pad;
+      m->bb_hi[3 * K + a] = hi + pad;
+      if (lo - pad < glo[a]) glo[a] = lo - pad;
+      if (hi + pad > ghi[a]) ghi[a] = hi + pad;
+    }
+  }
+  int64_t nbins = 1;
+  for (int a = 0; a < 3; ++a) {
+    if (a < d) {
+      m->nb[a] = m->n[a];
+      m->org[a] = glo[a];
+      m->bs[a] = (ghi[a] - glo[a]) / (double)m->nb[a];
+    } else {
+      m->nb[a] = 1;
+      m->org[a] = 0;
+      m->bs[a] = 1;
+    }
+    nbins *= m->nb[a];
+  }
+  /* two passes: count, then fill (CSR) */
+  m->bin_start = (int64_t *)calloc(nbins + 1, sizeof(int64_t));
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t *fill = NULL;
+    if (pass == 1) {
+      for (int64_t b = 0; b < nbins; ++b) m->bin_start[b + 1] += m->bin_start[b];
+      m->bin_cells = (int64_t *)malloc(sizeof(int64_t) * (m->bin_start[nbins] + 1));
+      fill = (int64_t *)calloc(nbins, sizeof(int64_t));
+    }
+    for (int64_t K = 0; K < m->ncells; ++K) {
+      int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) {
+        lo[a] = clampi((int64_t)floor((m->bb_lo[3 * K + a] - m->org[a]) / m->bs[a]), 0, m->nb[a] - 1);
+        hi[a] = clampi((int64_t)floor((m->bb_hi[3 * K + a] - m->org[a]) / m->bs[a]), 0, m->nb[a] - 1);
+      }
+      for (int64_t bk = lo[2]; bk <= hi[2]; ++bk)
+        for (int64_t bj = lo[1]; bj <= hi[1]; ++bj)
+          for (int64_t bi = lo[0]; bi <= hi[0]; ++bi) {
+            int64_t b = bi + m->nb[0] * (bj + m->nb[1] * bk);
+            if (pass == 0)
+              m->bin_start[b + 1]++;
+            else
+              m->bin_cells[m->bin_start[b] + fill[b]++] = K;
+          }
+    }
+    free(fill);
+  }
+}
+
+/* ------------------------------------------- mapping Phi_K (Remark 2.1) --- */
+
+/* Multilinear weight of local vertex v at x-hat: prod_j (bit_j ? t_j : 1-t_j) */
+static double vertex_weight(int dim, int v, const double *t) {
+  double w = 1.0;
+  for (int j = 0; j < dim; ++j) w = w * (((v >> j) & 1) ? t[j] : 1.0 - t[j]);
+  return w;
+}
+
+/* d w_v / d t_jd */
+static double vertex_weight_deriv(int dim, int v, const double *t, int jd) {
+  double w = 1.0;
+  for (int j = 0; j < dim; ++j) {
+    if (j == jd)
+      w = w * (((v >> j) & 1) ? 1.0 : -1.0);
+    else
+      w = w * (((v >> j) & 1) ? t[j] : 1.0 - t[j]);
+  }
+  return w;
+}
+
+/* x = Phi_K(x-hat) = sum_v X_{K,v} w_v(x-hat), the (bi/tri)linear map. */
+void orc_phi(const orc_mesh *m, int64_t K, const double *xhat, double *x) {
+  int d = m->dim;
+  for (int i = 0; i < d; ++i) {
+    double s = 0.0;
+    for (int v = 0; v < (1 << d); ++v) s = s + cell_vertex(m, K, v, i) * vertex_weight(d, v, xhat);
+    x[i] = s;
+  }
+}
+
+/* Phi_K(x-hat) - X_{K,0} written with vertex offsets (same map; keeps the
+ * Newton residual free of the cancellation of two O(1) coordinates). */
+static void phi_local(const orc_mesh *m, int64_t K, const double *xhat, double *y) {
+  int d = m->dim;
+  for (int i = 0; i < d; ++i) {
+    double x0 = cell_vertex(m, K, 0, i), s = 0.0;
+    for (int v = 1; v < (1 << d); ++v) s = s + (cell_vertex(m, K, v, i) - x0) * vertex_weight(d, v, xhat);
+    y[i] = s;
+  }
+}
+
+/* J_ij = d Phi_i / d xhat_j */
+static void phi_jacobian(const orc_mesh *m, int64_t K, const double *xhat, double J[3][3]) {
+  int d = m->dim;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int v = 0; v < (1 << d); ++v) s = s + cell_vertex(m, K, v, i) * vertex_weight_deriv(d, v, xhat, j);
+      J[i][j] = s;
+    }
+}
+
+/* Solve J delta = r by Cramer's rule. Returns 0 if J is singular. */
+static int solve_cramer(int d, double J[3][3], const double *r, double *delta) {
+  if (d == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (det == 0.0 || !isfinite(det)) return 0;
+    delta[0] = (r[0] * J[1][1] - J[0][1] * r[1]) / det;
+    delta[1] = (J[0][0] * r[1] - r[0] * J[1][0]) / det;
+    return 1;
+  }
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if (det == 0.0 || !isfinite(det)) return 0;
+  for (int c = 0; c < 3; ++c) {
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) A[i][j] = (j == c) ? r[i] : J[i][j];
+    double dc = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    delta[c] = dc / det;
+  }
+  return 1;
+}
+
+/* x-hat = Phi_K^{-1}(x) by Newton's method (the "iterative inversion" of
+ * Sec. 2.2 and Remark 2.1; reading R2 for start, tolerance and iteration cap).
+ * Returns 1 if converged; *iters receives the iteration count. */
+int orc_newton(const orc_mesh *m, int64_t K, const double *x, const double *start, double *xhat, int *iters) {
+  int d = m->dim;
+  double t[3] = {0, 0, 0}, rhs[3] = {0, 0, 0};
+  for (int j = 0; j < d; ++j) {
+    t[j] = start[j];
+    rhs[j] = x[j] - cell_vertex(m, K, 0, j);
+  }
+  int conv = 0, it = 0;
+  for (it = 1; it <= ORC_NEWTON_MAXIT; ++it) {
+    double y[3], r[3], J[3][3], delta[3];
+    phi_local(m, K, t, y);
+    for (int j = 0; j < d; ++j) r[j] = rhs[j] - y[j];
+    phi_jacobian(m, K, t, J);
+    if (!solve_cramer(d, J, r, delta)) break;
+    double dmax = 0.0;
+    for (int j = 0; j < d; ++j) {
+      t[j] = t[j] + delta[j];
+      if (fabs(delta[j]) > dmax) dmax = fabs(delta[j]);
+    }
+    if (!isfinite(dmax)) break;
+    if (dmax <= ORC_NEWTON_TOL) {
+      conv = 1;
+      break;
+    }
+  }
+  for (int j = 0; j < d; ++j) xhat[j] = t[j];
+  if (iters) *iters = it > ORC_NEWTON_MAXIT ? ORC_NEWTON_MAXIT : it;
+  return conv;
+}
+
+/* inside(K, x): Newton from the cell centre converges and x-hat lies in the
+ * closed reference cell widened by eps (R2, R3; Sec. 2.4 "testing whether
+ * x-hat is in K-hat"). */
+int orc_inside(const orc_mesh *m, int64_t K, const double *x, double *xhat) {
+  double start[3] = {0.5, 0.5, 0.5}, t[3] = {0, 0, 0};
+  int conv = orc_newton(m, K, x, start, t, NULL);
+  if (xhat)
+    for (int j = 0; j < m->dim; ++j) xhat[j] = t[j];
+  if (!conv) return 0;
+  for (int j = 0; j < m->dim; ++j)
+    if (!(t[j] >= -ORC_INSIDE_EPS && t[j] <= 1.0 + ORC_INSIDE_EPS)) return 0;
+  return 1;
+}
+
+/* owner(x) = min { K : inside(K, x) } over ALL cells, no filter at all
+ * (Sec. 2.2, generation at prescribed positions: search all cells; R4 fixes
+ * the lowest index on shared faces).  -1 if no cell contains x (lost). */
+int64_t orc_owner_brute(const orc_mesh *m, const double *x, double *xhat) {
+  for (int64_t K = 0; K < m->ncells; ++K) {
+    double t[3];
+    if (orc_inside(m, K, x, t)) {
+      if (xhat)
+        for (int j = 0; j < m->dim; ++j) xhat[j] = t[j];
+      return K;
+    }
+  }
+  return -1;
+}
+
+/* The same minimum, visiting only cells whose padded bounding box holds x
+ * (a necessary condition for inside, so the minimum is unchanged). */
+int64_t orc_owner(const orc_mesh *m, const double *x, double *xhat) {
+  int d = m->dim;
+  int64_t bi[3] = {0, 0, 0};
+  for (int a = 0; a < d; ++a) {
+    if (!isfinite(x[a])) return -1;
+    double f = floor((x[a] - m->org[a]) / m->bs[a]);
+    if (f < 0 || f >= (double)m->nb[a]) {
+      /* the padded global box can still hold x on its upper face */
+      if (!(x[a] >= m->org[a] && x[a] <= m->org[a] + m->bs[a] * (double)m->nb[a])) return -1;
+    }
+    bi[a] = clampi((int64_t)f, 0, m->nb[a] - 1);
+  }
+  int64_t b = bi[0] + m->nb[0] * (bi[1] + m->nb[1] * bi[2]);
+  int64_t best = -1;
+  double tb[3] = {0, 0, 0};
+  for (int64_t q = m->bin_start[b]; q < m->bin_start[b + 1]; ++q) {
+    int64_t K = m->bin_cells[q];
+    if (best >= 0 && K > best) continue;
+    int inbox = 1;
+    for (int a = 0; a < d; ++a)
+      if (!(x[a] >= m->bb_lo[3 * K + a] && x[a] <= m->bb_hi[3 * K + a])) inbox = 0;
+    if (!inbox) continue;
+    double t[3];
+    if (orc_inside(m, K, x, t)) {
+      best = K;
+      for (int j = 0; j < d; ++j) tb[j] = t[j];
+    }
+  }
+  if (best >= 0 && xhat)
+    for (int j = 0; j < d; ++j) xhat[j] = tb[j];
+  return best;
+}
+
+/* --------------------------------------------- Q2 velocity (Sec. 2.3) --- */
+
+/* 1D quadratic Lagrange basis on nodes 0, 1/2, 1. */
+static double lagrange2(int a, double t) {
+  if (a == 0) return (1.0 - t) * (1.0 - 2.0 * t);
+  if (a == 1) return 4.0 * t * (1.0 - t);
+  return t * (2.0 * t - 1.0);
+}
+
+/* u_h(x) = sum_i U_i phi-hat_i(x-hat) over the 3^d Q2 nodes of cell K: the
+ * finite-element field evaluated at the stored reference coordinates
+ * (Sec. 2.3, "evaluation of the velocity field", and Remark 2.1). */
+void orc_q2_eval(const orc_mesh *m, int64_t K, const double *xhat, double *u) {
+  int d = m->dim;
+  int64_t i, j, k;
+  cell_ijk(m, K, &i, &j, &k);
+  int cmax = d == 3 ? 3 : 1;
+  for (int comp = 0; comp < d; ++comp) {
+    double s = 0.0;
+    for (int c = 0; c < cmax; ++c)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          int64_t node = (2 * i + a) + m->nq[0] * ((2 * j + b) + m->nq[1] * (2 * k + c));
+          double w = lagrange2(a, xhat[0]) * lagrange2(b, xhat[1]);
+          if (d == 3) w = w * lagrange2(c, xhat[2]);
+          s = s + m->U[(int64_t)comp * m->nnodes + node] * w;
+        }
+    u[comp] = s;
+  }
+}
+
+/* ------------------------------------------------ seeding (Sec. 2.2) --- */
+
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output n (n >= 0) of the
+ * generator seeded with `seed` is mix(seed + (n+1) * golden gamma). */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* R11: local-coordinate generation (Remark "local generation"): walk the
+ * cells in order, draw x-hat uniform in [0,1)^d, x = Phi_K(x-hat), ids in
+ * creation order.  per_cell may be NULL (then uniform_count in every cell).
+ * Outputs particle-major: x[N][dim], xhat[N][dim], cell[N], id[N].
+ * Returns N. */
+int64_t orc_seed(const orc_mesh *m, const uint32_t *per_cell, uint32_t uniform_count, uint64_t seed,
+                 uint64_t first_id, double *x, double *xhat, int64_t *cell, uint64_t *id) {
+  int d = m->dim;
+  int64_t g = 0;
+  for (int64_t K = 0; K < m->ncells; ++K) {
+    uint32_t nk = per_cell ? per_cell[K] : uniform_count;
+    for (uint32_t q = 0; q < nk; ++q, ++g) {
+      double t[3] = {0, 0, 0}, p[3] = {0, 0, 0};
+      for (int j = 0; j < d; ++j) {
+        uint64_t r = orc_splitmix64(seed, (uint64_t)g * (uint64_t)d + (uint64_t)j);
+        t[j] = (double)(r >> 11) * 0x1.0p-53;
+      }
+      orc_phi(m, K, t, p);
+      for (int j = 0; j < d; ++j) {
+        x[g * d + j] = p[j];
+        xhat[g * d + j] = t[j];
+      }
+      cell[g] = K;
+      id[g] = first_id + (uint64_t)g;
+    }
+  }
+  return g;
+}
+
+/* -------------------------------------------- advection (Sec. 2.3/2.4) --- */
+
+/* Velocity at a stage point: locate it (R7: every sub-step is followed by a
+ * determination of the containing cell, Sec. 2.4), then evaluate u_h there.
+ * Returns 0 if the point has no owner (the particle is lost, option 3). */
+static int stage_velocity(const orc_mesh *m, const double *y, double *u) {
+  double t[3];
+  int64_t K = orc_owner(m, y, t);
+  if (K < 0) return 0;
+  orc_q2_eval(m, K, t, u);
+  return 1;
+}
+
+/* One time step of one particle (Sec. 2.3 with reading R5):
+ *   Euler: x' = x + dt u(x)
+ *   RK2  : k1 = dt u(x);             x' = x + dt u(x + k1/2)      (midpoint)
+ *   RK4  : k1 = dt u(x), k2 = dt u(x + k1/2), k3 = dt u(x + k2/2),
+ *          k4 = dt u(x + k3);        x' = x + (k1 + 2k2 + 2k3 + k4)/6
+ * The first stage uses the stored (cell, x-hat) (Remark 2.1).  Then x' is
+ * located (Sec. 2.4); no owner -> lost (option 3, R7). */
+static void step_particle(const orc_mesh *m, orc_particle *p, double dt, int integrator) {
+  int d = m->dim;
+  double u[3] = {0, 0, 0}, k1[3] = {0, 0, 0}, k2[3] = {0, 0, 0}, k3[3] = {0, 0, 0}, k4[3] = {0, 0, 0};
+  double y[3] = {0, 0, 0}, xn[3] = {0, 0, 0};
+  orc_q2_eval(m, p->cell, p->xhat, u);
+  for (int j = 0; j < d; ++j) k1[j] = dt * u[j];
+  if (integrator == 1) {
+    for (int j = 0; j < d; ++j) xn[j] = p->x[j] + k1[j];
+  } else if (integrator == 2) {
+    for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k1[j];
+    if (!stage_velocity(m, y, u)) goto lost;
+    for (int j = 0; j < d; ++j) k2[j] = dt * u[j];
+    for (int j = 0; j < d; ++j) xn[j] = p->x[j] + k2[j];
+  } else {
+    for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k1[j];
+    if (!stage_velocity(m, y, u)) goto lost;
+    for (int j = 0; j < d; ++j) k2[j] = dt * u[j];
+    for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k2[j];
+    if (!stage_velocity(m, y, u)) goto lost;
+    for (int j = 0; j < d; ++j) k3[j] = dt * u[j];
+    for (int j = 0; j < d; ++j) y[j] = p->x[j] + k3[j];
+    if (!stage_velocity(m, y, u)) goto lost;
+    for (int j = 0; j < d; ++j) k4[j] = dt * u[j];
+    for (int j = 0; j < d; ++j) xn[j] = p->x[j] + (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]) / 6.0;
+  }
+  {
+    double t[3] = {0, 0, 0};
+    int64_t K = orc_owner(m, xn, t);
+    if (K < 0) goto lost;
+    for (int j = 0; j < d; ++j) {
+      p->x[j] = xn[j];
+      p->xhat[j] = t[j];
+    }
+    p->cell = K;
+  }
+  return;
+lost:
+  p->cell = -1;
+}
+
+static int cmp_cell_id(const void *a, const void *b) {
+  const orc_particle *p = (const orc_particle *)a, *q = (const orc_particle *)b;
+  if (p->cell != q->cell) return p->cell < q->cell ? -1 : 1;
+  if (p->id != q->id) return p->id < q->id ? -1 : 1;
+  return 0;
+}
+
+/* n_steps x (advance every particle, then update the particle-cell map):
+ * lost particles are removed (option 3 of the Sec. 2.4 listing), the rest
+ * are ordered by (cell, id) (R9: the multimap's order, made canonical).
+ * Arrays are particle-major and updated in place; props is [N][n_props].
+ * Returns the number of particles still alive; *n_lost_out gets the rest. */
+int64_t orc_advect(const orc_mesh *m, int64_t N, double *x, double *xhat, int64_t *cell, uint64_t *id, double *props,
+                   int n_props, double dt, int integrator, int n_steps, int64_t *n_lost_out) {
+  int d = m->dim;
+  orc_particle *P = (orc_particle *)calloc(N > 0 ? N : 1, sizeof(orc_particle));
+  double *pool = (double *)malloc(sizeof(double) * (N * n_props + 1));
+  for (int64_t i = 0; i < N; ++i) {
+    P[i].id = id[i];
+    P[i].cell = cell[i];
+    for (int j = 0; j < d; ++j) {
+      P[i].x[j] = x[i * d + j];
+      P[i].xhat[j] = xhat[i * d + j];
+    }
+    P[i].props = pool + i * n_props;
+    for (int q = 0; q < n_props; ++q) P[i].props[q] = props[i * n_props + q];
+  }
+  int64_t n = N, lost = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    for (int64_t i = 0; i < n; ++i) step_particle(m, &P[i], dt, integrator);
+    int64_t w = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (P[i].cell < 0) {
+        ++lost;
+        continue;
+      }
+      P[w++] = P[i];
+    }
+    n = w;
+    qsort(P, (size_t)n, sizeof(orc_particle), cmp_cell_id);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    id[i] = P[i].id;
+    cell[i] = P[i].cell;
+    for (int j = 0; j < d; ++j) {
+      x[i * d + j] = P[i].x[j];
+      xhat[i * d + j] = P[i].xhat[j];
+    }
+    for (int q = 0; q < n_props; ++q) props[i * n_props + q] = P[i].props[q];
+  }
+  free(pool);
+  free(P);
+  if (n_lost_out) *n_lost_out = lost;
+  return n;
+}
+
+/* Relocate arbitrary points: owner cell and x-hat of each (Sec. 2.4). */
+void orc_locate_points(const orc_mesh *m, int64_t n, const double *x, int64_t *cell, double *xhat, int brute) {
+  int d = m->dim;
+  for (int64_t i = 0; i < n; ++i) {
+    double t[3] = {0, 0, 0};
+    int64_t K = brute ? orc_owner_brute(m, x + i * d, t) : orc_owner(m, x + i * d, t);
+    cell[i] = K;
+    for (int j = 0; j < d; ++j) xhat[i * d + j] = K >= 0 ? t[j] : 0.0;
+  }
+}
+
+/* --------------------------- particle -> cell transfer (Sec. 2.7 (ii)) --- */
+
+/* Arithmetic average of one property over the particles of each cell, left
+ * fold in store order, divided by the count; empty cells get empty_fill and
+ * count 0 (R10). */
+void orc_cell_average(int64_t ncells, int64_t N, const int64_t *cell, const double *value, double empty_fill,
+                      double *avg, int64_t *count) {
+  double *sum = (double *)calloc(ncells > 0 ? ncells : 1, sizeof(double));
+  for (int64_t K = 0; K < ncells; ++K) count[K] = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    sum[cell[i]] = sum[cell[i]] + value[i];
+    count[cell[i]] += 1;
+  }
+  for (int64_t K = 0; K < ncells; ++K) avg[K] = count[K] > 0 ? sum[K] / (double)count[K] : empty_fill;
+  free(sum);
+}
