@@ -1,0 +1,196 @@
+/*
+ * pic.h -- C ABI of libpic.so, the GB300 (sm_103a) particle hot path of the
+ * particle-in-cell method of Gassmoeller, Heien, Puckett & Bangerth,
+ * "Flexible and scalable particle-in-cell methods for massively parallel
+ * computations" (arXiv 1612.03369).
+ *
+ * What the library computes, per call:
+ *   - particle generation from local coordinates  (Sec. 2.2, Remark "local generation")
+ *   - evaluation of the Q2 velocity u_h at stored reference coordinates
+ *     x-hat = Phi_K^{-1}(x)                        (Sec. 2.3, Remark 2.1)
+ *   - forward Euler / RK2 / RK4 advection          (Sec. 2.3)
+ *   - location of every stage point and of the new position: inverse of the
+ *     (bi/tri)linear cell map by Newton, then the vertex-neighbour walk, then
+ *     a search over all cells                      (Sec. 2.4)
+ *   - re-binning into a store sorted by (cell, id), lost particles removed
+ *                                                  (Sec. 2.1 data structure, Sec. 2.4 listing)
+ *   - arithmetic per-cell averages of a property   (Sec. 2.7, scheme (ii))
+ *
+ * Conventions
+ *   - Every call that takes a `stream` (a cudaStream_t, 0 = legacy default)
+ *     is asynchronous on it, unless its comment says it synchronises.
+ *   - Arguments are checked on the host before anything is enqueued; a bad
+ *     argument returns PIC_ERR_ARG and enqueues nothing.  pic_last_error()
+ *     gives a message for the last failure on the calling thread.
+ *   - Conditions found on the device (Newton non-convergence in a cell that
+ *     is then treated as not containing the point, capacity overflow, an
+ *     out-of-range index caught by a bounds check) are latched in a device
+ *     status word that pic_get_state() returns; the kernels never trap.
+ *   - Lost particles (a stage point or the new position in no cell, option 3
+ *     of the Sec. 2.4 listing) are not errors: they are removed and counted.
+ *   - Handles are not thread-safe; use one stream per particle handle.
+ *   - Coordinates are FP64.  Layouts are structure-of-arrays, component
+ *     major: an array documented as [dim][n] holds component a of item i at
+ *     a*n + i.
+ *   - Mesh topology is structured: n_cells[0] x n_cells[1] (x n_cells[2])
+ *     cells, cell (i,j,k) has index i + nx*(j + ny*k); vertex (i,j,k) has
+ *     index i + (nx+1)*(j + (ny+1)*k); Q2 node (I,J,K) has index
+ *     I + (2nx+1)*(J + (2ny+1)*K), and node (2i+a, 2j+b, 2k+c), a,b,c in
+ *     {0,1,2}, is node (a,b,c) of cell (i,j,k).  Vertex positions are free
+ *     (any non-degenerate (bi/tri)linear cells).
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_mesh_s *pic_mesh;           /* owned by the library; pic_destroy_mesh */
+typedef struct pic_particles_s *pic_particles; /* owned by the library; pic_destroy_particles */
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = 1,           /* invalid argument; nothing was enqueued */
+  PIC_ERR_OOM = 2,           /* device allocation failed */
+  PIC_ERR_CAPACITY = 3,      /* more particles than the store's capacity */
+  PIC_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in pic_last_error) */
+  PIC_ERR_NOT_CONVERGED = 5, /* reserved for callers that treat Newton failure as fatal */
+  PIC_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+  PIC_ERR_STATE = 7          /* call not valid in the handle's current state */
+} pic_status;
+
+typedef enum { PIC_EULER = 1, PIC_RK2 = 2, PIC_RK4 = 4 } pic_integrator;
+typedef enum { PIC_FP64 = 0, PIC_FP32_BASIS = 1 } pic_precision;
+typedef enum { PIC_AVG_ARITHMETIC = 0 } pic_average;
+
+/* Bits of the device status word (pic_get_state). */
+#define PIC_STATUS_NEWTON_NONCONV 0x1u /* Newton hit its iteration cap in some candidate cell */
+#define PIC_STATUS_CAPACITY 0x2u       /* a store or list overflowed; data past capacity dropped */
+#define PIC_STATUS_GLOBAL_SEARCH 0x4u  /* the all-cells search ran for some point */
+#define PIC_STATUS_BOUNDS 0x8u         /* a bounds check caught an out-of-range index; access skipped */
+
+/* Mesh of (bi/tri)linear cells with a Q2 velocity field (Sec. 2.1, 2.3).
+ *   dim       2 or 3
+ *   n_cells   [dim] cells per axis, each >= 1; total cells < 2^31
+ *   vertices  [dim][nverts] FP64 positions, nverts = prod(n_cells[a]+1);
+ *             on the device if vertices_on_device, else host memory
+ *   stream    stream for the upload and the per-cell set-up kernels
+ *   out       receives the handle
+ * The library copies the vertices; the caller keeps ownership of its array.
+ * Synchronises `stream` before returning (the handle is usable at once).
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_create_mesh(int dim, const int *n_cells, const double *vertices, int vertices_on_device, void *stream,
+                           pic_mesh *out);
+pic_status pic_destroy_mesh(pic_mesh mesh);
+
+/* Q2 nodal velocity u_h (Sec. 2.3: the finite-element field whose evaluation
+ * at particle positions is "the primary expense").
+ *   U       [dim][nnodes] FP64 on the device, nnodes = prod(2*n_cells[a]+1)
+ *   U_next  must be NULL (time interpolation between two fields is not built)
+ * The library copies U (stream-ordered); the caller may reuse U afterwards.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_set_velocity_dofs(pic_mesh mesh, const double *U, const double *U_next, void *stream);
+
+/* Generation from local coordinates (Sec. 2.2, Remark "local generation"):
+ * cells are visited in index order and n_K particles created in cell K with
+ * reference coordinates x-hat uniform in [0,1)^dim, position x = Phi_K(x-hat),
+ * id = first_id + (number of particles created before it).  x-hat_j of the
+ * g-th particle is (r >> 11) * 2^-53 with r output number g*dim + j (0-based)
+ * of SplitMix64 (Steele, Lea & Flood 2014) seeded with `seed`.
+ *   per_cell       [n_cells] u32 on the device, or NULL for uniform_count per cell
+ *   n_props        properties per particle (0..16), initialised to 0
+ *   capacity       store capacity (>= number created); 0 = exactly the number created
+ *   out            receives the handle; the store is sorted by (cell, id)
+ * Synchronises `stream` (reads the total count).  Errors: PIC_ERR_ARG,
+ * PIC_ERR_CAPACITY, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_seed_particles(pic_mesh mesh, const uint32_t *per_cell, uint32_t uniform_count, uint64_t seed,
+                              uint64_t first_id, int n_props, size_t capacity, void *stream, pic_particles *out);
+pic_status pic_destroy_particles(pic_particles parts);
+
+/* Property p of every particle from values [N] (device, store order).
+ * Sec. 2.6: a run-time number of scalars per particle. */
+pic_status pic_set_properties(pic_particles parts, int prop, const double *values, void *stream);
+
+/* n_steps time steps (Sec. 2.3 and the Sec. 2.4 listing), each:
+ *   - every particle advances with the integrator; the first stage uses the
+ *     stored (cell, x-hat); every later stage point and the new position are
+ *     located (Newton in the hint cell, vertex-neighbour walk, all-cells
+ *     search; the lowest cell index owns points on shared faces)
+ *   - a particle with a stage point or new position in no cell is lost
+ *   - the store is rebuilt sorted by (cell, id) with lost particles removed
+ * Integrators (classical forms, reading of the garbled printed formulas):
+ *   PIC_EULER x + dt u(x);  PIC_RK2 midpoint x + dt u(x + dt/2 u(x));
+ *   PIC_RK4 x + (k1 + 2 k2 + 2 k3 + k4)/6, k1 = dt u(x), k2 = dt u(x + k1/2),
+ *   k3 = dt u(x + k2/2), k4 = dt u(x + k3).
+ *   precision  PIC_FP64, or PIC_FP32_BASIS (Q2 basis and contraction in FP32;
+ *              positions and the inverse-map residual stay FP64)
+ * Errors: PIC_ERR_ARG (mesh/store mismatch, dt not finite, n_steps < 0,
+ * velocity not set), PIC_ERR_CUDA. */
+pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                      pic_precision precision, int n_steps, void *stream);
+
+/* Re-locate every particle at its current position, using its current cell
+ * as the hint (Sec. 2.4), then rebuild the store as pic_rebin does.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_locate(pic_particles parts, pic_mesh mesh, void *stream);
+
+/* Rebuild the store sorted by (cell, id), dropping particles marked lost
+ * (Sec. 2.1 "sorted by their containing cells", Sec. 2.4 batched
+ * re-insertion).  Uses the cells found by the last locate.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_rebin(pic_particles parts, void *stream);
+
+/* Stateless point location (Sec. 2.4, and Sec. 2.2 prescribed positions):
+ *   x        [dim][n] device positions
+ *   hint     [n] device start cells, or NULL (then cell 0's neighbourhood is
+ *            skipped and every point goes to the all-cells search)
+ *   cell_out [n] device owner cells (lowest index on shared faces), or
+ *            0xFFFFFFFF if no cell contains the point
+ *   xhat_out [dim][n] device reference coordinates in the owner (0 if none)
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_locate_points(pic_mesh mesh, size_t n, const double *x, const uint32_t *hint, uint32_t *cell_out,
+                             double *xhat_out, void *stream);
+
+/* Particle -> cell transfer (Sec. 2.7, scheme (ii), arithmetic average):
+ * avg[K] = (sum of property `prop` over the particles of K) / n_K, summed in
+ * a fixed order (deterministic); count[K] = n_K; empty cells get empty_fill.
+ *   avg    [n_cells] FP64 device;  count  [n_cells] u32 device (may be NULL)
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_interpolate_to_cells(pic_particles parts, pic_mesh mesh, int prop, pic_average kind, double *avg,
+                                    uint32_t *count, double empty_fill, void *stream);
+
+/* Synchronises the particle stream and reads the state: alive particles,
+ * particles lost since seeding, and the device status word (bits above).
+ * Any output pointer may be NULL. */
+pic_status pic_get_state(pic_particles parts, size_t *n_alive, size_t *n_lost, uint32_t *status_word);
+
+/* Per-call counters since seeding: particle-steps advanced, points that
+ * needed the neighbour walk, points that needed the all-cells search, Newton
+ * iterations.  Synchronises. */
+pic_status pic_get_stats(pic_particles parts, uint64_t *particle_steps, uint64_t *walks, uint64_t *global_searches,
+                         uint64_t *newton_iterations);
+
+/* Copy the store out in (cell, id) order.  Synchronises `stream` first to
+ * read the particle count.  Any pointer may be NULL; host or device memory.
+ *   x, xhat [dim][N] FP64;  id [N] u64;  cell [N] u32;  props [n_props][N] FP64 */
+pic_status pic_export(pic_particles parts, double *x, double *xhat, uint64_t *id, uint32_t *cell, double *props,
+                      void *stream);
+
+/* Cell offsets of the sorted store: off[K]..off[K+1] are the particles of
+ * cell K.  off is [n_cells + 1] u32, device or host. */
+pic_status pic_cell_offsets(pic_particles parts, uint32_t *off, void *stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *pic_last_error(void);
+
+/* Library version string. */
+const char *pic_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,55 @@
+// average.cu -- particle -> cell transfer, scheme (ii) of Sec. 2.7
+// (arithmetic average of the particles of each cell; optimal complexity
+// because the store is sorted by cell).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// Warp per cell.  Lane l sums elements l, l+32, ... of the cell's segment in
+// order, then a fixed xor-butterfly combines the 32 partial sums, so the
+// result depends only on the segment (deterministic, no atomics).
+__global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __restrict__ cell_off,
+                                                           const double* __restrict__ prop, uint32_t C, size_t cap,
+                                                           double empty_fill, double* __restrict__ avg,
+                                                           uint32_t* __restrict__ count, DevCounters* __restrict__ ctr) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
+    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
+    if (end > cap || beg > end) {
+      if (lane == 0) latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    double s = 0.0;
+    for (uint32_t i = beg + lane; i < end; i += 32) s += prop[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      const uint32_t n = end - beg;
+      avg[K] = n ? s / (double)n : empty_fill;
+      if (count) count[K] = n;
+    }
+  }
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" pic_status pic_interpolate_to_cells(pic_particles p, pic_mesh mesh, int prop, pic_average kind, double* avg,
+                                               uint32_t* count, double empty_fill, void* stream) {
+  if (!p || !mesh || !avg) return (set_error("pic_interpolate_to_cells: null argument"), PIC_ERR_ARG);
+  if (p->mesh != mesh) return (set_error("pic_interpolate_to_cells: mesh mismatch"), PIC_ERR_ARG);
+  if (prop < 0 || prop >= p->n_props)
+    return (set_error("pic_interpolate_to_cells: property %d out of range", prop), PIC_ERR_ARG);
+  if (kind != PIC_AVG_ARITHMETIC) return (set_error("pic_interpolate_to_cells: unknown average %d", (int)kind), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t warps_needed = p->C;
+  size_t grid = (warps_needed * 32 + 255) / 256;
+  const size_t cap = (size_t)num_sms() * 16;
+  if (grid > cap) grid = cap;
+  cell_average_kernel<<<(int)(grid ? grid : 1), 256, 0, st>>>(p->cell_off, p->props[p->cur] + (size_t)prop * p->capacity,
+                                                              p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}

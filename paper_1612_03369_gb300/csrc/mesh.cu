@@ -1,0 +1,151 @@
+// mesh.cu -- mesh and velocity handles: vertex upload, per-cell bounding
+// boxes for the all-cells search, and the Q2 nodal velocity (Sec. 2.3).
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// Padded bounding box of every cell (lo xyz, hi xyz): the all-cells search
+// of Sec. 2.4 only runs the inverse map in cells whose box holds the point.
+template <int D>
+__global__ void cell_bbox_kernel(MeshView m, double* __restrict__ bbox) {
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
+    CellGeom<D> g;
+    load_cell<D>(m, K, g);
+    for (int a = 0; a < 3; ++a) {
+      double lo = 0.0, hi = 0.0;
+      if (a < D) {
+        lo = hi = g.x0[a];
+        for (int v = 1; v < (1 << D); ++v) {
+          lo = fmin(lo, g.x0[a] + g.e[v][a]);
+          hi = fmax(hi, g.x0[a] + g.e[v][a]);
+        }
+        const double pad = 1e-6 * (hi - lo);
+        lo -= pad;
+        hi += pad;
+      }
+      bbox[6 * (size_t)K + a] = lo;
+      bbox[6 * (size_t)K + 3 + a] = hi;
+    }
+  }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double* vertices, int vertices_on_device,
+                                      void* stream, pic_mesh* out) {
+  if (!out) return (set_error("pic_create_mesh: out is NULL"), PIC_ERR_ARG);
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return (set_error("pic_create_mesh: dim must be 2 or 3 (got %d)", dim), PIC_ERR_ARG);
+  if (!n_cells || !vertices) return (set_error("pic_create_mesh: null array"), PIC_ERR_ARG);
+  uint64_t C = 1, nv = 1, nq = 1;
+  for (int a = 0; a < dim; ++a) {
+    if (n_cells[a] < 1) return (set_error("pic_create_mesh: n_cells[%d] = %d < 1", a, n_cells[a]), PIC_ERR_ARG);
+    C *= (uint64_t)n_cells[a];
+    nv *= (uint64_t)n_cells[a] + 1;
+    nq *= 2 * (uint64_t)n_cells[a] + 1;
+  }
+  if (C >= (1ull << 31) || nq >= (1ull << 40))
+    return (set_error("pic_create_mesh: mesh too large (%llu cells)", (unsigned long long)C), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  pic_mesh_s* m = (pic_mesh_s*)calloc(1, sizeof(pic_mesh_s));
+  if (!m) return (set_error("pic_create_mesh: host allocation failed"), PIC_ERR_OOM);
+  m->dim = dim;
+  for (int a = 0; a < 3; ++a) {
+    m->n[a] = a < dim ? n_cells[a] : 1;
+    m->nv[a] = a < dim ? n_cells[a] + 1 : 1;
+    m->nq[a] = a < dim ? 2 * n_cells[a] + 1 : 1;
+  }
+  m->C = (uint32_t)C;
+  m->nverts = (int64_t)nv;
+  m->nnodes = (int64_t)nq;
+  auto fail = [&](pic_status s) {
+    pic_destroy_mesh(m);
+    return s;
+  };
+  if (cudaMalloc(&m->X, sizeof(double) * dim * nv) != cudaSuccess ||
+      cudaMalloc(&m->bbox, sizeof(double) * 6 * C) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("pic_create_mesh: device allocation failed");
+    return fail(PIC_ERR_OOM);
+  }
+  // Host copy of the vertices for the padded domain box.
+  std::vector<double> hX((size_t)dim * nv);
+  cudaError_t e = cudaMemcpyAsync(hX.data(), vertices, sizeof(double) * dim * nv,
+                                  vertices_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->X, hX.data(), sizeof(double) * dim * nv, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "pic_create_mesh: vertex upload"));
+  for (int a = 0; a < 3; ++a) {
+    double lo = 0.0, hi = 0.0;
+    if (a < dim) {
+      lo = INFINITY;
+      hi = -INFINITY;
+      for (uint64_t v = 0; v < nv; ++v) {
+        const double c = hX[(size_t)a * nv + v];
+        if (!std::isfinite(c)) {
+          set_error("pic_create_mesh: vertex %llu has a non-finite coordinate", (unsigned long long)v);
+          return fail(PIC_ERR_ARG);
+        }
+        lo = c < lo ? c : lo;
+        hi = c > hi ? c : hi;
+      }
+      const double pad = 1e-9 * (hi - lo);
+      lo -= pad;
+      hi += pad;
+    }
+    m->dlo[a] = lo;
+    m->dhi[a] = hi;
+  }
+  const MeshView mv = mesh_view(m);
+  const int grid = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
+  if (dim == 2)
+    cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox);
+  else
+    cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "pic_create_mesh: set-up kernels"));
+  *out = m;
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
+  if (!m) return PIC_OK;
+  cudaFree(m->X);
+  cudaFree(m->U);
+  cudaFree(m->U32);
+  cudaFree(m->bbox);
+  free(m);
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const double* U_next, void* stream) {
+  if (!m || !U) return (set_error("pic_set_velocity_dofs: null argument"), PIC_ERR_ARG);
+  if (U_next)
+    return (set_error("pic_set_velocity_dofs: time interpolation between two fields is not supported"), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
+  if (!m->U) {
+    if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32, sizeof(float) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
+    }
+  }
+  PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
+  to_f32_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(m->U, m->U32, n);
+  PIC_CUDA(cudaGetLastError());
+  m->has_velocity = 1;
+  return PIC_OK;
+}

@@ -1,0 +1,277 @@
+// particles.cu -- the particle store (Sec. 2.1): generation from local
+// coordinates (Sec. 2.2), properties (Sec. 2.6), state queries and export.
+#include <cstdlib>
+#include <cstring>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a counter-based
+// generator: output n of the stream seeded with `seed` is the finaliser
+// applied to seed + (n + 1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
+  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void fill_counts_kernel(const uint32_t* __restrict__ per_cell, uint32_t uniform, uint32_t* __restrict__ counts,
+                                   uint32_t C) {
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < C; K += gridDim.x * blockDim.x)
+    counts[K] = per_cell ? per_cell[K] : uniform;
+}
+
+// Remark "local generation" (Sec. 2.2): loop over cells in order and over
+// local coordinates inside each; only the forward map Phi_K is needed.
+template <int D>
+__global__ void seed_kernel(MeshView m, StoreView s, const uint32_t* __restrict__ cell_off, uint64_t seed,
+                            uint64_t first_id) {
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
+    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
+    if (end > s.cap) continue;
+    CellGeom<D> g;
+    load_cell<D>(m, K, g);
+    for (uint32_t q = beg; q < end; ++q) {
+      double t[D], x[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const uint64_t r = splitmix64_at(seed, (uint64_t)q * D + j);
+        t[j] = (double)(r >> 11) * 0x1.0p-53;
+      }
+      map_point<D>(g, t, x);
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        s.x[j * s.cap + q] = x[j];
+        s.xhat[j * s.cap + q] = t[j];
+      }
+      s.id[q] = first_id + q;
+      s.cell[q] = K;
+      for (int p = 0; p < s.n_props; ++p) s.props[p * s.cap + q] = 0.0;
+    }
+  }
+}
+
+__global__ void set_prop_kernel(double* __restrict__ dst, const double* __restrict__ src, const DevCounters* ctr) {
+  const uint32_t n = ctr->n_alive;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" pic_status pic_destroy_particles(pic_particles p) {
+  if (!p) return PIC_OK;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(p->x[b]);
+    cudaFree(p->xhat[b]);
+    cudaFree(p->id[b]);
+    cudaFree(p->cell[b]);
+    cudaFree(p->props[b]);
+  }
+  cudaFree(p->cell_off);
+  cudaFree(p->cell_new);
+  cudaFree(p->counts);
+  cudaFree(p->cursor);
+  cudaFree(p->block_sums);
+  cudaFree(p->key_id);
+  cudaFree(p->key_src);
+  cudaFree(p->perm);
+  cudaFree(p->ctr);
+  free(p);
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, uint64_t seed,
+                                         uint64_t first_id, int n_props, size_t capacity, void* stream,
+                                         pic_particles* out) {
+  if (!out) return (set_error("pic_seed_particles: out is NULL"), PIC_ERR_ARG);
+  *out = nullptr;
+  if (!mesh) return (set_error("pic_seed_particles: null mesh"), PIC_ERR_ARG);
+  if (n_props < 0 || n_props > kMaxProps)
+    return (set_error("pic_seed_particles: n_props must be in [0, %d]", kMaxProps), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  const uint32_t C = mesh->C;
+  // Count first (per-cell numbers may live on the device).
+  uint32_t *counts = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
+  const uint32_t nb = scan_block_count(C);
+  if (cudaMalloc(&counts, sizeof(uint32_t) * C) != cudaSuccess || cudaMalloc(&off, sizeof(uint32_t) * (C + 1)) != cudaSuccess ||
+      cudaMalloc(&sums, sizeof(uint32_t) * (nb + 1)) != cudaSuccess || cudaMalloc(&total, sizeof(uint32_t) * 2) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(counts);
+    cudaFree(off);
+    cudaFree(sums);
+    cudaFree(total);
+    return (set_error("pic_seed_particles: device allocation failed"), PIC_ERR_OOM);
+  }
+  auto cleanup_tmp = [&]() {
+    cudaFree(counts);
+    cudaFree(sums);
+    cudaFree(total);
+  };
+  fill_counts_kernel<<<(C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096, 256, 0, st>>>(per_cell, uniform_count, counts, C);
+  // 64-bit total check: the scan is 32-bit, so guard against overflow first
+  uint64_t total64 = 0;
+  if (per_cell) {
+    uint32_t* h = (uint32_t*)malloc(sizeof(uint32_t) * C);
+    cudaError_t e = cudaMemcpyAsync(h, per_cell, sizeof(uint32_t) * C, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      free(h);
+      cleanup_tmp();
+      cudaFree(off);
+      return cuda_fail(e, "pic_seed_particles: reading per_cell");
+    }
+    for (uint32_t K = 0; K < C; ++K) total64 += h[K];
+    free(h);
+  } else {
+    total64 = (uint64_t)uniform_count * C;
+  }
+  if (total64 >= 0xFFFFFFF0ull) {
+    cleanup_tmp();
+    cudaFree(off);
+    return (set_error("pic_seed_particles: %llu particles exceed the 32-bit store", (unsigned long long)total64),
+            PIC_ERR_CAPACITY);
+  }
+  const size_t N = (size_t)total64;
+  if (capacity == 0) capacity = N;
+  if (capacity < N) {
+    cleanup_tmp();
+    cudaFree(off);
+    return (set_error("pic_seed_particles: capacity %zu < %zu particles", capacity, N), PIC_ERR_CAPACITY);
+  }
+  if (capacity >= 0xFFFFFFF0ull) {
+    cleanup_tmp();
+    cudaFree(off);
+    return (set_error("pic_seed_particles: capacity exceeds the 32-bit store"), PIC_ERR_CAPACITY);
+  }
+  pic_status r = scan_u32(counts, off, C, sums, total, nullptr, st);
+  cleanup_tmp();
+  if (r != PIC_OK) {
+    cudaFree(off);
+    return r;
+  }
+
+  pic_particles_s* p = (pic_particles_s*)calloc(1, sizeof(pic_particles_s));
+  p->dim = mesh->dim;
+  p->n_props = n_props;
+  p->C = C;
+  p->mesh = mesh;
+  p->capacity = capacity > 0 ? capacity : 1;
+  p->cell_off = off;
+  p->stream = st;
+  const size_t cap = p->capacity, d = (size_t)mesh->dim;
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; ++b) {
+    ok = ok && cudaMalloc(&p->x[b], sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->xhat[b], sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->id[b], sizeof(uint64_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->cell[b], sizeof(uint32_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->props[b], sizeof(double) * (n_props > 0 ? n_props : 1) * cap) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&p->cell_new, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->counts, sizeof(uint32_t) * C) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->cursor, sizeof(uint32_t) * C) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->block_sums, sizeof(uint32_t) * (nb + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->key_id, sizeof(uint64_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->key_src, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->perm, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->ctr, sizeof(DevCounters)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pic_destroy_particles(p);
+    return (set_error("pic_seed_particles: device allocation failed (capacity %zu)", cap), PIC_ERR_OOM);
+  }
+  DevCounters h{};
+  h.n_alive = (uint32_t)N;
+  h.n_next = (uint32_t)N;
+  cudaError_t e = cudaMemcpyAsync(p->ctr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    pic_destroy_particles(p);
+    return cuda_fail(e, "pic_seed_particles: counters");
+  }
+  const MeshView m = mesh_view(mesh);
+  const int grid = (int)((C + 127) / 128 < 8192 ? (C + 127) / 128 : 8192);
+  if (mesh->dim == 2)
+    seed_kernel<2><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id);
+  else
+    seed_kernel<3><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    pic_destroy_particles(p);
+    return cuda_fail(e, "pic_seed_particles: seed kernel");
+  }
+  p->cur = 0;
+  *out = p;
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_set_properties(pic_particles p, int prop, const double* values, void* stream) {
+  if (!p || !values) return (set_error("pic_set_properties: null argument"), PIC_ERR_ARG);
+  if (prop < 0 || prop >= p->n_props) return (set_error("pic_set_properties: property %d out of range", prop), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  set_prop_kernel<<<1024, 256, 0, st>>>(p->props[p->cur] + (size_t)prop * p->capacity, values, p->ctr);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+static pic_status read_counters(pic_particles p, DevCounters* h) {
+  PIC_CUDA(cudaDeviceSynchronize());
+  PIC_CUDA(cudaMemcpy(h, p->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost));
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_get_state(pic_particles p, size_t* n_alive, size_t* n_lost, uint32_t* status_word) {
+  if (!p) return (set_error("pic_get_state: null handle"), PIC_ERR_ARG);
+  DevCounters h;
+  pic_status r = read_counters(p, &h);
+  if (r != PIC_OK) return r;
+  if (n_alive) *n_alive = h.n_alive;
+  if (n_lost) *n_lost = (size_t)h.lost_total;
+  if (status_word) *status_word = h.status;
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_get_stats(pic_particles p, uint64_t* particle_steps, uint64_t* walks, uint64_t* global_searches,
+                                    uint64_t* newton_iterations) {
+  if (!p) return (set_error("pic_get_stats: null handle"), PIC_ERR_ARG);
+  DevCounters h;
+  pic_status r = read_counters(p, &h);
+  if (r != PIC_OK) return r;
+  if (particle_steps) *particle_steps = h.particle_steps;
+  if (walks) *walks = h.walks;
+  if (global_searches) *global_searches = h.global_searches;
+  if (newton_iterations) *newton_iterations = h.newton_iterations;
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_export(pic_particles p, double* x, double* xhat, uint64_t* id, uint32_t* cell, double* props,
+                                 void* stream) {
+  if (!p) return (set_error("pic_export: null handle"), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  DevCounters h;
+  pic_status r = read_counters(p, &h);
+  if (r != PIC_OK) return r;
+  const size_t N = h.n_alive, cap = p->capacity;
+  const int c = p->cur;
+  if (N == 0) return PIC_OK;
+  for (int a = 0; a < p->dim; ++a) {
+    if (x) PIC_CUDA(cudaMemcpyAsync(x + a * N, p->x[c] + a * cap, sizeof(double) * N, cudaMemcpyDefault, st));
+    if (xhat) PIC_CUDA(cudaMemcpyAsync(xhat + a * N, p->xhat[c] + a * cap, sizeof(double) * N, cudaMemcpyDefault, st));
+  }
+  if (id) PIC_CUDA(cudaMemcpyAsync(id, p->id[c], sizeof(uint64_t) * N, cudaMemcpyDefault, st));
+  if (cell) PIC_CUDA(cudaMemcpyAsync(cell, p->cell[c], sizeof(uint32_t) * N, cudaMemcpyDefault, st));
+  for (int q = 0; q < p->n_props && props; ++q)
+    PIC_CUDA(cudaMemcpyAsync(props + q * N, p->props[c] + q * cap, sizeof(double) * N, cudaMemcpyDefault, st));
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_cell_offsets(pic_particles p, uint32_t* off, void* stream) {
+  if (!p || !off) return (set_error("pic_cell_offsets: null argument"), PIC_ERR_ARG);
+  PIC_CUDA(cudaMemcpyAsync(off, p->cell_off, sizeof(uint32_t) * ((size_t)p->C + 1), cudaMemcpyDefault,
+                           (cudaStream_t)stream));
+  return PIC_OK;
+}

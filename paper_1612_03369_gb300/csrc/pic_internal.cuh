@@ -1,0 +1,373 @@
+// pic_internal.cuh -- handle layouts, device views and device-side building
+// blocks shared by the translation units of libpic.so.
+//
+// The method is the particle hot path of Gassmoeller, Heien, Puckett &
+// Bangerth, arXiv 1612.03369: Q2 velocity evaluated at stored reference
+// coordinates (Sec. 2.3, Remark 2.1), RK integration (Sec. 2.3), point
+// location by inverse mapping plus a vertex-neighbour walk (Sec. 2.4), and a
+// particle store kept sorted by cell (Sec. 2.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pic.h"
+
+#define PIC_LOST 0xFFFFFFFFu
+
+namespace pic {
+
+// ------------------------------------------------------------ constants --
+// Inverse-map Newton: stop when max|delta| <= 1e-14 (reference coordinates
+// are dimensionless), give up after 30 iterations (then "not in this cell").
+constexpr double kNewtonTol = 1e-14;
+constexpr int kNewtonMaxIt = 30;
+// A point is inside K when its reference coordinates lie in [-eps, 1+eps]^d;
+// the band keeps points on shared faces inside both neighbours, and the
+// lowest cell index then owns them.
+constexpr double kInsideEps = 1e-10;
+// Reference-coordinate distance to a facet under which the cells across that
+// facet are also tested for the lowest-index rule.  Any other cell that holds
+// the point (within kInsideEps) must lie across a facet closer than this.
+constexpr double kTieBand = 1e-6;
+constexpr int kMaxProps = 16;
+
+// ------------------------------------------------------------ handles --
+
+struct DevCounters {
+  unsigned long long particle_steps;
+  unsigned long long walks;
+  unsigned long long global_searches;
+  unsigned long long newton_iterations;
+  unsigned long long lost_total;
+  unsigned int status;
+  unsigned int n_alive;  // particles in the store
+  unsigned int n_next;   // particles after the pending rebin
+  unsigned int fail_count;
+};
+
+}  // namespace pic
+
+struct pic_mesh_s {
+  int dim;
+  int n[3];      // cells per axis (1 on unused axes)
+  int nv[3];     // vertices per axis
+  int nq[3];     // Q2 nodes per axis
+  uint32_t C;    // cells
+  int64_t nverts, nnodes;
+  double* X;     // [dim][nverts]
+  double* U;     // [dim][nnodes]
+  float* U32;    // [dim][nnodes] FP32 copy for the FP32-basis form
+  double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
+  double dlo[3], dhi[3];  // padded domain bounding box
+  int has_velocity;
+};
+
+struct pic_particles_s {
+  int dim;
+  int n_props;
+  uint32_t C;             // cells of the mesh it was seeded on
+  const pic_mesh_s* mesh;
+  size_t capacity;
+  // double-buffered store, component-major with stride `capacity`
+  double* x[2];
+  double* xhat[2];
+  uint64_t* id[2];
+  uint32_t* cell[2];
+  double* props[2];
+  int cur;                // which buffer holds the sorted store
+  uint32_t* cell_off;     // [C+1]
+  // scratch for the rebin
+  uint32_t* cell_new;     // [capacity]
+  uint32_t* counts;       // [C]
+  uint32_t* cursor;       // [C]
+  uint32_t* block_sums;   // [scan blocks]
+  uint64_t* key_id;       // [capacity]
+  uint32_t* key_src;      // [capacity]
+  uint32_t* perm;         // [capacity]
+  pic::DevCounters* ctr;  // device counters and status word
+  cudaStream_t stream;
+};
+
+namespace pic {
+
+// ---------------------------------------------------- host error helpers --
+void set_error(const char* fmt, ...);
+pic_status cuda_fail(cudaError_t e, const char* what);
+#define PIC_CUDA(call)                                 \
+  do {                                                 \
+    cudaError_t _e = (call);                           \
+    if (_e != cudaSuccess) return pic::cuda_fail(_e, #call); \
+  } while (0)
+
+// ------------------------------------------------------- device views --
+
+struct MeshView {
+  int n[3], nv[3], nq[3];
+  uint32_t C;
+  int64_t nverts, nnodes;
+  const double* X;
+  const double* U;
+  const float* U32;
+  const double* bbox;
+  double dlo[3], dhi[3];
+};
+
+inline MeshView mesh_view(const pic_mesh_s* m) {
+  MeshView v;
+  for (int a = 0; a < 3; ++a) {
+    v.n[a] = m->n[a];
+    v.nv[a] = m->nv[a];
+    v.nq[a] = m->nq[a];
+    v.dlo[a] = m->dlo[a];
+    v.dhi[a] = m->dhi[a];
+  }
+  v.C = m->C;
+  v.nverts = m->nverts;
+  v.nnodes = m->nnodes;
+  v.X = m->X;
+  v.U = m->U;
+  v.U32 = m->U32;
+  v.bbox = m->bbox;
+  return v;
+}
+
+struct StoreView {
+  double* x;      // [dim][cap]
+  double* xhat;   // [dim][cap]
+  uint64_t* id;
+  uint32_t* cell;
+  double* props;  // [P][cap]
+  size_t cap;
+  int n_props;
+};
+
+inline StoreView store_view(pic_particles_s* p, int buf) {
+  StoreView s;
+  s.x = p->x[buf];
+  s.xhat = p->xhat[buf];
+  s.id = p->id[buf];
+  s.cell = p->cell[buf];
+  s.props = p->props[buf];
+  s.cap = p->capacity;
+  s.n_props = p->n_props;
+  return s;
+}
+
+__device__ __forceinline__ void latch_status(DevCounters* c, unsigned int bit) {
+  if ((c->status & bit) == 0) atomicOr(&c->status, bit);
+}
+
+// Cell (i,j,k) from its index.
+template <int D>
+__device__ __forceinline__ void cell_ijk(const MeshView& m, uint32_t K, int ijk[3]) {
+  ijk[0] = (int)(K % (uint32_t)m.n[0]);
+  if (D == 3) {
+    uint32_t r = K / (uint32_t)m.n[0];
+    ijk[1] = (int)(r % (uint32_t)m.n[1]);
+    ijk[2] = (int)(r / (uint32_t)m.n[1]);
+  } else {
+    ijk[1] = (int)(K / (uint32_t)m.n[0]);
+    ijk[2] = 0;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t cell_index(const MeshView& m, int i, int j, int k) {
+  return (uint32_t)i + (uint32_t)m.n[0] * ((uint32_t)j + (D == 3 ? (uint32_t)m.n[1] * (uint32_t)k : 0u));
+}
+
+// --------------------------------------------------- cell geometry (FP64) --
+// The (bi/tri)linear map Phi_K(t) = sum_v X_v w_v(t), w_v = prod_j (v_j ? t_j
+// : 1-t_j), is held as offsets from vertex 0 so that the Newton residual
+// (y - X_0) - sum_v (X_v - X_0) w_v(t) carries no cancellation of O(1)
+// coordinates.
+
+template <int D>
+struct CellGeom {
+  double x0[D];                 // vertex 0
+  double e[(1 << D)][D];        // X_v - X_0 (e[0] = 0)
+};
+
+template <int D>
+__device__ __forceinline__ void load_cell(const MeshView& m, uint32_t K, CellGeom<D>& g) {
+  int c[3];
+  cell_ijk<D>(m, K, c);
+  int64_t v0 = (int64_t)c[0] + (int64_t)m.nv[0] * ((int64_t)c[1] + (D == 3 ? (int64_t)m.nv[1] * c[2] : 0));
+#pragma unroll
+  for (int a = 0; a < D; ++a) g.x0[a] = __ldg(m.X + a * m.nverts + v0);
+#pragma unroll
+  for (int v = 0; v < (1 << D); ++v) {
+    int64_t off = (int64_t)(v & 1) + (int64_t)m.nv[0] * ((int64_t)((v >> 1) & 1) +
+                                                        (D == 3 ? (int64_t)m.nv[1] * ((v >> 2) & 1) : 0));
+#pragma unroll
+    for (int a = 0; a < D; ++a) g.e[v][a] = (v == 0) ? 0.0 : __ldg(m.X + a * m.nverts + v0 + off) - g.x0[a];
+  }
+}
+
+// phi = Phi_K(t) - X_0 and J = dPhi/dt.
+template <int D>
+__device__ __forceinline__ void map_and_jacobian(const CellGeom<D>& g, const double t[D], double phi[D],
+                                                 double J[D][D]) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    phi[a] = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) J[a][j] = 0.0;
+  }
+#pragma unroll
+  for (int v = 1; v < (1 << D); ++v) {
+    double w = 1.0, dw[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) dw[j] = 1.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const bool hi = (v >> j) & 1;
+      const double f = hi ? t[j] : 1.0 - t[j];
+      const double df = hi ? 1.0 : -1.0;
+      w *= f;
+#pragma unroll
+      for (int q = 0; q < D; ++q) dw[q] *= (q == j) ? df : f;
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      phi[a] += g.e[v][a] * w;
+#pragma unroll
+      for (int j = 0; j < D; ++j) J[a][j] += g.e[v][a] * dw[j];
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void map_point(const CellGeom<D>& g, const double t[D], double x[D]) {
+  double phi[D], J[D][D];
+  map_and_jacobian<D>(g, t, phi, J);
+#pragma unroll
+  for (int a = 0; a < D; ++a) x[a] = g.x0[a] + phi[a];
+}
+
+// Solve J d = r with the adjugate; false if J is singular.
+template <int D>
+__device__ __forceinline__ bool solve(const double J[D][D], const double r[D], double d[D]) {
+  if (D == 2) {
+    double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+    double inv = 1.0 / det;
+    d[0] = (J[1][1] * r[0] - J[0][1] * r[1]) * inv;
+    d[1] = (J[0][0] * r[1] - J[1][0] * r[0]) * inv;
+    return true;
+  } else {
+    double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+    double inv = 1.0 / det;
+    double c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    double c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    double c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    double c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    double c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    double c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    // inverse = adj / det, adj[i][j] = cofactor[j][i]
+    d[0] = (c00 * r[0] + c10 * r[1] + c20 * r[2]) * inv;
+    d[1] = (c01 * r[0] + c11 * r[1] + c21 * r[2]) * inv;
+    d[2] = (c02 * r[0] + c12 * r[1] + c22 * r[2]) * inv;
+    return true;
+  }
+}
+
+// Newton for t = Phi_K^{-1}(y); `t` holds the start on entry.  Returns true
+// on convergence; adds the iterations to `iters`.
+template <int D>
+__device__ __forceinline__ bool newton(const CellGeom<D>& g, const double y[D], double t[D], int& iters) {
+  double y0[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) y0[a] = y[a] - g.x0[a];
+  for (int it = 0; it < kNewtonMaxIt; ++it) {
+    ++iters;
+    double phi[D], J[D][D], r[D], d[D];
+    map_and_jacobian<D>(g, t, phi, J);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[a] = y0[a] - phi[a];
+    if (!solve<D>(J, r, d)) return false;
+    double dm = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      t[a] += d[a];
+      dm = fmax(dm, fabs(d[a]));
+    }
+    if (!isfinite(dm)) return false;
+    if (dm <= kNewtonTol) return true;
+  }
+  return false;
+}
+
+template <int D>
+__device__ __forceinline__ bool in_ref_cell(const double t[D]) {
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) in = in && (t[a] >= -kInsideEps) && (t[a] <= 1.0 + kInsideEps);
+  return in;
+}
+
+// --------------------------------------------------------- Q2 velocity --
+// u_h(x) = sum_{a,b,c} U[node(K; a,b,c)] l_a(t0) l_b(t1) l_c(t2), with the 1D
+// quadratic Lagrange basis on {0, 1/2, 1}:
+//   l0 = (1-t)(1-2t), l1 = 4t(1-t), l2 = t(2t-1)
+// contracted one axis at a time (sum factorisation).
+
+template <typename T>
+__device__ __forceinline__ void lagrange2(T t, T l[3]) {
+  const T one = (T)1, two = (T)2, four = (T)4;
+  l[0] = (one - t) * (one - two * t);
+  l[1] = four * t * (one - t);
+  l[2] = t * (two * t - one);
+}
+
+template <int D, typename T>
+__device__ __forceinline__ void q2_eval(const MeshView& m, const T* __restrict__ U, uint32_t K, const double tin[D],
+                                        double u[D]) {
+  int c[3];
+  cell_ijk<D>(m, K, c);
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  T l[D][3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) lagrange2<T>((T)tin[a], l[a]);
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) {
+    const T* Uc = U + comp * m.nnodes + base;
+    T s = (T)0;
+#pragma unroll
+    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
+      T sc = (T)0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T* row = Uc + b * sy + (D == 3 ? cz * sz : 0);
+        T sb = l[0][0] * __ldg(row) + l[0][1] * __ldg(row + 1) + l[0][2] * __ldg(row + 2);
+        sc += l[1][b] * sb;
+      }
+      if (D == 3)
+        s += l[2][cz] * sc;
+      else
+        s = sc;
+    }
+    u[comp] = (double)s;
+  }
+}
+
+}  // namespace pic
+
+namespace pic {
+// ---------------------------------------------- host-side internal calls --
+// Rebuild the sorted store from the cells found by the last locate
+// (cell_new, counts already filled).  Defined in rebin.cu.
+pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s);
+// Exclusive scan of n u32 values into out[0..n] (out[n] = total); total also
+// written to *total_dev when non-null.  Defined in rebin.cu.
+pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,
+                    uint32_t* cursor_init, cudaStream_t s);
+uint32_t scan_block_count(uint32_t n);
+int num_sms();
+}  // namespace pic

@@ -1,0 +1,273 @@
+// rebin.cu -- rebuilding the particle store sorted by (cell, id) after the
+// particles have been located (Sec. 2.1: the store keeps particles sorted
+// by containing cell; Sec. 2.4: movers are collected and re-inserted in one
+// batch, and particles in no cell are discarded).
+//
+// A counting sort by new cell followed by a rank sort by id inside each
+// cell's segment:
+//   counts[K]   particles whose new cell is K (filled by the locate kernel)
+//   scan        cell_off = exclusive prefix sum of counts; cursor = cell_off
+//   scatter     (id, old slot) of each particle to a free slot of its cell
+//   rank        warp per cell: slot of each particle = its rank by id
+//   gather      every field copied from the old slot to the new slot
+// The result is a function of the particle set alone (no dependence on the
+// order the atomics of the scatter were served in).
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+
+uint32_t scan_block_count(uint32_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
+    uint32_t si = warp_incl_scan(s);
+    if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = si - s;
+    if (lane == 31) *total = si;
+  }
+  __syncthreads();
+  const uint32_t r = warp_sums[w] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                                                   uint32_t* __restrict__ block_sums) {
+  const uint32_t base = blockIdx.x * kScanTile;
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const uint32_t i = base + q * kScanThreads + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  s = __reduce_add_sync(0xffffffffu, s);
+  __shared__ uint32_t ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t t = ws[threadIdx.x];
+    t = __reduce_add_sync(0xffffffffu, t);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
+  }
+}
+
+// Single block: exclusive scan of the block sums in place.
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __restrict__ sums, uint32_t nb) {
+  __shared__ uint32_t carry_s;
+  __shared__ uint32_t tot;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nb; base += kScanThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < nb ? sums[i] : 0u;
+    const uint32_t ex = block_excl_scan(v, &tot);
+    const uint32_t carry = carry_s;
+    if (i < nb) sums[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+  }
+}
+
+// Each block scans its tile, adds its block offset, writes out[] (and the
+// cursor copy); the last element writes out[n] and the total.
+__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                                                  const uint32_t* __restrict__ block_sums,
+                                                                  uint32_t* __restrict__ out,
+                                                                  uint32_t* __restrict__ cursor,
+                                                                  uint32_t* __restrict__ total_dev) {
+  __shared__ uint32_t tot;
+  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = (base + q < n) ? in[base + q] : 0u;
+    s += v[q];
+  }
+  uint32_t ex = block_excl_scan(s, &tot) + block_sums[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const uint32_t i = base + q;
+    if (i < n) {
+      out[i] = ex;
+      if (cursor) cursor[i] = ex;
+    }
+    ex += v[q];
+    if (i + 1 == n) {
+      out[n] = ex;
+      if (total_dev) *total_dev = ex;
+    }
+  }
+}
+
+pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,
+                    uint32_t* cursor_init, cudaStream_t s) {
+  const uint32_t nb = scan_block_count(n);
+  if (n == 0) return PIC_OK;
+  scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums);
+  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb);
+  scan_apply_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums, out, cursor_init, total_dev);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+// (id, old slot) of every located particle into a free slot of its new cell.
+__global__ void __launch_bounds__(256) scatter_keys_kernel(const uint32_t* __restrict__ cell_new,
+                                                           const uint64_t* __restrict__ id, uint32_t* __restrict__ cursor,
+                                                           uint64_t* __restrict__ key_id, uint32_t* __restrict__ key_src,
+                                                           uint32_t C, size_t cap, DevCounters* __restrict__ ctr) {
+  const uint32_t n = ctr->n_alive;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t K = cell_new[i];
+    if (K == PIC_LOST) continue;
+    if (K >= C) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    const uint32_t slot = atomicAdd(cursor + K, 1u);
+    if (slot >= cap) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    key_id[slot] = id[i];
+    key_src[slot] = i;
+  }
+}
+
+// Warp per cell: the new slot of each element of the cell's segment is the
+// segment start plus the number of elements with a smaller id (ids are
+// unique).  Also publishes the new particle count.
+__global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
+                                                         const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,
+                                                         uint32_t* __restrict__ cell_out, uint32_t C, size_t cap,
+                                                         DevCounters* __restrict__ ctr) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_alive = ctr->n_next;
+  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
+    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
+    if (end > cap || beg > end) {
+      if (lane == 0) latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    const uint32_t n = end - beg;
+    for (uint32_t e0 = 0; e0 < n; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const uint64_t my = e < n ? key_id[beg + e] : ~0ull;
+      uint32_t rank = 0;
+      for (uint32_t f0 = 0; f0 < n; f0 += 32) {
+        const uint64_t other = (f0 + lane < n) ? key_id[beg + f0 + lane] : ~0ull;
+        const uint32_t lim = (n - f0) < 32u ? (n - f0) : 32u;
+        for (uint32_t q = 0; q < lim; ++q) {
+          const uint64_t o = __shfl_sync(0xffffffffu, other, q);
+          rank += (o < my) ? 1u : 0u;
+        }
+      }
+      if (e < n) {
+        perm[beg + rank] = key_src[beg + e];
+        cell_out[beg + rank] = K;
+      }
+    }
+  }
+}
+
+// Copy every field from the old slot perm[j] to the new slot j.
+__global__ void __launch_bounds__(256) gather_kernel(StoreView src, StoreView dst, const uint32_t* __restrict__ perm, int dim,
+                                                     DevCounters* __restrict__ ctr) {
+  const uint32_t n = ctr->n_alive;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t s = perm[j];
+    if (s >= src.cap) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    for (int a = 0; a < dim; ++a) {
+      dst.x[a * dst.cap + j] = src.x[a * src.cap + s];
+      dst.xhat[a * dst.cap + j] = src.xhat[a * src.cap + s];
+    }
+    dst.id[j] = src.id[s];
+    for (int q = 0; q < src.n_props; ++q) dst.props[q * dst.cap + j] = src.props[q * src.cap + s];
+  }
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+  }
+  return sms;
+}
+
+static int grid_cap(size_t n, int block, int per_sm) {
+  size_t want = (n + block - 1) / block;
+  size_t cap = (size_t)num_sms() * per_sm;
+  size_t g = want < cap ? want : cap;
+  return (int)(g ? g : 1);
+}
+
+pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
+  pic_status r = scan_u32(p->counts, p->cell_off, p->C, p->block_sums, &p->ctr->n_next, p->cursor, s);
+  if (r != PIC_OK) return r;
+  const StoreView a = store_view(p, p->cur), b = store_view(p, 1 - p->cur);
+  scatter_keys_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(p->cell_new, a.id, p->cursor, p->key_id, p->key_src,
+                                                                     p->C, p->capacity, p->ctr);
+  rank_by_id_kernel<<<grid_cap((size_t)p->C * 32, 256, 16), 256, 0, s>>>(p->cell_off, p->key_id, p->key_src, p->perm,
+                                                                        b.cell, p->C, p->capacity, p->ctr);
+  gather_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(a, b, p->perm, p->dim, p->ctr);
+  PIC_CUDA(cudaGetLastError());
+  p->cur = 1 - p->cur;
+  return PIC_OK;
+}
+
+// cell_new = cell, counts = histogram of cell (the identity relocation).
+__global__ void identity_cells_kernel(const uint32_t* __restrict__ cell, uint32_t* __restrict__ cell_new,
+                                      uint32_t* __restrict__ counts, uint32_t C, DevCounters* __restrict__ ctr) {
+  const uint32_t n = ctr->n_alive;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t K = cell[i];
+    if (K >= C) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      K = PIC_LOST;
+    } else {
+      atomicAdd(counts + K, 1u);
+    }
+    cell_new[i] = K;
+  }
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" pic_status pic_rebin(pic_particles parts, void* stream) {
+  if (!parts) return (set_error("pic_rebin: null handle"), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
+  identity_cells_kernel<<<grid_cap(parts->capacity, 256, 16), 256, 0, st>>>(parts->cell[parts->cur], parts->cell_new,
+                                                                          parts->counts, parts->C, parts->ctr);
+  PIC_CUDA(cudaGetLastError());
+  return rebin_from_counts(parts, st);
+}

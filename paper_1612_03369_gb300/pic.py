@@ -1,0 +1,292 @@
+"""Thin ctypes binding of libpic.so (include/pic.h).
+
+Every function has the name of its C entry point and only marshals
+arguments: torch tensors supply device memory (data_ptr) and the current
+CUDA stream; every step of the particle path runs in the library's kernels.
+There is no CPU fallback: if libpic.so is missing or cannot be loaded, the
+import of this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CAPACITY, PIC_ERR_CUDA, PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, \
+    PIC_ERR_STATE = range(8)
+PIC_EULER, PIC_RK2, PIC_RK4 = 1, 2, 4
+PIC_FP64, PIC_FP32_BASIS = 0, 1
+PIC_AVG_ARITHMETIC = 0
+PIC_STATUS_NEWTON_NONCONV, PIC_STATUS_CAPACITY, PIC_STATUS_GLOBAL_SEARCH, PIC_STATUS_BOUNDS = 1, 2, 4, 8
+LOST = 0xFFFFFFFF
+
+# name -> (restype, argtypes)
+_P, _I, _U32, _U64, _SZ, _F64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64, C.c_size_t, C.c_double
+SIGNATURES = {
+    "pic_create_mesh": (_I, [_I, _P, _P, _I, _P, _P]),
+    "pic_destroy_mesh": (_I, [_P]),
+    "pic_set_velocity_dofs": (_I, [_P, _P, _P, _P]),
+    "pic_seed_particles": (_I, [_P, _P, _U32, _U64, _U64, _I, _SZ, _P, _P]),
+    "pic_destroy_particles": (_I, [_P]),
+    "pic_set_properties": (_I, [_P, _I, _P, _P]),
+    "pic_advect": (_I, [_P, _P, _F64, _I, _I, _I, _P]),
+    "pic_locate": (_I, [_P, _P, _P]),
+    "pic_rebin": (_I, [_P, _P]),
+    "pic_locate_points": (_I, [_P, _SZ, _P, _P, _P, _P, _P]),
+    "pic_interpolate_to_cells": (_I, [_P, _P, _I, _I, _P, _P, _F64, _P]),
+    "pic_get_state": (_I, [_P, _P, _P, _P]),
+    "pic_get_stats": (_I, [_P, _P, _P, _P, _P]),
+    "pic_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "pic_cell_offsets": (_I, [_P, _P, _P]),
+    "pic_last_error": (C.c_char_p, []),
+    "pic_version": (C.c_char_p, []),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError("libpic.so not built at %s (run __graft_entry__.build())" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+class PicError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.pic_last_error().decode(errors="replace")
+        super().__init__("%s failed with status %d: %s" % (where, status, msg))
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != PIC_OK:
+        raise PicError(status, where)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+# ------------------------------------------------------------- raw calls --
+
+
+def pic_create_mesh(dim: int, n_cells, vertices, stream=None) -> int:
+    """vertices: torch tensor [dim][nverts] float64 (device or host)."""
+    nc = (C.c_int * dim)(*[int(v) for v in n_cells])
+    out = C.c_void_p()
+    on_dev = 1 if vertices.is_cuda else 0
+    _check(_lib.pic_create_mesh(dim, nc, _ptr(vertices), on_dev, _stream(stream), C.byref(out)), "pic_create_mesh")
+    return out.value
+
+
+def pic_destroy_mesh(h: int):
+    _check(_lib.pic_destroy_mesh(h), "pic_destroy_mesh")
+
+
+def pic_set_velocity_dofs(h: int, U, stream=None):
+    _check(_lib.pic_set_velocity_dofs(h, _ptr(U), None, _stream(stream)), "pic_set_velocity_dofs")
+
+
+def pic_seed_particles(mesh: int, per_cell=None, uniform_count: int = 0, seed: int = 0, first_id: int = 0,
+                       n_props: int = 0, capacity: int = 0, stream=None) -> int:
+    out = C.c_void_p()
+    _check(_lib.pic_seed_particles(mesh, _ptr(per_cell), int(uniform_count), seed & (2**64 - 1), first_id, int(n_props),
+                                   int(capacity), _stream(stream), C.byref(out)), "pic_seed_particles")
+    return out.value
+
+
+def pic_destroy_particles(h: int):
+    _check(_lib.pic_destroy_particles(h), "pic_destroy_particles")
+
+
+def pic_set_properties(h: int, prop: int, values, stream=None):
+    _check(_lib.pic_set_properties(h, int(prop), _ptr(values), _stream(stream)), "pic_set_properties")
+
+
+def pic_advect(parts: int, mesh: int, dt: float, integrator: int, precision: int, n_steps: int, stream=None):
+    _check(_lib.pic_advect(parts, mesh, float(dt), int(integrator), int(precision), int(n_steps), _stream(stream)),
+           "pic_advect")
+
+
+def pic_locate(parts: int, mesh: int, stream=None):
+    _check(_lib.pic_locate(parts, mesh, _stream(stream)), "pic_locate")
+
+
+def pic_rebin(parts: int, stream=None):
+    _check(_lib.pic_rebin(parts, _stream(stream)), "pic_rebin")
+
+
+def pic_locate_points(mesh: int, x, hint=None, cell_out=None, xhat_out=None, stream=None):
+    """x: device [dim][n] float64.  Returns (cell_out u32-as-int32 tensor,
+    xhat_out [dim][n])."""
+    import torch
+
+    dim, n = x.shape
+    if cell_out is None:
+        cell_out = torch.empty(n, dtype=torch.int32, device=x.device)
+    if xhat_out is None:
+        xhat_out = torch.empty((dim, n), dtype=torch.float64, device=x.device)
+    _check(_lib.pic_locate_points(mesh, n, _ptr(x), _ptr(hint), _ptr(cell_out), _ptr(xhat_out), _stream(stream)),
+           "pic_locate_points")
+    return cell_out, xhat_out
+
+
+def pic_interpolate_to_cells(parts: int, mesh: int, prop: int, avg, count=None, empty_fill: float = 0.0,
+                             kind: int = PIC_AVG_ARITHMETIC, stream=None):
+    _check(_lib.pic_interpolate_to_cells(parts, mesh, int(prop), int(kind), _ptr(avg), _ptr(count), float(empty_fill),
+                                         _stream(stream)), "pic_interpolate_to_cells")
+
+
+def pic_get_state(parts: int):
+    na, nl, st = C.c_size_t(), C.c_size_t(), C.c_uint32()
+    _check(_lib.pic_get_state(parts, C.byref(na), C.byref(nl), C.byref(st)), "pic_get_state")
+    return int(na.value), int(nl.value), int(st.value)
+
+
+def pic_get_stats(parts: int):
+    v = [C.c_uint64() for _ in range(4)]
+    _check(_lib.pic_get_stats(parts, *[C.byref(a) for a in v]), "pic_get_stats")
+    return dict(zip(("particle_steps", "walks", "global_searches", "newton_iterations"), [int(a.value) for a in v]))
+
+
+def pic_export(parts: int, x=None, xhat=None, id=None, cell=None, props=None, stream=None):
+    _check(_lib.pic_export(parts, _ptr(x), _ptr(xhat), _ptr(id), _ptr(cell), _ptr(props), _stream(stream)),
+           "pic_export")
+
+
+def pic_cell_offsets(parts: int, off, stream=None):
+    _check(_lib.pic_cell_offsets(parts, _ptr(off), _stream(stream)), "pic_cell_offsets")
+
+
+def pic_version() -> str:
+    return _lib.pic_version().decode()
+
+
+# --------------------------------------------------------- conveniences --
+
+
+class Mesh:
+    """Owning wrapper of a pic_mesh handle."""
+
+    def __init__(self, n_cells, vertices, U=None, device="cuda", stream=None):
+        import torch
+
+        self.dim = len(n_cells)
+        self.n = tuple(int(v) for v in n_cells)
+        self.ncells = int(np.prod(self.n))
+        X = torch.as_tensor(np.ascontiguousarray(vertices, dtype=np.float64), device=device)
+        self.h = pic_create_mesh(self.dim, self.n, X, stream)
+        if U is not None:
+            self.set_velocity(U, stream)
+
+    def set_velocity(self, U, stream=None):
+        import torch
+
+        self.U = torch.as_tensor(np.ascontiguousarray(U, dtype=np.float64), device="cuda")
+        pic_set_velocity_dofs(self.h, self.U, stream)
+
+    def locate_points(self, x, hint=None, stream=None):
+        return pic_locate_points(self.h, x, hint, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_destroy_mesh(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Particles:
+    """Owning wrapper of a pic_particles handle."""
+
+    def __init__(self, mesh: Mesh, per_cell=None, uniform_count: int = 0, seed: int = 0, first_id: int = 0,
+                 n_props: int = 0, capacity: int = 0, stream=None):
+        import torch
+
+        self.mesh = mesh
+        self.dim = mesh.dim
+        self.n_props = n_props
+        pc = None
+        if per_cell is not None:
+            pc = torch.as_tensor(np.ascontiguousarray(per_cell, dtype=np.uint32).view(np.int32), device="cuda")
+        self.h = pic_seed_particles(mesh.h, pc, uniform_count, seed, first_id, n_props, capacity, stream)
+
+    def advect(self, dt, integrator=PIC_RK4, n_steps=1, precision=PIC_FP64, stream=None):
+        pic_advect(self.h, self.mesh.h, dt, integrator, precision, n_steps, stream)
+
+    def locate(self, stream=None):
+        pic_locate(self.h, self.mesh.h, stream)
+
+    def rebin(self, stream=None):
+        pic_rebin(self.h, stream)
+
+    def set_property(self, prop, values, stream=None):
+        pic_set_properties(self.h, prop, values, stream)
+
+    def state(self):
+        return pic_get_state(self.h)
+
+    def stats(self):
+        return pic_get_stats(self.h)
+
+    def average(self, prop, empty_fill=0.0, stream=None):
+        import torch
+
+        avg = torch.empty(self.mesh.ncells, dtype=torch.float64, device="cuda")
+        cnt = torch.empty(self.mesh.ncells, dtype=torch.int32, device="cuda")
+        pic_interpolate_to_cells(self.h, self.mesh.h, prop, avg, cnt, empty_fill, stream=stream)
+        return avg, cnt
+
+    def export(self, stream=None):
+        """Store contents as torch device tensors in (cell, id) order."""
+        import torch
+
+        n, _, _ = self.state()
+        x = torch.empty((self.dim, n), dtype=torch.float64, device="cuda")
+        xh = torch.empty((self.dim, n), dtype=torch.float64, device="cuda")
+        ids = torch.empty(n, dtype=torch.int64, device="cuda")
+        cell = torch.empty(n, dtype=torch.int32, device="cuda")
+        props = torch.empty((max(self.n_props, 1), n), dtype=torch.float64, device="cuda")
+        pic_export(self.h, x, xh, ids, cell, props if self.n_props else None, stream)
+        return {"x": x, "xhat": xh, "id": ids, "cell": cell, "props": props[: self.n_props]}
+
+    def cell_offsets(self, stream=None):
+        import torch
+
+        off = torch.empty(self.mesh.ncells + 1, dtype=torch.int32, device="cuda")
+        pic_cell_offsets(self.h, off, stream)
+        return off
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_destroy_particles(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
