@@ -1,0 +1,351 @@
+"""Benchmark of the particle hot path: RK4 particle-steps/s for
+advect + locate + rebin on a 3D Q2 mesh, with its HBM roofline fraction.
+
+Workload (default): 3D unit cube, 64^3 hexes with interior vertices jittered
+by up to 0.1 h, Q2 velocity = curl of 8 random-phase sinusoidal vector
+potentials (zero wall-normal flow), 20 particles per cell (5,242,880), three
+FP64 properties, RK4 at CFL 0.5.  One benchmark step = one time step of every
+particle (advect with located stages, final locate, rebin into the
+(cell, id)-sorted store).  The particle state (~440 MB) is larger than L2,
+so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config c2|c1|c3]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload
+(independent problems, no data-path collective: weak scaling); the time is
+the maximum over ranks.  --impl reference times the CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1612_03369_gb300 import workloads as W  # noqa: E402
+
+# Algorithmic bytes per particle-step of the whole step and of the advect
+# kernel (FP64 form, 3D, P properties, u64 ids): each particle's state is
+# read and written once, cell data (8 unique Q2 nodes x 3 x 8 B + one vertex
+# x 3 x 8 B + a u32 offset) amortised over the particles per cell.
+def step_bytes(dim: int, n_props: int, ppc: float, xhat_bytes: int = 8) -> float:
+    state = dim * 8 + dim * xhat_bytes + 8 + n_props * 8
+    cell_data = ((2 ** dim) * dim * 8 + dim * 8 + 4) / ppc
+    return 2 * state + 8 + cell_data
+
+
+def advect_bytes(dim: int, ppc: float, xhat_bytes: int = 8) -> float:
+    # reads x, x-hat, cell; writes x, x-hat, new cell; cell data amortised
+    return 2 * (dim * 8 + dim * xhat_bytes + 4) + ((2 ** dim) * dim * 8 + dim * 8) / ppc
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name: str):
+    if name == "c1":
+        return W.c1()
+    if name == "c3":
+        return W.c3()
+    return W.c2()
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1612_03369_gb300 import pic as P
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = workload(args.config)
+    precision = P.PIC_FP32_BASIS if args.config == "c3" else P.PIC_FP64
+    mesh = P.Mesh(wl.n, wl.X, wl.U)
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
+    st = parts.export()
+    for q in range(min(wl.n_props, wl.dim)):
+        parts.set_property(q, st["x"][q].contiguous())
+    del st
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+
+    # warm-up
+    parts.advect(wl.dt, wl.integrator, args.warmup, precision)
+    torch.cuda.synchronize()
+    n0, _, _ = parts.state()
+    stats0 = parts.stats()
+    launches0 = P.pic_kernel_launches()
+    P.pic_timing_enable(parts.h, True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    parts.advect(wl.dt, wl.integrator, args.steps, precision)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    P.pic_timing_enable(parts.h, False)
+    launches = P.pic_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    adv_ms, reb_ms, nsteps = P.pic_timing_read(parts.h)
+    stats1 = parts.stats()
+    psteps = stats1["particle_steps"] - stats0["particle_steps"]
+    n1, nlost, status = parts.state()
+
+    # ---- end to end through the C ABI with host buffers: every step copies
+    # the step's velocity DOFs host->device (a flow solver hands over a new
+    # field each step), advances one step, averages the properties per cell
+    # and reads the averages back to the host.
+    Uh = torch.from_numpy(np.ascontiguousarray(wl.U)).pin_memory()
+    avg_d = torch.empty((max(wl.n_props, 1), wl.ncells), dtype=torch.float64, device=dev)
+    cnt_d = torch.empty(wl.ncells, dtype=torch.int32, device=dev)
+    avg_h = torch.empty((max(wl.n_props, 1), wl.ncells), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 20))
+    stats_e0 = parts.stats()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.pic_set_velocity_dofs(mesh.h, Uh)  # host pointer: H2D copy inside the library call
+        P.pic_advect(parts.h, mesh.h, wl.dt, wl.integrator, precision, 1)
+        for q in range(wl.n_props):
+            P.pic_interpolate_to_cells(parts.h, mesh.h, q, avg_d[q], cnt_d if q == 0 else None)
+        avg_h.copy_(avg_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_psteps = parts.stats()["particle_steps"] - stats_e0["particle_steps"]
+
+    tmax = ms
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax, e2e_s = float(t[0]), float(t[1])
+        ps = torch.tensor([psteps, e2e_psteps], device=dev, dtype=torch.float64)
+        dist.all_reduce(ps)
+        psteps_all, e2e_all = float(ps[0]), float(ps[1])
+    else:
+        psteps_all, e2e_all = float(psteps), float(e2e_psteps)
+
+    hbm, peak_kind = load_peaks()
+    ppc = float(wl.ppc)
+    value = psteps_all / (tmax / 1e3)
+    adv_bytes = advect_bytes(wl.dim, ppc)
+    adv_avg_ms = adv_ms / max(nsteps, 1)
+    per_launch_particles = psteps / max(nsteps, 1)
+    achieved = adv_bytes * per_launch_particles / (adv_avg_ms / 1e3) / 1e9
+    sbytes = step_bytes(wl.dim, wl.n_props, ppc)
+    res = {
+        "metric": "RK4 particle-steps/s (advect+locate+rebin), 3D Q2 mesh; % of HBM roofline",
+        "value": value,
+        "unit": "particle-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if precision == 0 else "f64+f32basis",
+        "data": "synthetic (seeded jittered mesh, curl-of-potential Q2 field, local-coordinate seeding)",
+        "config": {"workload": wl.name, "mesh": "x".join(str(v) for v in wl.n), "particles": wl.n_particles,
+                   "particles_per_cell": wl.ppc, "n_props": wl.n_props, "integrator": "RK4" if wl.integrator == 4 else
+                   ("RK2" if wl.integrator == 2 else "Euler"), "dt": wl.dt, "cfl": 0.5,
+                   "l2": "state ~%.0f MB > 129 MB L2, no flush" % (wl.n_particles * sbytes / 2 / 1e6),
+                   "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
+        "step_fraction_of_hbm_roofline": (value * sbytes / 1e9) / hbm,
+        "step_algorithmic_bytes_per_particle_step": sbytes,
+        "roofline": {"kernel": "advect_kernel<3,RK4>", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "algorithmic_bytes_per_particle": adv_bytes,
+                     "avg_launch_ms": adv_avg_ms, "rebin_ms_per_step": reb_ms / max(nsteps, 1),
+                     "note": "ALU-bound in fact: FP64 pipe; see fp64 section"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": e2e_all / e2e_s, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": int(wl.U.nbytes),
+                "d2h_bytes_per_step": int(wl.n_props * wl.ncells * 8), "steps": e2e_steps,
+                "what": "per step: velocity DOFs H2D (pinned) + pic_advect 1 step + per-cell averages of all "
+                        "properties + D2H of the averages"},
+        "state": {"alive": n1, "lost_total": nlost, "status_word": status,
+                  "walks": stats1["walks"] - stats0["walks"],
+                  "global_searches": stats1["global_searches"] - stats0["global_searches"],
+                  "fp64_fallback_particle_steps": stats1["fallback64"] - stats0["fallback64"],
+                  "fp64_walk_particle_steps": stats1["walk64"] - stats0["walk64"],
+                  "newton_iterations_per_particle_step": (stats1["newton_iterations"] - stats0["newton_iterations"])
+                  / max(psteps, 1)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
+    parts.close()
+    mesh.close()
+    return res
+
+
+def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
+    """The oracle as it stands, single thread, on a bounded random sample of
+    the workload's particles advanced one time step at a time."""
+    import oracle as O
+
+    om = O.Mesh(wl.n, wl.X, wl.U)
+    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
+    rng = np.random.default_rng(0)
+    n = sample or 2000
+    pick = np.sort(rng.choice(op.n, min(n, op.n), replace=False))
+    sub = op.subset(pick)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        before = sub.n
+        sub = O.advect(om, sub, wl.dt, wl.integrator, 1)
+        done += before
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d random particles of %s advanced one step at a time for %.1f s (%d particle-steps)"
+                      % (len(pick), wl.name, el, done)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = workload(args.config)
+    import oracle as O
+
+    om = O.Mesh(wl.n, wl.X, wl.U)
+    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
+    rng = np.random.default_rng(1)
+    sample = 300
+    pick = np.sort(rng.choice(op.n, sample, replace=False))
+    sub = op.subset(pick)
+    for _ in range(args.warmup):
+        sub = O.advect(om, sub, wl.dt, wl.integrator, 1)
+    done = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        before = sub.n
+        sub = O.advect(om, sub, wl.dt, wl.integrator, 1)
+        done += before
+    el = time.perf_counter() - t0
+    value = done / el
+    return {
+        "impl": "reference",
+        "metric": "RK4 particle-steps/s (advect+locate+rebin), 3D Q2 mesh; % of HBM roofline",
+        "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": wl.name},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d random particles of %s, one time step per benchmark step" % (sample, wl.name)},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,14 @@ pic_status pic_get_state(pic_particles parts, size_t *n_alive, size_t *n_lost, u
 pic_status pic_get_stats(pic_particles parts, uint64_t *particle_steps, uint64_t *walks, uint64_t *global_searches,
                          uint64_t *newton_iterations);
 
+/* All device counters since seeding, in this order (up to n_values of them):
+ * particle-steps, neighbour walks, all-cells searches, Newton iterations,
+ * particles lost, particle-steps where some cell needed the FP64 Newton
+ * fallback, particle-steps whose walk went past the predicted neighbour.
+ * Synchronises. */
+#define PIC_N_COUNTERS 7
+pic_status pic_get_counters(pic_particles parts, uint64_t *values, int n_values);
+
 /* Copy the store out in (cell, id) order.  Synchronises `stream` first to
  * read the particle count.  Any pointer may be NULL; host or device memory.
  *   x, xhat [dim][N] FP64;  id [N] u64;  cell [N] u32;  props [n_props][N] FP64 */
@@ -183,6 +191,17 @@ pic_status pic_export(pic_particles parts, double *x, double *xhat, uint64_t *id
 /* Cell offsets of the sorted store: off[K]..off[K+1] are the particles of
  * cell K.  off is [n_cells + 1] u32, device or host. */
 pic_status pic_cell_offsets(pic_particles parts, uint32_t *off, void *stream);
+
+/* Instrumentation (no counterpart in the paper).
+ * pic_timing_enable: while on, pic_advect records CUDA events on its stream
+ * around the advect kernel and around the rebin of every step.
+ * pic_timing_read synchronises, returns the summed milliseconds and the
+ * number of timed steps since the last read, and resets the sums. */
+pic_status pic_timing_enable(pic_particles parts, int on);
+pic_status pic_timing_read(pic_particles parts, double *advect_ms, double *rebin_ms, uint64_t *steps);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t pic_kernel_launches(void);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *pic_last_error(void);

@@ -7,6 +7,7 @@
 // loads of a warp hit the same lines in L1.
 #include <cmath>
 
+#include "fastpath.cuh"
 #include "locate.cuh"
 #include "pic_internal.cuh"
 
@@ -22,6 +23,8 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
   const unsigned w = __reduce_add_sync(mask, walks);
   const unsigned g = __reduce_add_sync(mask, globals);
   const unsigned f = __reduce_or_sync(mask, flags);
+  const unsigned fb = __reduce_add_sync(mask, (flags & kFlagFallback64) ? 1u : 0u);
+  const unsigned w64 = __reduce_add_sync(mask, (flags & kFlagWalk64) ? 1u : 0u);
   const int leader = __ffs(mask) - 1;
   if ((int)(threadIdx.x & 31) == leader) {
     if (s) atomicAdd(&ctr->particle_steps, (unsigned long long)s);
@@ -29,6 +32,8 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
     if (l) atomicAdd(&ctr->lost_total, (unsigned long long)l);
     if (w) atomicAdd(&ctr->walks, (unsigned long long)w);
     if (g) atomicAdd(&ctr->global_searches, (unsigned long long)g);
+    if (fb) atomicAdd(&ctr->fallback64, (unsigned long long)fb);
+    if (w64) atomicAdd(&ctr->walk64, (unsigned long long)w64);
     unsigned st = 0;
     if (f & kFlagNonConv) st |= PIC_STATUS_NEWTON_NONCONV;
     if (f & kFlagGlobal) st |= PIC_STATUS_GLOBAL_SEARCH;
@@ -37,13 +42,14 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
   }
 }
 
-// Velocity at reference coordinates t of cell K, FP64 or FP32 basis.
+// Velocity at double-float reference coordinates t of cell K: the Q2
+// contraction in double-float, or in FP32 for the precision form.
 template <int D, bool F32B>
-__device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const double t[D], double u[D]) {
-  if (F32B)
-    q2_eval<D, float>(m, m.U32, K, t, u);
+__device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
+  if constexpr (F32B)
+    q2_eval_f32<D>(m, K, t, u);
   else
-    q2_eval<D, double>(m, m.U, K, t, u);
+    q2_eval_df<D>(m, K, t, u);
 }
 
 // One time step for every particle of the store (in place), recording the
@@ -55,106 +61,114 @@ __device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const do
 // with k1 = dt u(x) taken at the stored (cell, x-hat), and every later stage
 // point located before u_h is evaluated there (Sec. 2.4: every sub-step is
 // followed by a determination of the containing cell).
+//
+// The stages run as one loop over evaluation points p = 0..S (S = number of
+// stages): point 0 is the stored position, points 1..S-1 the stage points,
+// point S the new position.  Each point p > 0 is located, each p < S gets a
+// velocity evaluation, so the kernel holds one copy of the locate and of
+// the Q2 contraction (instruction-cache footprint).
+//
+// Arithmetic: the stored position x is FP64; it is split once into a
+// double-float, and the stages, the increments k_s and the stage points are
+// double-floats on the FP32 pipe.  The new position is x + D in FP64, where
+// D is the double-float increment; the new position is located from the
+// double-float x + D (the two differ by ~1e-16).
+template <int RK>
+struct Tableau;
+template <>
+struct Tableau<1> {  // forward Euler
+  static constexpr int S = 1;
+  __device__ static float c(int) { return 0.f; }
+  __device__ static float w(int) { return 1.f; }
+  __device__ static bool divide6() { return false; }
+};
+template <>
+struct Tableau<2> {  // midpoint rule
+  static constexpr int S = 2;
+  __device__ static float c(int p) { return 0.5f; }  // y_1 = x + k_0 / 2
+  __device__ static float w(int p) { return p == 0 ? 0.f : 1.f; }
+  __device__ static bool divide6() { return false; }
+};
+template <>
+struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x + k2
+  static constexpr int S = 4;
+  __device__ static float c(int p) { return p == 3 ? 1.f : 0.5f; }
+  __device__ static float w(int p) { return (p == 0 || p == 3) ? 1.f : 2.f; }  // then / 6
+  __device__ static bool divide6() { return true; }
+};
+
+// Resident blocks per SM requested from the register allocator (tuning knob,
+// swept at build time with -DPIC_ADVECT_MIN_BLOCKS=n).
+#ifndef PIC_ADVECT_MIN_BLOCKS
+#define PIC_ADVECT_MIN_BLOCKS 5
+#endif
+
 template <int D, int RK, bool F32B>
-__global__ void __launch_bounds__(128) advect_kernel(MeshView m, StoreView s, double dt, uint32_t* __restrict__ cell_new,
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(MeshView m, StoreView s, df dt, uint32_t* __restrict__ cell_new,
                                                      uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
+  using TB = Tableau<RK>;
   const uint32_t n = ctr->n_alive;
   const uint32_t stride = gridDim.x * blockDim.x;
+  const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);  // 1/6 = hi + lo
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const uint32_t i = base + threadIdx.x;
     int iters = 0;
-    unsigned flags = 0, lost = 0, walks = 0, globals = 0, steps = 0;
+    unsigned flags = 0, lost = 0, steps = 0;
     if (i < n) {
       steps = 1;
-      const uint32_t K = s.cell[i];
+      uint32_t Ks = s.cell[i];
       uint32_t Kn = PIC_LOST;
-      double x[D], t[D], xn[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        x[a] = s.x[a * s.cap + i];
-        t[a] = s.xhat[a * s.cap + i];
-      }
-      if (K >= m.C) {
+      if (Ks >= m.C) {
         flags |= kFlagBounds;
       } else {
-        double u[D], k[D], acc[D], y[D], ts[D];
-        uint32_t Ks = K;
-        unsigned f0 = 0;
-        velocity<D, F32B>(m, K, t, u);
+        double x[D];
+        df xd[D], ts[D], k[D], acc[D], y[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) k[a] = dt * u[a];
+        for (int a = 0; a < D; ++a) {
+          x[a] = s.x[a * s.cap + i];
+          const float2 v = s.xhat[a * s.cap + i];
+          ts[a] = df_make(v.x, v.y);
+          xd[a] = df_from_double(x[a]);
+          acc[a] = df_make(0.f, 0.f);
+        }
         bool ok = true;
-        if (RK == 1) {
-#pragma unroll
-          for (int a = 0; a < D; ++a) xn[a] = x[a] + k[a];
-#pragma unroll
-          for (int a = 0; a < D; ++a) ts[a] = t[a];
-        } else if (RK == 2) {
-#pragma unroll
-          for (int a = 0; a < D; ++a) y[a] = x[a] + 0.5 * k[a];
-          Ks = locate<D>(m, y, K, t, ts, iters, f0);
-          ok = Ks != PIC_LOST;
-          if (ok) {
-            velocity<D, F32B>(m, Ks, ts, u);
-#pragma unroll
-            for (int a = 0; a < D; ++a) xn[a] = x[a] + dt * u[a];
-          }
-        } else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            acc[a] = k[a];
-            y[a] = x[a] + 0.5 * k[a];
-          }
-          double tp[D];
-#pragma unroll
-          for (int a = 0; a < D; ++a) tp[a] = t[a];
 #pragma unroll 1
-          for (int stage = 2; stage <= 4 && ok; ++stage) {
-            Ks = locate<D>(m, y, Ks, tp, ts, iters, f0);
-            ok = Ks != PIC_LOST;
-            if (!ok) break;
-            velocity<D, F32B>(m, Ks, ts, u);
+        for (int p = 0; p <= TB::S; ++p) {
+          if (p > 0) {
+            float hint[D];
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-              k[a] = dt * u[a];
-              tp[a] = ts[a];
+              hint[a] = ts[a].hi;
+              y[a] = df_add(xd[a], p < TB::S ? df_scale2(k[a], TB::c(p)) : acc[a]);
             }
-            if (stage == 2) {
-#pragma unroll
-              for (int a = 0; a < D; ++a) {
-                acc[a] += 2.0 * k[a];
-                y[a] = x[a] + 0.5 * k[a];
-              }
-            } else if (stage == 3) {
-#pragma unroll
-              for (int a = 0; a < D; ++a) {
-                acc[a] += 2.0 * k[a];
-                y[a] = x[a] + k[a];
-              }
-            } else {
-#pragma unroll
-              for (int a = 0; a < D; ++a) acc[a] += k[a];
+            Ks = locate_df<D>(m, y, Ks, hint, ts, iters, flags);
+            if (Ks == PIC_LOST) {
+              ok = false;
+              break;
             }
+            if (p == TB::S) break;
           }
-          if (ok) {
+          df u[D];
+          velocity<D, F32B>(m, Ks, ts, u);
+          const float w = TB::w(p);
 #pragma unroll
-            for (int a = 0; a < D; ++a) xn[a] = x[a] + acc[a] / 6.0;
+          for (int a = 0; a < D; ++a) {
+            k[a] = df_mul(dt, u[a]);
+            if (w != 0.f) acc[a] = df_add(acc[a], df_scale2(k[a], w));
+          }
+          if (p == TB::S - 1 && TB::divide6()) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) acc[a] = df_mul(acc[a], sixth);
           }
         }
         if (ok) {
-          double tn[D];
-          Kn = locate<D>(m, xn, Ks, ts, tn, iters, f0);
-          if (Kn != PIC_LOST) {
+          Kn = Ks;
 #pragma unroll
-            for (int a = 0; a < D; ++a) {
-              s.x[a * s.cap + i] = xn[a];
-              s.xhat[a * s.cap + i] = tn[a];
-            }
+          for (int a = 0; a < D; ++a) {
+            s.x[a * s.cap + i] = (x[a] + (double)acc[a].hi) + (double)acc[a].lo;
+            s.xhat[a * s.cap + i] = make_float2(ts[a].hi, ts[a].lo);
           }
         }
-        flags |= f0;
-        walks = (f0 & kFlagWalk) ? 1u : 0u;
-        globals = (f0 & kFlagGlobal) ? 1u : 0u;
       }
       cell_new[i] = Kn;
       if (Kn != PIC_LOST)
@@ -162,7 +176,7 @@ __global__ void __launch_bounds__(128) advect_kernel(MeshView m, StoreView s, do
       else
         lost = 1;
     }
-    flush_counters(ctr, steps, iters, lost, walks, globals, flags);
+    flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
   }
 }
 
@@ -177,16 +191,17 @@ __global__ void __launch_bounds__(128) relocate_kernel(MeshView m, StoreView s, 
     int iters = 0;
     unsigned flags = 0, lost = 0;
     if (i < n) {
-      double x[D], t[D], tn[D];
+      df y[D], tn[D];
+      float hint[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        x[a] = s.x[a * s.cap + i];
-        t[a] = s.xhat[a * s.cap + i];
+        y[a] = df_from_double(s.x[a * s.cap + i]);
+        hint[a] = s.xhat[a * s.cap + i].x;
       }
-      const uint32_t Kn = locate<D>(m, x, s.cell[i], t, tn, iters, flags);
+      const uint32_t Kn = locate_df<D>(m, y, s.cell[i], hint, tn, iters, flags);
       if (Kn != PIC_LOST) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) s.xhat[a * s.cap + i] = tn[a];
+        for (int a = 0; a < D; ++a) s.xhat[a * s.cap + i] = make_float2(tn[a].hi, tn[a].lo);
         atomicAdd(counts + Kn, 1u);
       } else {
         lost = 1;
@@ -241,8 +256,26 @@ static int grid_for(size_t n, int block) {
 
 template <int D, int RK, bool F32B>
 static void launch_advect(pic_particles_s* p, const MeshView& m, double dt, cudaStream_t st) {
-  advect_kernel<D, RK, F32B><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dt, p->cell_new,
+  const float hi = (float)dt;
+  const df dtd = {hi, (float)(dt - (double)hi)};
+  advect_kernel<D, RK, F32B><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd, p->cell_new,
                                                                          p->counts, p->ctr);
+  count_launches(1);
+}
+
+// Three events per timed step (before advect, after advect, after rebin),
+// created on first use and kept with the handle.
+static cudaEvent_t* timing_slot(pic_particles_s* p) {
+  if (p->n_ev == p->ev_cap) {
+    const int cap = p->ev_cap ? 2 * p->ev_cap : 64;
+    cudaEvent_t* ev = (cudaEvent_t*)realloc(p->ev, sizeof(cudaEvent_t) * 3 * cap);
+    if (!ev) return nullptr;
+    for (int k = 3 * p->ev_cap; k < 3 * cap; ++k)
+      if (cudaEventCreate(&ev[k]) != cudaSuccess) return nullptr;
+    p->ev = ev;
+    p->ev_cap = cap;
+  }
+  return p->ev + 3 * (p->n_ev++);
 }
 
 template <int D, bool F32B>
@@ -274,6 +307,8 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
   const MeshView m = mesh_view(mesh);
   for (int step = 0; step < n_steps; ++step) {
     PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
+    cudaEvent_t* ev = parts->timing ? timing_slot(parts) : nullptr;
+    if (ev) PIC_CUDA(cudaEventRecord(ev[0], st));
     const bool f32 = precision == PIC_FP32_BASIS;
     if (mesh->dim == 2) {
       if (f32)
@@ -287,8 +322,10 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
         launch_advect_rk<3, false>(parts, m, dt, (int)integrator, st);
     }
     PIC_CUDA(cudaGetLastError());
+    if (ev) PIC_CUDA(cudaEventRecord(ev[1], st));
     pic_status r = rebin_from_counts(parts, st);
     if (r != PIC_OK) return r;
+    if (ev) PIC_CUDA(cudaEventRecord(ev[2], st));
   }
   return PIC_OK;
 }
@@ -305,6 +342,7 @@ extern "C" pic_status pic_locate(pic_particles parts, pic_mesh mesh, void* strea
   else
     relocate_kernel<3><<<grid_for(parts->capacity, 128), 128, 0, st>>>(m, store_view(parts, parts->cur),
                                                                        parts->cell_new, parts->counts, parts->ctr);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return rebin_from_counts(parts, st);
 }
@@ -320,6 +358,7 @@ extern "C" pic_status pic_locate_points(pic_mesh mesh, size_t n, const double* x
     locate_points_kernel<2><<<grid_for(n, 128), 128, 0, st>>>(m, n, x, hint, cell_out, xhat_out);
   else
     locate_points_kernel<3><<<grid_for(n, 128), 128, 0, st>>>(m, n, x, hint, cell_out, xhat_out);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;
 }

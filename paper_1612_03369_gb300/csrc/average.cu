@@ -50,6 +50,7 @@ extern "C" pic_status pic_interpolate_to_cells(pic_particles p, pic_mesh mesh, i
   if (grid > cap) grid = cap;
   cell_average_kernel<<<(int)(grid ? grid : 1), 256, 0, st>>>(p->cell_off, p->props[p->cur] + (size_t)prop * p->capacity,
                                                               p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;
 }

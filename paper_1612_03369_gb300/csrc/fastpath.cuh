@@ -1,0 +1,474 @@
+// fastpath.cuh -- the advection hot path in double-float arithmetic on the
+// FP32 pipe (Sec. 2.3 velocity evaluation, Sec. 2.4 location).
+//
+// Layouts (built once per mesh / velocity field):
+//   cell block   per cell, the (bi/tri)linear map in monomial form about
+//                vertex 0: Phi_K(t) = X_0 + sum_k a_k m_k(t) with
+//                m = (t0, t1, t2, t0 t1, t0 t2, t1 t2, t0 t1 t2) in 3D and
+//                (t0, t1, t0 t1) in 2D; X_0 and every a_k as double-floats
+//                (192 B per hex, 64 B per quad, 16-byte aligned)
+//   U2           Q2 nodal values as double-floats, node-major [node][dim]
+//
+// Inverse map (Newton, Sec. 2.2 / Remark 2.1): FP32 iterations on the local
+// offset y - X_0 until the update falls below 1e-5, then one Newton step
+// whose residual (y - X_0) - sum_k a_k m_k(t) is evaluated in double-float
+// (absolute accuracy ~2^-47 h), with the FP32 Jacobian at the current
+// iterate.  That leaves |t - t*| ~ 1e-14.  If the FP32 phase does not settle
+// the cell is handed to the FP64 Newton of pic_internal.cuh (rare).
+#pragma once
+
+#include "df.cuh"
+#include "locate.cuh"
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr float kSettle32 = 1e-5f;  // FP32 phase ends when max|update| <= this
+constexpr int kMaxIt32 = 8;
+
+template <int D>
+struct CellBlock {
+  df x0[D];
+  df a[(1 << D) - 1][D];
+};
+
+template <int D>
+__host__ __device__ constexpr int block_float4s() {
+  return (2 * D + 2 * D * ((1 << D) - 1)) / 4;  // 12 (3D) or 4 (2D)
+}
+
+template <int D>
+__device__ __forceinline__ void load_block(const MeshView& m, uint32_t K, CellBlock<D>& cb) {
+  constexpr int NF4 = block_float4s<D>();
+  const float4* p = m.blk + (size_t)K * NF4;
+  float f[4 * NF4];
+#pragma unroll
+  for (int q = 0; q < NF4; ++q) {
+    const float4 v = __ldg(p + q);
+    f[4 * q] = v.x;
+    f[4 * q + 1] = v.y;
+    f[4 * q + 2] = v.z;
+    f[4 * q + 3] = v.w;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) cb.x0[a] = df_make(f[2 * a], f[2 * a + 1]);
+#pragma unroll
+  for (int k = 0; k < (1 << D) - 1; ++k)
+#pragma unroll
+    for (int a = 0; a < D; ++a) cb.a[k][a] = df_make(f[2 * D + 2 * (k * D + a)], f[2 * D + 2 * (k * D + a) + 1]);
+}
+
+// FP32 map offset phi(t) = sum_k a_k m_k(t) and Jacobian, from the high parts.
+template <int D>
+__device__ __forceinline__ void map32(const CellBlock<D>& cb, const float t[D], float phi[D], float J[D][D]) {
+  if constexpr (D == 2) {
+    const float t01 = t[0] * t[1];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi;
+      phi[c] = fmaf(a3, t01, fmaf(a2, t[1], a1 * t[0]));
+      J[c][0] = fmaf(a3, t[1], a1);
+      J[c][1] = fmaf(a3, t[0], a2);
+    }
+  } else {
+    const float t01 = t[0] * t[1], t02 = t[0] * t[2], t12 = t[1] * t[2], t012 = t01 * t[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi, a4 = cb.a[3][c].hi;
+      const float a5 = cb.a[4][c].hi, a6 = cb.a[5][c].hi, a7 = cb.a[6][c].hi;
+      phi[c] = fmaf(a7, t012, fmaf(a6, t12, fmaf(a5, t02, fmaf(a4, t01, fmaf(a3, t[2], fmaf(a2, t[1], a1 * t[0]))))));
+      J[c][0] = fmaf(a7, t12, fmaf(a5, t[2], fmaf(a4, t[1], a1)));
+      J[c][1] = fmaf(a7, t02, fmaf(a6, t[2], fmaf(a4, t[0], a2)));
+      J[c][2] = fmaf(a7, t01, fmaf(a6, t[1], fmaf(a5, t[0], a3)));
+    }
+  }
+}
+
+template <int D>
+__device__ __forceinline__ bool solve32(const float J[D][D], const float r[D], float d[D]) {
+  if constexpr (D == 2) {
+    const float det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
+    const float inv = 1.0f / det;
+    d[0] = (J[1][1] * r[0] - J[0][1] * r[1]) * inv;
+    d[1] = (J[0][0] * r[1] - J[1][0] * r[0]) * inv;
+    return true;
+  } else {
+    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
+    const float inv = 1.0f / det;
+    const float c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    const float c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    const float c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    const float c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    const float c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    d[0] = (c00 * r[0] + c10 * r[1] + c20 * r[2]) * inv;
+    d[1] = (c01 * r[0] + c11 * r[1] + c21 * r[2]) * inv;
+    d[2] = (c02 * r[0] + c12 * r[1] + c22 * r[2]) * inv;
+    return true;
+  }
+}
+
+__device__ __forceinline__ df neg(df a) { return df_make(-a.hi, -a.lo); }
+
+// Double-float residual r = dloc - sum_k a_k m_k(t) at a single-float point t
+// (the monomials of t are formed exactly with two_prod).
+template <int D>
+__device__ __forceinline__ void residual_df(const CellBlock<D>& cb, const df dloc[D], const float t[D], float r[D]) {
+  const df m01 = two_prod(t[0], t[1]);
+  if constexpr (D == 2) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      df_acc acc = acc_init(dloc[c]);
+      acc_mad_f(acc, neg(cb.a[0][c]), t[0]);
+      acc_mad_f(acc, neg(cb.a[1][c]), t[1]);
+      acc_mad(acc, neg(cb.a[2][c]), m01);
+      r[c] = __fadd_rn(acc.s, acc.e);
+    }
+  } else {
+    const df m02 = two_prod(t[0], t[2]);
+    const df m12 = two_prod(t[1], t[2]);
+    const df m012 = df_mul_f(m01, t[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      df_acc acc = acc_init(dloc[c]);
+      acc_mad_f(acc, neg(cb.a[0][c]), t[0]);
+      acc_mad_f(acc, neg(cb.a[1][c]), t[1]);
+      acc_mad_f(acc, neg(cb.a[2][c]), t[2]);
+      acc_mad(acc, neg(cb.a[3][c]), m01);
+      acc_mad(acc, neg(cb.a[4][c]), m02);
+      acc_mad(acc, neg(cb.a[5][c]), m12);
+      acc_mad(acc, neg(cb.a[6][c]), m012);
+      r[c] = __fadd_rn(acc.s, acc.e);
+    }
+  }
+}
+
+// Outcome of the inverse map in one cell.
+enum : int { kCellOut = 0, kCellIn = 1, kCellFail = -1 };
+
+// Inverse map of y in cell K (fast path).  t32 holds the FP32 start on entry;
+// on return t holds the double-float reference coordinates.
+template <int D>
+__device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
+                                             int& iters) {
+  CellBlock<D> cb;
+  load_block<D>(m, K, cb);
+  df dloc[D];
+  float d32[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    dloc[a] = df_sub(y[a], cb.x0[a]);
+    d32[a] = dloc[a].hi;
+  }
+  float phi[D], J[D][D], r[D], dt[D];
+  bool settled = false;
+#pragma unroll 1
+  for (int it = 0; it < kMaxIt32; ++it) {
+    ++iters;
+    map32<D>(cb, t32, phi, J);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[a] = d32[a] - phi[a];
+    if (!solve32<D>(J, r, dt)) return kCellFail;
+    float mx = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      t32[a] += dt[a];
+      mx = fmaxf(mx, fabsf(dt[a]));
+    }
+    if (!(mx <= 1e3f)) return kCellFail;  // diverging or NaN
+    if (mx <= kSettle32) {
+      settled = true;
+      break;
+    }
+  }
+  if (!settled) return kCellFail;
+  // one Newton step with the double-float residual
+  ++iters;
+  map32<D>(cb, t32, phi, J);
+  residual_df<D>(cb, dloc, t32, r);
+  if (!solve32<D>(J, r, dt)) return kCellFail;
+  float mx = 0.f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) mx = fmaxf(mx, fabsf(dt[a]));
+  if (!(mx <= 4.f * kSettle32)) return kCellFail;
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    t[a] = two_sum(t32[a], dt[a]);
+    // t >= -eps  <=>  t32 >= -eps - dt ;  t <= 1 + eps  <=>  t32 - 1 <= eps - dt
+    in = in && (t32[a] >= -(float)kInsideEps - dt[a]) && (t32[a] - 1.0f <= (float)kInsideEps - dt[a]);
+  }
+  return in ? kCellIn : kCellOut;
+}
+
+// FP64 Newton for a cell the fast path could not settle (rare; out of line
+// so that the hot loop stays small in the instruction cache).
+template <int D>
+__device__ __noinline__ int test_cell_fp64(const MeshView& m, uint32_t K, const df* y, float* t32, df* t, int* iters,
+                                           unsigned* flags) {
+  double yd[D], tt[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    yd[a] = df_to_double(y[a]);
+    tt[a] = isfinite(t32[a]) && fabsf(t32[a]) < 4.f ? (double)t32[a] : 0.5;
+  }
+  bool conv = false;
+  const bool in = try_cell<D>(m, K, yd, tt, *iters, *flags, &conv);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    t[a] = df_from_double(tt[a]);
+    t32[a] = t[a].hi;
+  }
+  if (!conv) return kCellFail;
+  return in ? kCellIn : kCellOut;
+}
+
+// Fast path, then the FP64 Newton when the fast path does not settle.
+template <int D>
+__device__ __forceinline__ int test_cell(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
+                                         int& iters, unsigned& flags) {
+  float s[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) s[a] = t32[a];
+  const int r = solve_cell_df<D>(m, K, y, t32, t, iters);
+  if (r != kCellFail) return r;
+  flags |= kFlagFallback64;
+#pragma unroll
+  for (int a = 0; a < D; ++a) t32[a] = s[a];
+  return test_cell_fp64<D>(m, K, y, t32, t, &iters, &flags);
+}
+
+// Lowest-index rule (see lowest_owner in locate.cuh) on the fast path.  The
+// band test is inline; the neighbour tests (rare) are out of line.
+template <int D>
+__device__ __noinline__ uint32_t lowest_owner_df_slow(const MeshView& m, const df* y, uint32_t found, df* t, int* iters,
+                                                      unsigned* flags) {
+  int c[3];
+  cell_ijk<D>(m, found, c);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lo[a] = (t[a].hi < (float)kTieBand && c[a] > 0) ? -1 : 0;
+    hi[a] = (t[a].hi > 1.0f - (float)kTieBand && c[a] < m.n[a] - 1) ? 1 : 0;
+  }
+  uint32_t best = found;
+  df tb[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) tb[a] = t[a];
+  for (int o2 = (D == 3 ? lo[2] : 0); o2 <= (D == 3 ? hi[2] : 0); ++o2)
+    for (int o1 = lo[1]; o1 <= hi[1]; ++o1)
+      for (int o0 = lo[0]; o0 <= hi[0]; ++o0) {
+        if (o0 == 0 && o1 == 0 && o2 == 0) continue;
+        const uint32_t K = cell_index<D>(m, c[0] + o0, c[1] + o1, c[2] + o2);
+        if (K >= best) continue;
+        const int o[3] = {o0, o1, o2};
+        float s[D];
+        df tt[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) s[a] = t[a].hi - (float)o[a];
+        if (test_cell<D>(m, K, y, s, tt, *iters, *flags) == kCellIn) {
+          best = K;
+#pragma unroll
+          for (int a = 0; a < D; ++a) tb[a] = tt[a];
+        }
+      }
+#pragma unroll
+  for (int a = 0; a < D; ++a) t[a] = tb[a];
+  return best;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t lowest_owner_df(const MeshView& m, const df y[D], uint32_t found, df t[D],
+                                                    int& iters, unsigned& flags) {
+  int c[3];
+  cell_ijk<D>(m, found, c);
+  bool any = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    any = any || (t[a].hi < (float)kTieBand && c[a] > 0) || (t[a].hi > 1.0f - (float)kTieBand && c[a] < m.n[a] - 1);
+  if (!any) return found;
+  return lowest_owner_df_slow<D>(m, y, found, t, &iters, &flags);
+}
+
+// Past the hint cell and its predicted neighbour: the FP64 walk over the
+// other vertex neighbours (paper's a.b order) and the all-cells search.
+template <int D>
+__device__ __noinline__ uint32_t locate_df_slow(const MeshView& m, const df* y, uint32_t hintK, df* t, int* iters,
+                                                unsigned* flags) {
+  double yd[D], th[D], to[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    yd[a] = df_to_double(y[a]);
+    th[a] = 0.5;
+  }
+  const uint32_t K = hintK < m.C ? locate<D>(m, yd, hintK, th, to, *iters, *flags)
+                                 : global_search<D>(m, yd, to, *iters, *flags);
+#pragma unroll
+  for (int a = 0; a < D; ++a) t[a] = df_from_double(to[a]);
+  return K;
+}
+
+// Owner of y (lowest index) and its double-float reference coordinates.
+// Search order: the hint cell, then up to two hops to the neighbour that the
+// current cell's Newton iterate points to (across every facet it violates),
+// then (out of line) the FP64 walk over the hint's vertex neighbours in the
+// paper's a.b order and the all-cells search.  The owner does not depend on
+// the order: the first cell found to hold y is settled by the lowest-index
+// rule.
+constexpr int kPredictedHops = 2;
+
+template <int D>
+__device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], uint32_t hintK, const float hint_t[D],
+                                              df t[D], int& iters, unsigned& flags) {
+  if (hintK >= m.C) {
+    flags |= kFlagBounds;
+    return locate_df_slow<D>(m, y, hintK, t, &iters, &flags);
+  }
+  float t32[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) t32[a] = hint_t[a];
+  uint32_t K = hintK;
+#pragma unroll 1
+  for (int pass = 0; pass <= kPredictedHops; ++pass) {
+    const int r = test_cell<D>(m, K, y, t32, t, iters, flags);
+    if (r == kCellIn) return lowest_owner_df<D>(m, y, K, t, iters, flags);
+    if (pass == kPredictedHops || r != kCellOut) break;
+    flags |= kFlagWalk;
+    int c[3], pred[3] = {0, 0, 0};
+    cell_ijk<D>(m, K, c);
+    bool have_pred = false;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      pred[a] = t32[a] < 0.f ? -1 : (t32[a] >= 1.f ? 1 : 0);
+      if (c[a] + pred[a] < 0 || c[a] + pred[a] >= m.n[a]) pred[a] = 0;
+      have_pred = have_pred || pred[a] != 0;
+      t32[a] -= (float)pred[a];
+    }
+    if (!have_pred) break;
+    K = cell_index<D>(m, c[0] + pred[0], c[1] + pred[1], c[2] + pred[2]);
+  }
+  flags |= kFlagWalk | kFlagWalk64;
+  return locate_df_slow<D>(m, y, hintK, t, &iters, &flags);
+}
+
+// ---------------------------------------------------------- Q2 velocity --
+// u_h = sum_{a,b,c} U[node(K; a,b,c)] l_a(t0) l_b(t1) l_c(t2) with the 1D
+// quadratic Lagrange basis on {0, 1/2, 1}:
+//   l0 = (1-t)(1-2t) = -w v,  l1 = 4 t w,  l2 = t v,  w = 1-t, v = 2t-1,
+// all in double-float, contracted one axis at a time.
+
+__device__ __forceinline__ void lagrange2_df(df t, df l[3]) {
+  const df ws = two_sum(1.0f, -t.hi);
+  const df w = fast_two_sum(ws.hi, __fsub_rn(ws.lo, t.lo));
+  const df vs = two_sum(__fmul_rn(2.0f, t.hi), -1.0f);
+  const df v = fast_two_sum(vs.hi, __fmaf_rn(2.0f, t.lo, vs.lo));
+  const df wv = df_mul(w, v);
+  l[0] = df_make(-wv.hi, -wv.lo);
+  l[1] = df_scale2(df_mul(t, w), 4.0f);
+  l[2] = df_mul(t, v);
+}
+
+template <int D>
+__device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
+  int c[3];
+  cell_ijk<D>(m, K, c);
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  df L0[3], L1[3], L2[3];
+  lagrange2_df(t[0], L0);
+  lagrange2_df(t[1], L1);
+  if constexpr (D == 3) lagrange2_df(t[2], L2);
+  df_acc outer[D];
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) outer[comp] = acc_zero();
+  // rows (b, cz) in order; the basis values of the current b and cz sit in
+  // L1[0] and L2[0] and are rotated after each row (no indexed register
+  // arrays, rolled loops keep the instruction footprint small)
+#pragma unroll 1
+  for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
+    df_acc mid[D];
+#pragma unroll
+    for (int comp = 0; comp < D; ++comp) mid[comp] = acc_zero();
+#pragma unroll 1
+    for (int b = 0; b < 3; ++b) {
+      const float2* row = m.U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
+      float2 nd[3 * D];
+#pragma unroll
+      for (int q = 0; q < 3 * D; ++q) nd[q] = __ldg(row + q);
+#pragma unroll
+      for (int comp = 0; comp < D; ++comp) {
+        df_acc r;
+        {
+          const df p = two_prod(nd[comp].x, L0[0].hi);
+          float lo = __fmaf_rn(nd[comp].x, L0[0].lo, p.lo);
+          r.s = p.hi;
+          r.e = __fmaf_rn(nd[comp].y, L0[0].hi, lo);
+        }
+        acc_mad(r, df_make(nd[D + comp].x, nd[D + comp].y), L0[1]);
+        acc_mad(r, df_make(nd[2 * D + comp].x, nd[2 * D + comp].y), L0[2]);
+        acc_mad(mid[comp], acc_pair(r), L1[0]);
+      }
+      const df l = L1[0];
+      L1[0] = L1[1];
+      L1[1] = L1[2];
+      L1[2] = l;
+    }
+#pragma unroll
+    for (int comp = 0; comp < D; ++comp) {
+      if constexpr (D == 3)
+        acc_mad(outer[comp], acc_pair(mid[comp]), L2[0]);
+      else
+        outer[comp] = mid[comp];
+    }
+    if constexpr (D == 3) {
+      const df l = L2[0];
+      L2[0] = L2[1];
+      L2[1] = L2[2];
+      L2[2] = l;
+    }
+  }
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) u[comp] = acc_result(outer[comp]);
+}
+
+// FP32 basis and contraction (precision form): only the high parts.
+template <int D>
+__device__ __forceinline__ void q2_eval_f32(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
+  int c[3];
+  cell_ijk<D>(m, K, c);
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  float L[D][3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) lagrange2<float>(t[a].hi, L[a]);
+  float out[D];
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) out[comp] = 0.f;
+#pragma unroll
+  for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
+    float mid[D];
+#pragma unroll
+    for (int comp = 0; comp < D; ++comp) mid[comp] = 0.f;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const float2* row = m.U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
+#pragma unroll
+      for (int comp = 0; comp < D; ++comp) {
+        const float s = fmaf(L[0][2], __ldg(row + 2 * D + comp).x,
+                             fmaf(L[0][1], __ldg(row + D + comp).x, L[0][0] * __ldg(row + comp).x));
+        mid[comp] = fmaf(L[1][b], s, mid[comp]);
+      }
+    }
+#pragma unroll
+    for (int comp = 0; comp < D; ++comp) out[comp] = (D == 3) ? fmaf(L[D - 1][cz], mid[comp], out[comp]) : mid[comp];
+  }
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) u[comp] = df_make(out[comp], 0.f);
+}
+
+}  // namespace pic

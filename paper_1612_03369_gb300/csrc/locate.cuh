@@ -9,7 +9,14 @@
 
 namespace pic {
 
-enum : unsigned { kFlagWalk = 1u, kFlagGlobal = 2u, kFlagNonConv = 4u, kFlagBounds = 8u };
+enum : unsigned {
+  kFlagWalk = 1u,
+  kFlagGlobal = 2u,
+  kFlagNonConv = 4u,
+  kFlagBounds = 8u,
+  kFlagFallback64 = 16u,  // the FP32/double-float inverse map handed a cell to the FP64 Newton
+  kFlagWalk64 = 32u       // the walk went past the predicted neighbour (FP64 walk)
+};
 
 // Newton in cell K from the start held in t; true if y is inside K.
 template <int D>

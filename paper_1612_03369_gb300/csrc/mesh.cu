@@ -34,6 +34,54 @@ __global__ void cell_bbox_kernel(MeshView m, double* __restrict__ bbox) {
   }
 }
 
+__device__ __forceinline__ float2 split_df(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
+// Per-cell map block: X_0 and the monomial coefficients of Phi_K - X_0
+// (3D: t0, t1, t2, t0t1, t0t2, t1t2, t0t1t2; 2D: t0, t1, t0t1), each as a
+// double-float.  With e_v = X_v - X_0 (v = bit pattern of the vertex):
+//   a_t0 = e1, a_t1 = e2, a_t2 = e4, a_t0t1 = e3 - e1 - e2,
+//   a_t0t2 = e5 - e1 - e4, a_t1t2 = e6 - e2 - e4,
+//   a_t0t1t2 = e7 - e3 - e5 - e6 + e1 + e2 + e4.
+template <int D>
+__global__ void cell_block_kernel(MeshView m, float2* __restrict__ blk) {
+  constexpr int NK = (1 << D) - 1;
+  constexpr int NF2 = D + NK * D;
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
+    CellGeom<D> g;
+    load_cell<D>(m, K, g);
+    float2* out = blk + (size_t)K * NF2;
+    for (int a = 0; a < D; ++a) out[a] = split_df(g.x0[a]);
+    for (int a = 0; a < D; ++a) {
+      double coef[NK];
+      if constexpr (D == 2) {
+        coef[0] = g.e[1][a];
+        coef[1] = g.e[2][a];
+        coef[2] = g.e[3][a] - g.e[1][a] - g.e[2][a];
+      } else {
+        coef[0] = g.e[1][a];
+        coef[1] = g.e[2][a];
+        coef[2] = g.e[4][a];
+        coef[3] = g.e[3][a] - g.e[1][a] - g.e[2][a];
+        coef[4] = g.e[5][a] - g.e[1][a] - g.e[4][a];
+        coef[5] = g.e[6][a] - g.e[2][a] - g.e[4][a];
+        coef[6] = g.e[7][a] - g.e[3][a] - g.e[5][a] - g.e[6][a] + g.e[1][a] + g.e[2][a] + g.e[4][a];
+      }
+      for (int k = 0; k < NK; ++k) out[D + k * D + a] = split_df(coef[k]);
+    }
+  }
+}
+
+// U [comp][node] FP64 -> U2 [node][comp] double-float.
+__global__ void to_df_nodes_kernel(const double* __restrict__ U, float2* __restrict__ U2, int dim, size_t nnodes) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nnodes * dim; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t node = i / dim, comp = i % dim;
+    U2[i] = split_df(U[comp * nnodes + node]);
+  }
+}
+
 __global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -74,8 +122,10 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
     pic_destroy_mesh(m);
     return s;
   };
+  const size_t blk_f4 = dim == 3 ? 12 : 4;
   if (cudaMalloc(&m->X, sizeof(double) * dim * nv) != cudaSuccess ||
-      cudaMalloc(&m->bbox, sizeof(double) * 6 * C) != cudaSuccess) {
+      cudaMalloc(&m->bbox, sizeof(double) * 6 * C) != cudaSuccess ||
+      cudaMalloc(&m->blk, sizeof(float4) * blk_f4 * C) != cudaSuccess) {
     cudaGetLastError();
     set_error("pic_create_mesh: device allocation failed");
     return fail(PIC_ERR_OOM);
@@ -110,10 +160,13 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   }
   const MeshView mv = mesh_view(m);
   const int grid = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
-  if (dim == 2)
+  if (dim == 2) {
     cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox);
-  else
+    cell_block_kernel<2><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+  } else {
     cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox);
+    cell_block_kernel<3><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_fail(e, "pic_create_mesh: set-up kernels"));
@@ -127,6 +180,8 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->U);
   cudaFree(m->U32);
   cudaFree(m->bbox);
+  cudaFree(m->blk);
+  cudaFree(m->U2);
   free(m);
   return PIC_OK;
 }
@@ -138,13 +193,16 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)m->dim * (size_t)m->nnodes;
   if (!m->U) {
-    if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32, sizeof(float) * n) != cudaSuccess) {
+    if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&m->U2, sizeof(float2) * n) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
-  to_f32_kernel<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256, 0, st>>>(m->U, m->U32, n);
+  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
+  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
   return PIC_OK;

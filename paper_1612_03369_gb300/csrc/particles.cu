@@ -44,12 +44,23 @@ __global__ void seed_kernel(MeshView m, StoreView s, const uint32_t* __restrict_
 #pragma unroll
       for (int j = 0; j < D; ++j) {
         s.x[j * s.cap + q] = x[j];
-        s.xhat[j * s.cap + q] = t[j];
+        const float hi = __double2float_rn(t[j]);
+        s.xhat[j * s.cap + q] = make_float2(hi, __double2float_rn(t[j] - (double)hi));
       }
       s.id[q] = first_id + q;
       s.cell[q] = K;
       for (int p = 0; p < s.n_props; ++p) s.props[p * s.cap + q] = 0.0;
     }
+  }
+}
+
+// double-float reference coordinates -> FP64 (export)
+__global__ void xhat_to_double_kernel(const float2* __restrict__ src, double* __restrict__ dst, size_t cap, size_t n,
+                                      int dim) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n * dim; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t a = i / n, j = i % n;
+    const float2 v = src[a * cap + j];
+    dst[a * n + j] = (double)v.x + (double)v.y;
   }
 }
 
@@ -80,6 +91,8 @@ extern "C" pic_status pic_destroy_particles(pic_particles p) {
   cudaFree(p->key_src);
   cudaFree(p->perm);
   cudaFree(p->ctr);
+  for (int k = 0; k < 3 * p->ev_cap; ++k) cudaEventDestroy(p->ev[k]);
+  free(p->ev);
   free(p);
   return PIC_OK;
 }
@@ -166,7 +179,7 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
   bool ok = true;
   for (int b = 0; b < 2 && ok; ++b) {
     ok = ok && cudaMalloc(&p->x[b], sizeof(double) * d * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&p->xhat[b], sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->xhat[b], sizeof(float2) * d * cap) == cudaSuccess;
     ok = ok && cudaMalloc(&p->id[b], sizeof(uint64_t) * cap) == cudaSuccess;
     ok = ok && cudaMalloc(&p->cell[b], sizeof(uint32_t) * cap) == cudaSuccess;
     ok = ok && cudaMalloc(&p->props[b], sizeof(double) * (n_props > 0 ? n_props : 1) * cap) == cudaSuccess;
@@ -214,6 +227,7 @@ extern "C" pic_status pic_set_properties(pic_particles p, int prop, const double
   if (prop < 0 || prop >= p->n_props) return (set_error("pic_set_properties: property %d out of range", prop), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   set_prop_kernel<<<1024, 256, 0, st>>>(p->props[p->cur] + (size_t)prop * p->capacity, values, p->ctr);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;
 }
@@ -248,6 +262,17 @@ extern "C" pic_status pic_get_stats(pic_particles p, uint64_t* particle_steps, u
   return PIC_OK;
 }
 
+extern "C" pic_status pic_get_counters(pic_particles p, uint64_t* values, int n_values) {
+  if (!p || (!values && n_values > 0) || n_values < 0) return (set_error("pic_get_counters: bad argument"), PIC_ERR_ARG);
+  DevCounters h;
+  pic_status r = read_counters(p, &h);
+  if (r != PIC_OK) return r;
+  const uint64_t v[PIC_N_COUNTERS] = {h.particle_steps, h.walks, h.global_searches, h.newton_iterations,
+                                      h.lost_total, h.fallback64, h.walk64};
+  for (int k = 0; k < n_values && k < PIC_N_COUNTERS; ++k) values[k] = v[k];
+  return PIC_OK;
+}
+
 extern "C" pic_status pic_export(pic_particles p, double* x, double* xhat, uint64_t* id, uint32_t* cell, double* props,
                                  void* stream) {
   if (!p) return (set_error("pic_export: null handle"), PIC_ERR_ARG);
@@ -260,7 +285,19 @@ extern "C" pic_status pic_export(pic_particles p, double* x, double* xhat, uint6
   if (N == 0) return PIC_OK;
   for (int a = 0; a < p->dim; ++a) {
     if (x) PIC_CUDA(cudaMemcpyAsync(x + a * N, p->x[c] + a * cap, sizeof(double) * N, cudaMemcpyDefault, st));
-    if (xhat) PIC_CUDA(cudaMemcpyAsync(xhat + a * N, p->xhat[c] + a * cap, sizeof(double) * N, cudaMemcpyDefault, st));
+  }
+  if (xhat) {
+    cudaPointerAttributes at;
+    const bool dev = cudaPointerGetAttributes(&at, xhat) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    double* tmp = xhat;
+    if (!dev) PIC_CUDA(cudaMallocAsync((void**)&tmp, sizeof(double) * p->dim * N, st));
+    xhat_to_double_kernel<<<1024, 256, 0, st>>>(p->xhat[c], tmp, cap, N, p->dim);
+    PIC_CUDA(cudaGetLastError());
+    if (!dev) {
+      PIC_CUDA(cudaMemcpyAsync(xhat, tmp, sizeof(double) * p->dim * N, cudaMemcpyDefault, st));
+      PIC_CUDA(cudaFreeAsync(tmp, st));
+    }
   }
   if (id) PIC_CUDA(cudaMemcpyAsync(id, p->id[c], sizeof(uint64_t) * N, cudaMemcpyDefault, st));
   if (cell) PIC_CUDA(cudaMemcpyAsync(cell, p->cell[c], sizeof(uint32_t) * N, cudaMemcpyDefault, st));

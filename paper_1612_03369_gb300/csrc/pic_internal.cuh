@@ -40,6 +40,8 @@ struct DevCounters {
   unsigned long long global_searches;
   unsigned long long newton_iterations;
   unsigned long long lost_total;
+  unsigned long long fallback64;  // particle-steps where a cell went to the FP64 Newton
+  unsigned long long walk64;      // particle-steps where the walk went past the predicted neighbour
   unsigned int status;
   unsigned int n_alive;  // particles in the store
   unsigned int n_next;   // particles after the pending rebin
@@ -59,6 +61,8 @@ struct pic_mesh_s {
   double* U;     // [dim][nnodes]
   float* U32;    // [dim][nnodes] FP32 copy for the FP32-basis form
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
+  float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
+  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo)
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
 };
@@ -69,9 +73,10 @@ struct pic_particles_s {
   uint32_t C;             // cells of the mesh it was seeded on
   const pic_mesh_s* mesh;
   size_t capacity;
-  // double-buffered store, component-major with stride `capacity`
+  // double-buffered store, component-major with stride `capacity`;
+  // reference coordinates are kept as double-floats (hi, lo)
   double* x[2];
-  double* xhat[2];
+  float2* xhat[2];
   uint64_t* id[2];
   uint32_t* cell[2];
   double* props[2];
@@ -87,6 +92,11 @@ struct pic_particles_s {
   uint32_t* perm;         // [capacity]
   pic::DevCounters* ctr;  // device counters and status word
   cudaStream_t stream;
+  // optional event timing of pic_advect (instrumentation)
+  int timing;
+  int n_ev;                // event pairs recorded since the last read
+  int ev_cap;
+  cudaEvent_t* ev;         // 3 events per step: before advect, after advect, after rebin
 };
 
 namespace pic {
@@ -110,6 +120,8 @@ struct MeshView {
   const double* U;
   const float* U32;
   const double* bbox;
+  const float4* blk;
+  const float2* U2;
   double dlo[3], dhi[3];
 };
 
@@ -129,12 +141,14 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.U = m->U;
   v.U32 = m->U32;
   v.bbox = m->bbox;
+  v.blk = m->blk;
+  v.U2 = m->U2;
   return v;
 }
 
 struct StoreView {
   double* x;      // [dim][cap]
-  double* xhat;   // [dim][cap]
+  float2* xhat;   // [dim][cap] double-float reference coordinates
   uint64_t* id;
   uint32_t* cell;
   double* props;  // [P][cap]
@@ -370,4 +384,6 @@ pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* blo
                     uint32_t* cursor_init, cudaStream_t s);
 uint32_t scan_block_count(uint32_t n);
 int num_sms();
+// Host-side count of kernel launches (instrumentation).
+void count_launches(int n);
 }  // namespace pic

@@ -128,6 +128,7 @@ pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* blo
   scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums);
   scan_sums_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb);
   scan_apply_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums, out, cursor_init, total_dev);
+  count_launches(3);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;
 }
@@ -237,6 +238,7 @@ pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
   rank_by_id_kernel<<<grid_cap((size_t)p->C * 32, 256, 16), 256, 0, s>>>(p->cell_off, p->key_id, p->key_src, p->perm,
                                                                         b.cell, p->C, p->capacity, p->ctr);
   gather_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(a, b, p->perm, p->dim, p->ctr);
+  count_launches(3);
   PIC_CUDA(cudaGetLastError());
   p->cur = 1 - p->cur;
   return PIC_OK;
@@ -268,6 +270,7 @@ extern "C" pic_status pic_rebin(pic_particles parts, void* stream) {
   PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
   identity_cells_kernel<<<grid_cap(parts->capacity, 256, 16), 256, 0, st>>>(parts->cell[parts->cur], parts->cell_new,
                                                                           parts->counts, parts->C, parts->ctr);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return rebin_from_counts(parts, st);
 }

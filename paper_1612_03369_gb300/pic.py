@@ -40,8 +40,12 @@ SIGNATURES = {
     "pic_interpolate_to_cells": (_I, [_P, _P, _I, _I, _P, _P, _F64, _P]),
     "pic_get_state": (_I, [_P, _P, _P, _P]),
     "pic_get_stats": (_I, [_P, _P, _P, _P, _P]),
+    "pic_get_counters": (_I, [_P, _P, _I]),
     "pic_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pic_cell_offsets": (_I, [_P, _P, _P]),
+    "pic_timing_enable": (_I, [_P, _I]),
+    "pic_timing_read": (_I, [_P, _P, _P, _P]),
+    "pic_kernel_launches": (_U64, []),
     "pic_last_error": (C.c_char_p, []),
     "pic_version": (C.c_char_p, []),
 }
@@ -168,6 +172,15 @@ def pic_get_stats(parts: int):
     return dict(zip(("particle_steps", "walks", "global_searches", "newton_iterations"), [int(a.value) for a in v]))
 
 
+COUNTER_NAMES = ("particle_steps", "walks", "global_searches", "newton_iterations", "lost", "fallback64", "walk64")
+
+
+def pic_get_counters(parts: int) -> dict:
+    v = (C.c_uint64 * len(COUNTER_NAMES))()
+    _check(_lib.pic_get_counters(parts, v, len(COUNTER_NAMES)), "pic_get_counters")
+    return dict(zip(COUNTER_NAMES, [int(a) for a in v]))
+
+
 def pic_export(parts: int, x=None, xhat=None, id=None, cell=None, props=None, stream=None):
     _check(_lib.pic_export(parts, _ptr(x), _ptr(xhat), _ptr(id), _ptr(cell), _ptr(props), _stream(stream)),
            "pic_export")
@@ -175,6 +188,20 @@ def pic_export(parts: int, x=None, xhat=None, id=None, cell=None, props=None, st
 
 def pic_cell_offsets(parts: int, off, stream=None):
     _check(_lib.pic_cell_offsets(parts, _ptr(off), _stream(stream)), "pic_cell_offsets")
+
+
+def pic_timing_enable(parts: int, on: bool):
+    _check(_lib.pic_timing_enable(parts, int(bool(on))), "pic_timing_enable")
+
+
+def pic_timing_read(parts: int):
+    a, r, n = C.c_double(), C.c_double(), C.c_uint64()
+    _check(_lib.pic_timing_read(parts, C.byref(a), C.byref(r), C.byref(n)), "pic_timing_read")
+    return float(a.value), float(r.value), int(n.value)
+
+
+def pic_kernel_launches() -> int:
+    return int(_lib.pic_kernel_launches())
 
 
 def pic_version() -> str:
@@ -250,7 +277,7 @@ class Particles:
         return pic_get_state(self.h)
 
     def stats(self):
-        return pic_get_stats(self.h)
+        return pic_get_counters(self.h)
 
     def average(self, prop, empty_fill=0.0, stream=None):
         import torch
