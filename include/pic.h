@@ -155,6 +155,21 @@ pic_status pic_rebin(pic_particles parts, void *stream);
 pic_status pic_locate_points(pic_mesh mesh, size_t n, const double *x, const uint32_t *hint, uint32_t *cell_out,
                              double *xhat_out, void *stream);
 
+/* Stateless form of the rebin (Sec. 2.1 "sorted by their containing cells",
+ * Sec. 2.2 "first put cell-particle pairs into a linear array ... then fill
+ * the multi-map"): the order of n items by (cell, id).
+ *   cell      [n] u32 device; items with cell >= n_cells (0xFFFFFFFF = lost)
+ *             are left out
+ *   id        [n] u64 device, unique among the items kept
+ *   perm      [n] u32 device: perm[0 .. kept-1] = item indices in (cell, id)
+ *             order; entries past `kept` are not written
+ *   cell_off  [n_cells + 1] u32 device: items of cell K are
+ *             perm[cell_off[K] .. cell_off[K+1]-1]; cell_off[n_cells] = kept
+ * Allocates its scratch (about 12 B per item + 8 B per cell) on `stream`
+ * with cudaMallocAsync and frees it there.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_sort_by_cell(size_t n, const uint32_t *cell, const uint64_t *id, uint32_t n_cells, uint32_t *perm,
+                            uint32_t *cell_off, void *stream);
+
 /* Particle -> cell transfer (Sec. 2.7, scheme (ii), arithmetic average):
  * avg[K] = (sum of property `prop` over the particles of K) / n_K, summed in
  * a fixed order (deterministic); count[K] = n_K; empty cells get empty_fill.

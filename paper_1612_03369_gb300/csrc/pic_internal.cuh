@@ -384,6 +384,22 @@ pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* blo
                     uint32_t* cursor_init, cudaStream_t s);
 uint32_t scan_block_count(uint32_t n);
 int num_sms();
+// Stateless sort of items by (cell, id), used by pic_sort_by_cell.  Defined
+// in rebin.cu.
+struct SortScratch {
+  uint32_t* misc;  // [0] item count, [1] status bits, [2] items kept
+  uint32_t* counts;
+  uint32_t* cursor;
+  uint32_t* block_sums;
+  uint64_t* key_id;
+  uint32_t* key_src;
+};
+size_t sort_scratch_bytes(size_t n, uint32_t C);
+SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C);
+pic_status sort_by_cell_check(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, const uint32_t* perm,
+                              const uint32_t* cell_off, const char* who);
+pic_status sort_by_cell_run(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, uint32_t* perm,
+                            uint32_t* cell_off, const SortScratch& sc, cudaStream_t s);
 // Host-side count of kernel launches (instrumentation).
 void count_launches(int n);
 }  // namespace pic

@@ -134,21 +134,23 @@ pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* blo
 }
 
 // (id, old slot) of every located particle into a free slot of its new cell.
+// The item count is *n_dev; anything else found wrong is latched in *status.
 __global__ void __launch_bounds__(256) scatter_keys_kernel(const uint32_t* __restrict__ cell_new,
                                                            const uint64_t* __restrict__ id, uint32_t* __restrict__ cursor,
                                                            uint64_t* __restrict__ key_id, uint32_t* __restrict__ key_src,
-                                                           uint32_t C, size_t cap, DevCounters* __restrict__ ctr) {
-  const uint32_t n = ctr->n_alive;
+                                                           uint32_t C, size_t cap, const uint32_t* __restrict__ n_dev,
+                                                           unsigned int* __restrict__ status) {
+  const uint32_t n = *n_dev;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t K = cell_new[i];
     if (K == PIC_LOST) continue;
     if (K >= C) {
-      latch_status(ctr, PIC_STATUS_BOUNDS);
+      atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
     }
     const uint32_t slot = atomicAdd(cursor + K, 1u);
     if (slot >= cap) {
-      latch_status(ctr, PIC_STATUS_BOUNDS);
+      atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
     }
     key_id[slot] = id[i];
@@ -158,18 +160,20 @@ __global__ void __launch_bounds__(256) scatter_keys_kernel(const uint32_t* __res
 
 // Warp per cell: the new slot of each element of the cell's segment is the
 // segment start plus the number of elements with a smaller id (ids are
-// unique).  Also publishes the new particle count.
+// unique).  cell_out may be NULL.  When publish_dst is given, block 0 copies
+// *publish_src there (the new particle count of the store).
 __global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
                                                          const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,
                                                          uint32_t* __restrict__ cell_out, uint32_t C, size_t cap,
-                                                         DevCounters* __restrict__ ctr) {
+                                                         unsigned int* __restrict__ status, uint32_t* publish_dst,
+                                                         const uint32_t* publish_src) {
   const int lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  if (blockIdx.x == 0 && threadIdx.x == 0) ctr->n_alive = ctr->n_next;
+  if (publish_dst && blockIdx.x == 0 && threadIdx.x == 0) *publish_dst = *publish_src;
   for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
     const uint32_t beg = cell_off[K], end = cell_off[K + 1];
     if (end > cap || beg > end) {
-      if (lane == 0) latch_status(ctr, PIC_STATUS_BOUNDS);
+      if (lane == 0) atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
     }
     const uint32_t n = end - beg;
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restr
       }
       if (e < n) {
         perm[beg + rank] = key_src[beg + e];
-        cell_out[beg + rank] = K;
+        if (cell_out) cell_out[beg + rank] = K;
       }
     }
   }
@@ -234,9 +238,10 @@ pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
   if (r != PIC_OK) return r;
   const StoreView a = store_view(p, p->cur), b = store_view(p, 1 - p->cur);
   scatter_keys_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(p->cell_new, a.id, p->cursor, p->key_id, p->key_src,
-                                                                     p->C, p->capacity, p->ctr);
+                                                                     p->C, p->capacity, &p->ctr->n_alive, &p->ctr->status);
   rank_by_id_kernel<<<grid_cap((size_t)p->C * 32, 256, 16), 256, 0, s>>>(p->cell_off, p->key_id, p->key_src, p->perm,
-                                                                        b.cell, p->C, p->capacity, p->ctr);
+                                                                        b.cell, p->C, p->capacity, &p->ctr->status,
+                                                                        &p->ctr->n_alive, &p->ctr->n_next);
   gather_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(a, b, p->perm, p->dim, p->ctr);
   count_launches(3);
   PIC_CUDA(cudaGetLastError());
@@ -260,9 +265,97 @@ __global__ void identity_cells_kernel(const uint32_t* __restrict__ cell, uint32_
   }
 }
 
+// Histogram of the cells of n items (entries >= C, lost or not, are skipped;
+// entries other than PIC_LOST that are >= C are flagged).
+__global__ void count_cells_kernel(const uint32_t* __restrict__ cell, uint32_t n, uint32_t C,
+                                   uint32_t* __restrict__ counts, unsigned int* __restrict__ status) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t K = cell[i];
+    if (K < C)
+      atomicAdd(counts + K, 1u);
+    else if (K != PIC_LOST)
+      atomicOr(status, PIC_STATUS_BOUNDS);
+  }
+}
+
+// Scratch of the stateless sort, carved from one block of device memory.
+size_t sort_scratch_bytes(size_t n, uint32_t C) {
+  const size_t nb = scan_block_count(C) + 1;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return up(sizeof(uint32_t) * 4) + 2 * up(sizeof(uint32_t) * (size_t)C) + up(sizeof(uint32_t) * nb) +
+         up(sizeof(uint64_t) * (n ? n : 1)) + up(sizeof(uint32_t) * (n ? n : 1));
+}
+
+SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C) {
+  const size_t nb = scan_block_count(C) + 1;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  char* p = (char*)base;
+  SortScratch sc;
+  sc.misc = (uint32_t*)p;  // [0] n, [1] status, [2] kept
+  p += up(sizeof(uint32_t) * 4);
+  sc.counts = (uint32_t*)p;
+  p += up(sizeof(uint32_t) * (size_t)C);
+  sc.cursor = (uint32_t*)p;
+  p += up(sizeof(uint32_t) * (size_t)C);
+  sc.block_sums = (uint32_t*)p;
+  p += up(sizeof(uint32_t) * nb);
+  sc.key_id = (uint64_t*)p;
+  p += up(sizeof(uint64_t) * (n ? n : 1));
+  sc.key_src = (uint32_t*)p;
+  return sc;
+}
+
+__global__ void sort_init_kernel(uint32_t* misc, uint32_t n) {
+  misc[0] = n;
+  misc[1] = 0;
+  misc[2] = 0;
+}
+
+// Order of n items by (cell, id): counting sort by cell, then rank by id
+// within each cell (the rebin of the store, on caller-owned arrays).
+pic_status sort_by_cell_run(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, uint32_t* perm,
+                            uint32_t* cell_off, const SortScratch& sc, cudaStream_t s) {
+  PIC_CUDA(cudaMemsetAsync(sc.counts, 0, sizeof(uint32_t) * C, s));
+  sort_init_kernel<<<1, 1, 0, s>>>(sc.misc, (uint32_t)n);
+  if (n) count_cells_kernel<<<grid_cap(n, 256, 16), 256, 0, s>>>(cell, (uint32_t)n, C, sc.counts, sc.misc + 1);
+  pic_status r = scan_u32(sc.counts, cell_off, C, sc.block_sums, sc.misc + 2, sc.cursor, s);
+  if (r != PIC_OK) return r;
+  if (n) {
+    scatter_keys_kernel<<<grid_cap(n, 256, 16), 256, 0, s>>>(cell, id, sc.cursor, sc.key_id, sc.key_src, C, n, sc.misc,
+                                                             sc.misc + 1);
+    rank_by_id_kernel<<<grid_cap((size_t)C * 32, 256, 16), 256, 0, s>>>(cell_off, sc.key_id, sc.key_src, perm, nullptr, C,
+                                                                        n, sc.misc + 1, nullptr, nullptr);
+  }
+  count_launches(n ? 4 : 1);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+pic_status sort_by_cell_check(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, const uint32_t* perm,
+                              const uint32_t* cell_off, const char* who) {
+  if (C == 0) return (set_error("%s: n_cells must be >= 1", who), PIC_ERR_ARG);
+  if (n >= 0xFFFFFFF0ull) return (set_error("%s: %zu items exceed the 32-bit index range", who, n), PIC_ERR_ARG);
+  if (!cell_off || (n && (!cell || !id || !perm))) return (set_error("%s: null array", who), PIC_ERR_ARG);
+  return PIC_OK;
+}
+
 }  // namespace pic
 
 using namespace pic;
+
+extern "C" pic_status pic_sort_by_cell(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t n_cells,
+                                       uint32_t* perm, uint32_t* cell_off, void* stream) {
+  pic_status r = sort_by_cell_check(n, cell, id, n_cells, perm, cell_off, "pic_sort_by_cell");
+  if (r != PIC_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  PIC_CUDA(cudaMallocAsync(&scratch, sort_scratch_bytes(n, n_cells), st));
+  r = sort_by_cell_run(n, cell, id, n_cells, perm, cell_off, sort_scratch_layout(scratch, n, n_cells), st);
+  cudaError_t e = cudaFreeAsync(scratch, st);
+  if (r != PIC_OK) return r;
+  if (e != cudaSuccess) return cuda_fail(e, "pic_sort_by_cell: cudaFreeAsync");
+  return PIC_OK;
+}
 
 extern "C" pic_status pic_rebin(pic_particles parts, void* stream) {
   if (!parts) return (set_error("pic_rebin: null handle"), PIC_ERR_ARG);

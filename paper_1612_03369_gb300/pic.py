@@ -37,6 +37,7 @@ SIGNATURES = {
     "pic_locate": (_I, [_P, _P, _P]),
     "pic_rebin": (_I, [_P, _P]),
     "pic_locate_points": (_I, [_P, _SZ, _P, _P, _P, _P, _P]),
+    "pic_sort_by_cell": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
     "pic_interpolate_to_cells": (_I, [_P, _P, _I, _I, _P, _P, _F64, _P]),
     "pic_get_state": (_I, [_P, _P, _P, _P]),
     "pic_get_stats": (_I, [_P, _P, _P, _P, _P]),
@@ -152,6 +153,21 @@ def pic_locate_points(mesh: int, x, hint=None, cell_out=None, xhat_out=None, str
     _check(_lib.pic_locate_points(mesh, n, _ptr(x), _ptr(hint), _ptr(cell_out), _ptr(xhat_out), _stream(stream)),
            "pic_locate_points")
     return cell_out, xhat_out
+
+
+def pic_sort_by_cell(cell, id, n_cells: int, perm=None, cell_off=None, stream=None):
+    """cell: device int32/uint32 [n]; id: device int64 [n].  Returns (perm,
+    cell_off) device int32 tensors; perm[:cell_off[-1]] is the order."""
+    import torch
+
+    n = int(cell.shape[0])
+    if perm is None:
+        perm = torch.empty(max(n, 1), dtype=torch.int32, device=cell.device)
+    if cell_off is None:
+        cell_off = torch.empty(n_cells + 1, dtype=torch.int32, device=cell.device)
+    _check(_lib.pic_sort_by_cell(n, _ptr(cell), _ptr(id), int(n_cells), _ptr(perm), _ptr(cell_off), _stream(stream)),
+           "pic_sort_by_cell")
+    return perm, cell_off
 
 
 def pic_interpolate_to_cells(parts: int, mesh: int, prop: int, avg, count=None, empty_fill: float = 0.0,
