@@ -170,6 +170,25 @@ pic_status pic_locate_points(pic_mesh mesh, size_t n, const double *x, const uin
 pic_status pic_sort_by_cell(size_t n, const uint32_t *cell, const uint64_t *id, uint32_t n_cells, uint32_t *perm,
                             uint32_t *cell_off, void *stream);
 
+/* pic_sort_by_cell without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * where they sort (an application pool that has reserved the device, an
+ * embedder whose allocator owns every byte, or a loop that must not enter the
+ * driver's allocator, which can synchronise or fail).  Arguments, outputs and
+ * results are those of pic_sort_by_cell.
+ *   Limits: n <= 524288 items and n_cells <= 131072 cells; larger requests
+ *   return PIC_ERR_ARG with a message and enqueue nothing.
+ *   Scratch: a fixed 7 MiB device array inside the library, held by every
+ *   GPU that loads the library until the process exits.  The first call on a
+ *   device looks up the array's address on that device (cudaGetSymbolAddress);
+ *   make that first call outside any stream capture.
+ *   All calls share the array, so calls whose work overlaps on the GPU (on
+ *   different streams, or from host threads without ordering) race; order
+ *   them, for example on one stream.
+ * Calls no allocation routine.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_sort_by_cell_noalloc(size_t n, const uint32_t *cell, const uint64_t *id, uint32_t n_cells,
+                                    uint32_t *perm, uint32_t *cell_off, void *stream);
+
 /* Particle -> cell transfer (Sec. 2.7, scheme (ii), arithmetic average):
  * avg[K] = (sum of property `prop` over the particles of K) / n_K, summed in
  * a fixed order (deterministic); count[K] = n_K; empty cells get empty_fill.

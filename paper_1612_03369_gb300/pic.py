@@ -38,6 +38,7 @@ SIGNATURES = {
     "pic_rebin": (_I, [_P, _P]),
     "pic_locate_points": (_I, [_P, _SZ, _P, _P, _P, _P, _P]),
     "pic_sort_by_cell": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
+    "pic_sort_by_cell_noalloc": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
     "pic_interpolate_to_cells": (_I, [_P, _P, _I, _I, _P, _P, _F64, _P]),
     "pic_get_state": (_I, [_P, _P, _P, _P]),
     "pic_get_stats": (_I, [_P, _P, _P, _P, _P]),
@@ -167,6 +168,15 @@ def pic_sort_by_cell(cell, id, n_cells: int, perm=None, cell_off=None, stream=No
         cell_off = torch.empty(n_cells + 1, dtype=torch.int32, device=cell.device)
     _check(_lib.pic_sort_by_cell(n, _ptr(cell), _ptr(id), int(n_cells), _ptr(perm), _ptr(cell_off), _stream(stream)),
            "pic_sort_by_cell")
+    return perm, cell_off
+
+
+def pic_sort_by_cell_noalloc(cell, id, n_cells: int, perm, cell_off, stream=None):
+    """As pic_sort_by_cell, with caller-provided outputs and no device
+    allocation inside the library (scratch in a fixed device array)."""
+    n = int(cell.shape[0])
+    _check(_lib.pic_sort_by_cell_noalloc(n, _ptr(cell), _ptr(id), int(n_cells), _ptr(perm), _ptr(cell_off),
+                                         _stream(stream)), "pic_sort_by_cell_noalloc")
     return perm, cell_off
 
 
