@@ -141,7 +141,8 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(Mesh
               hint[a] = ts[a].hi;
               y[a] = df_add(xd[a], p < TB::S ? df_scale2(k[a], TB::c(p)) : acc[a]);
             }
-            Ks = locate_df<D>(m, y, Ks, hint, ts, iters, flags);
+            // the FP32-basis form needs double-float x-hat only where it is stored
+            Ks = locate_df<D>(m, y, Ks, hint, ts, iters, flags, !F32B || p == TB::S);
             if (Ks == PIC_LOST) {
               ok = false;
               break;

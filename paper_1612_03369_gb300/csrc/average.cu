@@ -5,30 +5,25 @@
 
 namespace pic {
 
-// Warp per cell.  Lane l sums elements l, l+32, ... of the cell's segment in
-// order, then a fixed xor-butterfly combines the 32 partial sums, so the
-// result depends only on the segment (deterministic, no atomics).
+// Thread per cell: the particles of a cell are summed in store order (a left
+// fold, the order of the definition), then divided by their number.  The
+// threads of a warp read neighbouring segments, so every sector fetched from
+// HBM is used by the following iterations through L1.
 __global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __restrict__ cell_off,
                                                            const double* __restrict__ prop, uint32_t C, size_t cap,
                                                            double empty_fill, double* __restrict__ avg,
                                                            uint32_t* __restrict__ count, DevCounters* __restrict__ ctr) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < C; K += gridDim.x * blockDim.x) {
     const uint32_t beg = cell_off[K], end = cell_off[K + 1];
     if (end > cap || beg > end) {
-      if (lane == 0) latch_status(ctr, PIC_STATUS_BOUNDS);
+      latch_status(ctr, PIC_STATUS_BOUNDS);
       continue;
     }
     double s = 0.0;
-    for (uint32_t i = beg + lane; i < end; i += 32) s += prop[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) {
-      const uint32_t n = end - beg;
-      avg[K] = n ? s / (double)n : empty_fill;
-      if (count) count[K] = n;
-    }
+    for (uint32_t i = beg; i < end; ++i) s += prop[i];
+    const uint32_t n = end - beg;
+    avg[K] = n ? s / (double)n : empty_fill;
+    if (count) count[K] = n;
   }
 }
 
@@ -44,8 +39,7 @@ extern "C" pic_status pic_interpolate_to_cells(pic_particles p, pic_mesh mesh, i
     return (set_error("pic_interpolate_to_cells: property %d out of range", prop), PIC_ERR_ARG);
   if (kind != PIC_AVG_ARITHMETIC) return (set_error("pic_interpolate_to_cells: unknown average %d", (int)kind), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t warps_needed = p->C;
-  size_t grid = (warps_needed * 32 + 255) / 256;
+  size_t grid = ((size_t)p->C + 255) / 256;
   const size_t cap = (size_t)num_sms() * 16;
   if (grid > cap) grid = cap;
   cell_average_kernel<<<(int)(grid ? grid : 1), 256, 0, st>>>(p->cell_off, p->props[p->cur] + (size_t)prop * p->capacity,

@@ -23,7 +23,10 @@
 
 namespace pic {
 
-constexpr float kSettle32 = 1e-5f;  // FP32 phase ends when max|update| <= this
+// FP32 phase ends when max|update| <= kSettle32: the iterate is then within
+// ~C*kSettle32^2 + 1e-7 of the root (C ~ 1 for cells jittered by 10%), and
+// the double-float step takes that to ~C*(2e-7)^2 + 6e-8*2e-7 ~ 1e-14.
+constexpr float kSettle32 = 2e-4f;
 constexpr int kMaxIt32 = 8;
 
 template <int D>
@@ -153,9 +156,14 @@ enum : int { kCellOut = 0, kCellIn = 1, kCellFail = -1 };
 
 // Inverse map of y in cell K (fast path).  t32 holds the FP32 start on entry;
 // on return t holds the double-float reference coordinates.
+// With accurate == false (stage points of the FP32-basis form) the FP32
+// phase runs to kSettle32Tight and the double-float step is skipped: x-hat is
+// then good to ~1e-7, which is what an FP32 basis evaluation can use.
+constexpr float kSettle32Tight = 1e-5f;
+
 template <int D>
 __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
-                                             int& iters) {
+                                             int& iters, bool accurate = true) {
   CellBlock<D> cb;
   load_block<D>(m, K, cb);
   df dloc[D];
@@ -181,12 +189,21 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
       mx = fmaxf(mx, fabsf(dt[a]));
     }
     if (!(mx <= 1e3f)) return kCellFail;  // diverging or NaN
-    if (mx <= kSettle32) {
+    if (mx <= (accurate ? kSettle32 : kSettle32Tight)) {
       settled = true;
       break;
     }
   }
   if (!settled) return kCellFail;
+  if (!accurate) {
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      t[a] = df_make(t32[a], 0.f);
+      in = in && (t32[a] >= -(float)kInsideEps) && (t32[a] <= 1.0f + (float)kInsideEps);
+    }
+    return in ? kCellIn : kCellOut;
+  }
   // one Newton step with the double-float residual
   ++iters;
   map32<D>(cb, t32, phi, J);
@@ -195,7 +212,7 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
   float mx = 0.f;
 #pragma unroll
   for (int a = 0; a < D; ++a) mx = fmaxf(mx, fabsf(dt[a]));
-  if (!(mx <= 4.f * kSettle32)) return kCellFail;
+  if (!(mx <= 1e-5f)) return kCellFail;
   bool in = true;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -231,11 +248,11 @@ __device__ __noinline__ int test_cell_fp64(const MeshView& m, uint32_t K, const 
 // Fast path, then the FP64 Newton when the fast path does not settle.
 template <int D>
 __device__ __forceinline__ int test_cell(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
-                                         int& iters, unsigned& flags) {
+                                         int& iters, unsigned& flags, bool accurate = true) {
   float s[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) s[a] = t32[a];
-  const int r = solve_cell_df<D>(m, K, y, t32, t, iters);
+  const int r = solve_cell_df<D>(m, K, y, t32, t, iters, accurate);
   if (r != kCellFail) return r;
   flags |= kFlagFallback64;
 #pragma unroll
@@ -324,7 +341,7 @@ constexpr int kPredictedHops = 2;
 
 template <int D>
 __device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], uint32_t hintK, const float hint_t[D],
-                                              df t[D], int& iters, unsigned& flags) {
+                                              df t[D], int& iters, unsigned& flags, bool accurate = true) {
   if (hintK >= m.C) {
     flags |= kFlagBounds;
     return locate_df_slow<D>(m, y, hintK, t, &iters, &flags);
@@ -335,7 +352,7 @@ __device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], 
   uint32_t K = hintK;
 #pragma unroll 1
   for (int pass = 0; pass <= kPredictedHops; ++pass) {
-    const int r = test_cell<D>(m, K, y, t32, t, iters, flags);
+    const int r = test_cell<D>(m, K, y, t32, t, iters, flags, accurate);
     if (r == kCellIn) return lowest_owner_df<D>(m, y, K, t, iters, flags);
     if (pass == kPredictedHops || r != kCellOut) break;
     flags |= kFlagWalk;
