@@ -62,6 +62,10 @@ def _load():
     lib.orc_advect.argtypes = [P, i64, P, P, P, P, P, C.c_int, f64, C.c_int, C.c_int, P]
     lib.orc_locate_points.argtypes = [P, i64, P, P, P, C.c_int]
     lib.orc_cell_average.argtypes = [i64, i64, P, P, f64, P, P]
+    lib.orc_advect_adjoint.restype = f64
+    lib.orc_advect_adjoint.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P, P]
+    lib.orc_advect_loss.restype = f64
+    lib.orc_advect_loss.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P]
     _lib = lib
     return lib
 
@@ -213,3 +217,19 @@ def cell_average(ncells: int, cell, value, empty_fill: float = 0.0):
     _load().orc_cell_average(int(ncells), int(cell.shape[0]), _p(cell), _p(value), float(empty_fill), _p(avg),
                              _p(cnt))
     return avg, cnt
+
+
+def advect_adjoint(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, targets):
+    """(loss, dL/dU [dim][nnodes]) for L = sum over survivors of |x_final - target|^2;
+    targets [N][dim] in the order of `parts`."""
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    g = np.zeros((mesh.dim, mesh.U.shape[1]))
+    L = _load().orc_advect_adjoint(mesh._h, parts.n, _p(parts.x), _p(parts.xhat), _p(parts.cell), float(dt),
+                                   int(integrator), int(n_steps), _p(t), _p(g))
+    return float(L), g
+
+
+def advect_loss(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, targets) -> float:
+    t = np.ascontiguousarray(targets, dtype=np.float64)
+    return float(_load().orc_advect_loss(mesh._h, parts.n, _p(parts.x), _p(parts.xhat), _p(parts.cell), float(dt),
+                                         int(integrator), int(n_steps), _p(t)))

@@ -572,3 +572,223 @@ void orc_cell_average(int64_t ncells, int64_t N, const int64_t *cell, const doub
   for (int64_t K = 0; K < ncells; ++K) avg[K] = count[K] > 0 ? sum[K] / (double)count[K] : empty_fill;
   free(sum);
 }
+
+/* ------------------------------------ adjoint of the advection (form 3) --- */
+
+/* d l_a / dt for the quadratic Lagrange basis on {0, 1/2, 1}. */
+static double lagrange2_deriv(int a, double t) {
+  if (a == 0) return 4.0 * t - 3.0;
+  if (a == 1) return 4.0 - 8.0 * t;
+  return 4.0 * t - 1.0;
+}
+
+/* Gu[c][j] = d u_c / d xhat_j = sum_i U_i,c d phi-hat_i / d xhat_j in cell K. */
+static void q2_grad_ref(const orc_mesh *m, int64_t K, const double *xhat, double Gu[3][3]) {
+  int d = m->dim;
+  int64_t i, j, k;
+  cell_ijk(m, K, &i, &j, &k);
+  int cmax = d == 3 ? 3 : 1;
+  for (int comp = 0; comp < d; ++comp)
+    for (int jd = 0; jd < d; ++jd) {
+      double s = 0.0;
+      for (int c = 0; c < cmax; ++c)
+        for (int b = 0; b < 3; ++b)
+          for (int a = 0; a < 3; ++a) {
+            int64_t node = (2 * i + a) + m->nq[0] * ((2 * j + b) + m->nq[1] * (2 * k + c));
+            int idx[3] = {a, b, c};
+            double w = 1.0;
+            for (int q = 0; q < d; ++q) w = w * (q == jd ? lagrange2_deriv(idx[q], xhat[q]) : lagrange2(idx[q], xhat[q]));
+            s = s + m->U[(int64_t)comp * m->nnodes + node] * w;
+          }
+      Gu[comp][jd] = s;
+    }
+}
+
+/* Inverse of a 2x2 or 3x3 matrix by the adjugate. */
+static void inverse_small(int d, double A[3][3], double B[3][3]) {
+  if (d == 2) {
+    double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    B[0][0] = A[1][1] / det;
+    B[0][1] = -A[0][1] / det;
+    B[1][0] = -A[1][0] / det;
+    B[1][1] = A[0][0] / det;
+    return;
+  }
+  double c[3][3];
+  c[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  c[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  c[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  c[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+  c[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+  c[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+  c[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+  c[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+  c[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+  double det = A[0][0] * c[0][0] + A[0][1] * c[0][1] + A[0][2] * c[0][2];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) B[r][q] = c[q][r] / det;
+}
+
+/* du/dx at a located point: Gu J^{-1}, J = dPhi_K/dxhat (chain rule through
+ * the inverse map; the cell is held fixed, reading R12). */
+static void velocity_jacobian(const orc_mesh *m, int64_t K, const double *xhat, double G[3][3]) {
+  int d = m->dim;
+  double Gu[3][3] = {{0}}, J[3][3] = {{0}}, Ji[3][3] = {{0}};
+  q2_grad_ref(m, K, xhat, Gu);
+  phi_jacobian(m, K, xhat, J);
+  inverse_small(d, J, Ji);
+  for (int c = 0; c < d; ++c)
+    for (int q = 0; q < d; ++q) {
+      double s = 0.0;
+      for (int j = 0; j < d; ++j) s = s + Gu[c][j] * Ji[j][q];
+      G[c][q] = s;
+    }
+}
+
+/* grad[comp][node] += w[comp] * phi-hat_node(xhat) over the Q2 nodes of K. */
+static void scatter_basis(const orc_mesh *m, int64_t K, const double *xhat, const double *w, double *grad) {
+  int d = m->dim;
+  int64_t i, j, k;
+  cell_ijk(m, K, &i, &j, &k);
+  int cmax = d == 3 ? 3 : 1;
+  for (int c = 0; c < cmax; ++c)
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) {
+        int64_t node = (2 * i + a) + m->nq[0] * ((2 * j + b) + m->nq[1] * (2 * k + c));
+        double phi = lagrange2(a, xhat[0]) * lagrange2(b, xhat[1]);
+        if (d == 3) phi = phi * lagrange2(c, xhat[2]);
+        for (int comp = 0; comp < d; ++comp) grad[(int64_t)comp * m->nnodes + node] += w[comp] * phi;
+      }
+}
+
+/* Loss L = sum over particles alive after n_steps of |x_final - target|^2 and
+ * its gradient with respect to every nodal velocity value, by a reverse sweep
+ * of the Sec. 2.3 integrators (reading R5) recomputed from per-step position
+ * checkpoints.  Particles are independent, so each is swept on its own:
+ *   forward  x_{n+1} = x_n + sum_s b_s k_s,  k_s = dt u(y_s),  y_s = x_n + a_s k_{s-1}
+ *   reverse  lambda_k_s = b_s lambda + a_{s+1} lambda_y_{s+1},
+ *            lambda_y_s = dt G_s^T lambda_k_s  (G_s = du/dx at y_s),
+ *            dL/dU += dt phi-hat(xhat_s) lambda_k_s,
+ *            lambda  <- lambda + sum_s lambda_y_s
+ * Lost particles contribute nothing.  Inputs are particle-major; targets is
+ * [N][dim] in input order; grad is [dim][nnodes] (overwritten).  Returns L. */
+double orc_advect_adjoint(const orc_mesh *m, int64_t N, const double *x, const double *xhat, const int64_t *cell,
+                          double dt, int integrator, int n_steps, const double *targets, double *grad) {
+  int d = m->dim;
+  int S = integrator == 1 ? 1 : (integrator == 2 ? 2 : 4);
+  double a_[4] = {0.0, 0.5, 0.5, 1.0}, b_[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  if (S == 1) b_[0] = 1.0;
+  if (S == 2) {
+    b_[0] = 0.0;
+    b_[1] = 1.0;
+  }
+  for (int64_t q = 0; q < (int64_t)d * m->nnodes; ++q) grad[q] = 0.0;
+  double loss = 0.0;
+  double *xs = (double *)malloc(sizeof(double) * (size_t)(n_steps + 1) * 3);
+  double *ts = (double *)malloc(sizeof(double) * (size_t)(n_steps + 1) * 3);
+  int64_t *ks = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_steps + 1));
+  for (int64_t p = 0; p < N; ++p) {
+    /* forward with checkpoints */
+    orc_particle P;
+    double props_dummy = 0.0;
+    P.id = 0;
+    P.cell = cell[p];
+    P.props = &props_dummy;
+    for (int j = 0; j < d; ++j) {
+      P.x[j] = x[p * d + j];
+      P.xhat[j] = xhat[p * d + j];
+    }
+    int alive = 1;
+    for (int n = 0; n < n_steps; ++n) {
+      for (int j = 0; j < d; ++j) {
+        xs[n * 3 + j] = P.x[j];
+        ts[n * 3 + j] = P.xhat[j];
+      }
+      ks[n] = P.cell;
+      step_particle(m, &P, dt, integrator);
+      if (P.cell < 0) {
+        alive = 0;
+        break;
+      }
+    }
+    if (!alive) continue;
+    double lam[3] = {0, 0, 0};
+    for (int j = 0; j < d; ++j) {
+      double r = P.x[j] - targets[p * d + j];
+      loss = loss + r * r;
+      lam[j] = 2.0 * r;
+    }
+    /* reverse sweep */
+    for (int n = n_steps - 1; n >= 0; --n) {
+      double xn[3], y[4][3], k[4][3], th[4][3], u[3];
+      int64_t K[4];
+      for (int j = 0; j < d; ++j) xn[j] = xs[n * 3 + j];
+      K[0] = ks[n];
+      for (int j = 0; j < d; ++j) {
+        y[0][j] = xn[j];
+        th[0][j] = ts[n * 3 + j];
+      }
+      for (int s = 0; s < S; ++s) {
+        if (s > 0) {
+          for (int j = 0; j < d; ++j) y[s][j] = xn[j] + a_[s] * k[s - 1][j];
+          K[s] = orc_owner(m, y[s], th[s]);
+        }
+        orc_q2_eval(m, K[s], th[s], u);
+        for (int j = 0; j < d; ++j) k[s][j] = dt * u[j];
+      }
+      double lam_x[3], lam_k[4][3], lam_y_next[3] = {0, 0, 0};
+      for (int j = 0; j < d; ++j) lam_x[j] = lam[j];
+      for (int s = S - 1; s >= 0; --s) {
+        double G[3][3] = {{0}}, w[3];
+        for (int j = 0; j < d; ++j) lam_k[s][j] = b_[s] * lam[j] + (s + 1 < S ? a_[s + 1] * lam_y_next[j] : 0.0);
+        velocity_jacobian(m, K[s], th[s], G);
+        double lam_y[3];
+        for (int q = 0; q < d; ++q) {
+          double acc = 0.0;
+          for (int c = 0; c < d; ++c) acc = acc + G[c][q] * lam_k[s][c];
+          lam_y[q] = dt * acc;
+        }
+        for (int j = 0; j < d; ++j) {
+          w[j] = dt * lam_k[s][j];
+          lam_x[j] = lam_x[j] + lam_y[j];
+          lam_y_next[j] = lam_y[j];
+        }
+        scatter_basis(m, K[s], th[s], w, grad);
+      }
+      for (int j = 0; j < d; ++j) lam[j] = lam_x[j];
+    }
+  }
+  free(xs);
+  free(ts);
+  free(ks);
+  return loss;
+}
+
+/* The loss alone (the forward of the adjoint), for finite differences. */
+double orc_advect_loss(const orc_mesh *m, int64_t N, const double *x, const double *xhat, const int64_t *cell,
+                       double dt, int integrator, int n_steps, const double *targets) {
+  int d = m->dim;
+  double loss = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    orc_particle P;
+    double props_dummy = 0.0;
+    P.id = 0;
+    P.cell = cell[p];
+    P.props = &props_dummy;
+    for (int j = 0; j < d; ++j) {
+      P.x[j] = x[p * d + j];
+      P.xhat[j] = xhat[p * d + j];
+    }
+    int alive = 1;
+    for (int n = 0; n < n_steps && alive; ++n) {
+      step_particle(m, &P, dt, integrator);
+      if (P.cell < 0) alive = 0;
+    }
+    if (!alive) continue;
+    for (int j = 0; j < d; ++j) {
+      double r = P.x[j] - targets[p * d + j];
+      loss = loss + r * r;
+    }
+  }
+  return loss;
+}
