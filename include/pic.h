@@ -51,6 +51,7 @@ extern "C" {
 
 typedef struct pic_mesh_s *pic_mesh;           /* owned by the library; pic_destroy_mesh */
 typedef struct pic_particles_s *pic_particles; /* owned by the library; pic_destroy_particles */
+typedef struct pic_tape_s *pic_tape;           /* owned by the library; pic_destroy_tape */
 
 typedef enum {
   PIC_OK = 0,
@@ -132,6 +133,30 @@ pic_status pic_set_properties(pic_particles parts, int prop, const double *value
  * velocity not set), PIC_ERR_CUDA. */
 pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
                       pic_precision precision, int n_steps, void *stream);
+
+/* Adjoint (gradients with respect to the velocity field).
+ * pic_advect_record: n_steps of pic_advect (FP64 form) that also keep, for
+ * every step, the store at the start of the step (x, x-hat, cell) and the
+ * rebin's permutation; the store ends where pic_advect would leave it.
+ * Memory: about (dim*16 + 8) bytes per particle per step plus work arrays.
+ * The mesh and its velocity must not change until the tape is used.
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator, int n_steps,
+                             void *stream, pic_tape *out);
+
+/* Reverse sweep of a recorded run (adjoint of the Sec. 2.3 integrators over
+ * located stages; a stage's cell is held fixed, where u_h is continuous):
+ *   dL_dxfinal [dim][N_final] device: dL/dx of the particles alive at the end,
+ *              in the store order at the end (pic_export order)
+ *   dL_dU      [dim][nnodes] device, overwritten with dL/dU
+ *   dL_dx0     [dim][N_0] device or NULL: dL/dx at the start, store order at
+ *              the start (0 for particles lost during the run)
+ * The stages are recomputed in FP64 from the checkpoints.  Per-stage
+ * contributions are summed per cell in (cell, particle slot, stage) order and
+ * the cells into the nodes in cell order: the result is reproducible bit for
+ * bit.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_tape_adjoint(pic_tape tape, const double *dL_dxfinal, double *dL_dU, double *dL_dx0, void *stream);
+pic_status pic_destroy_tape(pic_tape tape);
 
 /* Re-locate every particle at its current position, using its current cell
  * as the hint (Sec. 2.4), then rebuild the store as pic_rebin does.

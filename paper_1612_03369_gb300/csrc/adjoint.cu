@@ -1,0 +1,548 @@
+// adjoint.cu -- gradients of a function of the final particle positions with
+// respect to the Q2 nodal velocities (the adjoint of the Sec. 2.3 integrators
+// over located stages), for inverse flow reconstruction from tracer
+// endpoints.
+//
+// pic_advect_record advances the store like pic_advect and keeps, for every
+// step, the store at the start of the step (x, x-hat, cell) and the rebin's
+// permutation (new slot -> old slot).  pic_tape_adjoint then sweeps the steps
+// backwards.  For one step, with y_s = x + a_s k_{s-1}, k_s = dt u(y_s),
+// x' = x + sum_s b_s k_s and G_s = du/dx at y_s (cell held fixed):
+//   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
+//   lambda_y_s = dt G_s^T lambda_k_s,       lambda = lambda' + sum_s lambda_y_s
+//   dL/dU_i   += dt phi-hat_i(x-hat_s) lambda_k_s
+// The stages are recomputed in FP64 from the checkpoint.  Each stage leaves a
+// record (stage cell, x-hat_s, dt lambda_k_s) keyed by (slot, stage); the
+// records are sorted by (cell, key), summed per cell in that order, and the
+// cells' sums are added into the nodes in increasing cell order.  No floating-
+// point atomics, so the gradient is bit-for-bit reproducible.
+#include <cstdlib>
+
+#include "locate.cuh"
+#include "pic_internal.cuh"
+
+struct pic_tape_s {
+  pic_particles_s* parts;
+  const pic_mesh_s* mesh;
+  int dim, n_steps, integrator;
+  double dt;
+  size_t cap;
+  uint32_t C;
+  double** x;      // [n_steps] of [dim][cap]
+  float2** xhat;   // [n_steps] of [dim][cap]
+  uint32_t** cell; // [n_steps] of [cap]
+  uint32_t** perm; // [n_steps] of [cap] (new slot -> old slot)
+  uint32_t* n_dev; // [n_steps + 1] particles at the start of each step (and at the end)
+  // reverse-sweep work
+  double* lam[2];      // [dim][cap]
+  uint32_t* rec_cell;  // [4 cap]
+  uint64_t* rec_key;   // [4 cap]
+  double* rec_t;       // [dim][4 cap]
+  double* rec_w;       // [dim][4 cap]
+  uint32_t* rec_perm;  // [4 cap]
+  uint32_t* rec_off;   // [C + 1]
+  void* sort_scratch;
+  double* partial;     // [C][3^dim][dim]
+};
+
+namespace pic {
+
+constexpr int kRecPerParticle = 4;
+
+// u and du/dt at reference coordinates t of cell K (FP64, sum factorisation):
+// Gu[c][j] = d u_c / d t_j.
+template <int D>
+__device__ __forceinline__ void q2_value_grad(const MeshView& m, uint32_t K, const double t[D], double u[D],
+                                              double Gu[D][D]) {
+  int c[3];
+  cell_ijk<D>(m, K, c);
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  double l[D][3], dl[D][3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lagrange2<double>(t[a], l[a]);
+    dl[a][0] = 4.0 * t[a] - 3.0;
+    dl[a][1] = 4.0 - 8.0 * t[a];
+    dl[a][2] = 4.0 * t[a] - 1.0;
+  }
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) {
+    const double* Uc = m.U + comp * m.nnodes + base;
+    double v = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+#pragma unroll
+    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
+      double sv = 0.0, s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double* row = Uc + b * sy + (D == 3 ? cz * sz : 0);
+        const double r0 = __ldg(row), r1 = __ldg(row + 1), r2 = __ldg(row + 2);
+        const double rv = l[0][0] * r0 + l[0][1] * r1 + l[0][2] * r2;
+        const double rd = dl[0][0] * r0 + dl[0][1] * r1 + dl[0][2] * r2;
+        sv += l[1][b] * rv;
+        s0 += l[1][b] * rd;
+        s1 += dl[1][b] * rv;
+      }
+      if constexpr (D == 3) {
+        v += l[2][cz] * sv;
+        g0 += l[2][cz] * s0;
+        g1 += l[2][cz] * s1;
+        g2 += dl[2][cz] * sv;
+      } else {
+        v = sv;
+        g0 = s0;
+        g1 = s1;
+      }
+    }
+    u[comp] = v;
+    Gu[comp][0] = g0;
+    Gu[comp][1] = g1;
+    if constexpr (D == 3) Gu[comp][2] = g2;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void invert(const double J[D][D], double Ji[D][D]) {
+  if constexpr (D == 2) {
+    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    Ji[0][0] = J[1][1] / det;
+    Ji[0][1] = -J[0][1] / det;
+    Ji[1][0] = -J[1][0] / det;
+    Ji[1][1] = J[0][0] / det;
+  } else {
+    double c[3][3];
+    c[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    c[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    c[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    c[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    c[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    c[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    c[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    c[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    c[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Ji[r][q] = c[q][r] / det;
+  }
+}
+
+template <int RK>
+struct AdjTableau;
+template <>
+struct AdjTableau<1> {
+  static constexpr int S = 1;
+  __device__ static double a(int) { return 0.0; }
+  __device__ static double b(int) { return 1.0; }
+};
+template <>
+struct AdjTableau<2> {
+  static constexpr int S = 2;
+  __device__ static double a(int s) { return s == 1 ? 0.5 : 0.0; }
+  __device__ static double b(int s) { return s == 1 ? 1.0 : 0.0; }
+};
+template <>
+struct AdjTableau<4> {
+  static constexpr int S = 4;
+  __device__ static double a(int s) { return s == 3 ? 1.0 : (s == 0 ? 0.0 : 0.5); }
+  __device__ static double b(int s) { return (s == 0 || s == 3) ? 1.0 / 6.0 : 1.0 / 3.0; }
+};
+
+struct TapeStep {
+  const double* x;
+  const float2* xhat;
+  const uint32_t* cell;
+  const uint32_t* perm;
+  const uint32_t* n_next;  // particles after the step
+};
+
+// One reverse step for every particle alive after it (thread per new slot j).
+template <int D, int RK>
+__global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep tp, size_t cap, double dt,
+                                                           const double* __restrict__ lam_in,
+                                                           double* __restrict__ lam_out,
+                                                           uint32_t* __restrict__ rec_cell,
+                                                           uint64_t* __restrict__ rec_key, double* __restrict__ rec_t,
+                                                           double* __restrict__ rec_w, DevCounters* __restrict__ ctr) {
+  using TB = AdjTableau<RK>;
+  constexpr int S = TB::S;
+  const uint32_t n = *tp.n_next;
+  const size_t rcap = kRecPerParticle * cap;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = tp.perm[j];
+    if (i >= cap) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    double x[D], lam[D];
+    double ts[S][D], G[S][D][D];
+    uint32_t Ks[S];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      x[a] = tp.x[a * cap + i];
+      const float2 v = tp.xhat[a * cap + i];
+      ts[0][a] = (double)v.x + (double)v.y;
+      lam[a] = lam_in[a * cap + j];
+    }
+    Ks[0] = tp.cell[i];
+    bool ok = Ks[0] < m.C;
+    double k[D];
+    // forward recomputation of the stages, with du/dx at each
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if (!ok) break;
+      if (s > 0) {
+        double y[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) y[a] = x[a] + TB::a(s) * k[a];
+        int iters = 0;
+        unsigned flags = 0;
+        Ks[s] = locate<D>(m, y, Ks[s - 1], ts[s - 1], ts[s], iters, flags);
+        if (Ks[s] == PIC_LOST) {
+          ok = false;
+          break;
+        }
+      }
+      double u[D], Gu[D][D], J[D][D], Ji[D][D], phi[D];
+      q2_value_grad<D>(m, Ks[s], ts[s], u, Gu);
+      CellGeom<D> g;
+      load_cell<D>(m, Ks[s], g);
+      map_and_jacobian<D>(g, ts[s], phi, J);
+      invert<D>(J, Ji);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        k[c] = dt * u[c];
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          double acc = 0.0;
+#pragma unroll
+          for (int jj = 0; jj < D; ++jj) acc += Gu[c][jj] * Ji[jj][q];
+          G[s][c][q] = acc;
+        }
+      }
+    }
+    if (!ok) {
+      // cannot happen for a particle that survived the step; keep it harmless
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+#pragma unroll
+      for (int s = 0; s < kRecPerParticle; ++s) rec_cell[(size_t)kRecPerParticle * j + s] = PIC_LOST;
+      continue;
+    }
+    // reverse sweep over the stages
+    double lam_x[D], lam_ynext[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lam_x[a] = lam[a];
+      lam_ynext[a] = 0.0;
+    }
+#pragma unroll
+    for (int s = S - 1; s >= 0; --s) {
+      double lk[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) lk[a] = TB::b(s) * lam[a] + (s + 1 < S ? TB::a(s + 1) * lam_ynext[a] : 0.0);
+      const size_t r = (size_t)kRecPerParticle * j + s;
+      rec_cell[r] = Ks[s];
+      rec_key[r] = r;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rec_t[a * rcap + r] = ts[s][a];
+        rec_w[a * rcap + r] = dt * lk[a];
+      }
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc += G[s][c][q] * lk[c];
+        lam_ynext[q] = dt * acc;
+        lam_x[q] += lam_ynext[q];
+      }
+    }
+#pragma unroll
+    for (int s = S; s < kRecPerParticle; ++s) rec_cell[(size_t)kRecPerParticle * j + s] = PIC_LOST;
+#pragma unroll
+    for (int a = 0; a < D; ++a) lam_out[a * cap + i] = lam_x[a];
+  }
+}
+
+// Warp per cell: the records of the cell, in (cell, key) order, summed into
+// the cell's 3^D x D block of nodal gradient entries (lane e owns entries e,
+// e+32, ...).  Every cell is written, empty ones with zeros.
+template <int D>
+__global__ void __launch_bounds__(256) cell_partial_kernel(uint32_t C, const uint32_t* __restrict__ rec_off,
+                                                           const uint32_t* __restrict__ rec_perm,
+                                                           const double* __restrict__ rec_t,
+                                                           const double* __restrict__ rec_w, size_t rcap,
+                                                           double* __restrict__ partial) {
+  constexpr int NN = (D == 3 ? 27 : 9);
+  constexpr int NE = NN * D;
+  constexpr int PER = (NE + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
+    double acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = 0.0;
+    const uint32_t beg = rec_off[K], end = rec_off[K + 1];
+    for (uint32_t e = beg; e < end; ++e) {
+      const uint32_t r = rec_perm[e];
+      double t[D], w[D], l[D][3];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        t[a] = rec_t[a * rcap + r];
+        w[a] = rec_w[a * rcap + r];
+        lagrange2<double>(t[a], l[a]);
+      }
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int ent = lane + 32 * q;
+        if (ent < NE) {
+          const int node = ent / D, comp = ent % D;
+          const int na = node % 3, nb = (node / 3) % 3, nc = node / 9;
+          double phi = l[0][na] * l[1][nb];
+          if constexpr (D == 3) phi *= l[2][nc];
+          acc[q] += w[comp] * phi;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int ent = lane + 32 * q;
+      if (ent < NE) partial[(size_t)K * NE + ent] = acc[q];
+    }
+  }
+}
+
+// Thread per (node, component): add the blocks of the cells that share the
+// node, in increasing cell order.
+template <int D>
+__global__ void node_reduce_kernel(MeshView m, const double* __restrict__ partial, double* __restrict__ grad) {
+  constexpr int NN = (D == 3 ? 27 : 9);
+  const size_t total = (size_t)m.nnodes * D;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+    const size_t comp = q / m.nnodes, node = q % m.nnodes;
+    int I[3] = {(int)(node % m.nq[0]), (int)((node / m.nq[0]) % m.nq[1]), (int)(node / ((size_t)m.nq[0] * m.nq[1]))};
+    // cells touching the node along each axis: node index I = 2i + a, a in {0,1,2}
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (a >= D) continue;
+      if (I[a] % 2 == 1) {
+        lo[a] = hi[a] = I[a] / 2;
+      } else {
+        lo[a] = I[a] / 2 - 1;
+        hi[a] = I[a] / 2;
+        if (lo[a] < 0) lo[a] = 0;
+        if (hi[a] > m.n[a] - 1) hi[a] = m.n[a] - 1;
+      }
+    }
+    double s = 0.0;
+    for (int ck = lo[2]; ck <= hi[2]; ++ck)
+      for (int cj = lo[1]; cj <= hi[1]; ++cj)
+        for (int ci = lo[0]; ci <= hi[0]; ++ci) {
+          const uint32_t K = cell_index<D>(m, ci, cj, ck);
+          const int a = I[0] - 2 * ci, b = I[1] - 2 * cj, c = (D == 3 ? I[2] - 2 * ck : 0);
+          const int local = a + 3 * b + 9 * c;
+          s += partial[((size_t)K * NN + local) * D + comp];
+        }
+    grad[comp * m.nnodes + node] += s;
+  }
+}
+
+// lam[a*cap + j] = src[a*n + j] for j < n (dense caller layout -> strided).
+__global__ void copy_in_kernel(const double* __restrict__ src, double* __restrict__ dst, const uint32_t* n_dev, int dim,
+                               size_t cap) {
+  const uint32_t n = *n_dev;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x)
+    dst[(q / n) * cap + q % n] = src[q];
+}
+
+__global__ void copy_out_kernel(const double* __restrict__ src, double* __restrict__ dst, const uint32_t* n_dev, int dim,
+                                size_t cap) {
+  const uint32_t n = *n_dev;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x)
+    dst[q] = src[(q / n) * cap + q % n];
+}
+
+static int grid_of(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  const size_t cap = (size_t)num_sms() * 16;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+template <int D, int RK>
+static void launch_reverse(pic_tape_s* tp, const MeshView& m, const TapeStep& ts, const double* lin, double* lout,
+                           cudaStream_t st) {
+  reverse_step_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, lin, lout, tp->rec_cell,
+                                                                     tp->rec_key, tp->rec_t, tp->rec_w, tp->parts->ctr);
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" pic_status pic_destroy_tape(pic_tape tp) {
+  if (!tp) return PIC_OK;
+  for (int s = 0; s < tp->n_steps; ++s) {
+    if (tp->x) cudaFree(tp->x[s]);
+    if (tp->xhat) cudaFree(tp->xhat[s]);
+    if (tp->cell) cudaFree(tp->cell[s]);
+    if (tp->perm) cudaFree(tp->perm[s]);
+  }
+  free(tp->x);
+  free(tp->xhat);
+  free(tp->cell);
+  free(tp->perm);
+  cudaFree(tp->n_dev);
+  cudaFree(tp->lam[0]);
+  cudaFree(tp->lam[1]);
+  cudaFree(tp->rec_cell);
+  cudaFree(tp->rec_key);
+  cudaFree(tp->rec_t);
+  cudaFree(tp->rec_w);
+  cudaFree(tp->rec_perm);
+  cudaFree(tp->rec_off);
+  cudaFree(tp->sort_scratch);
+  cudaFree(tp->partial);
+  free(tp);
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                                        int n_steps, void* stream, pic_tape* out) {
+  if (!out) return (set_error("pic_advect_record: out is NULL"), PIC_ERR_ARG);
+  *out = nullptr;
+  if (!parts || !mesh || parts->mesh != mesh) return (set_error("pic_advect_record: bad handles"), PIC_ERR_ARG);
+  if (n_steps < 1) return (set_error("pic_advect_record: n_steps must be >= 1"), PIC_ERR_ARG);
+  if (integrator != PIC_EULER && integrator != PIC_RK2 && integrator != PIC_RK4)
+    return (set_error("pic_advect_record: unknown integrator"), PIC_ERR_ARG);
+  if (!mesh->has_velocity) return (set_error("pic_advect_record: velocity not set"), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  pic_tape_s* tp = (pic_tape_s*)calloc(1, sizeof(pic_tape_s));
+  tp->parts = parts;
+  tp->mesh = mesh;
+  tp->dim = mesh->dim;
+  tp->n_steps = n_steps;
+  tp->integrator = (int)integrator;
+  tp->dt = dt;
+  tp->cap = parts->capacity;
+  tp->C = mesh->C;
+  const size_t cap = tp->cap, d = (size_t)tp->dim, rcap = kRecPerParticle * cap;
+  const int NE = (tp->dim == 3 ? 27 : 9) * tp->dim;
+  tp->x = (double**)calloc(n_steps, sizeof(double*));
+  tp->xhat = (float2**)calloc(n_steps, sizeof(float2*));
+  tp->cell = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
+  tp->perm = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
+  bool ok = tp->x && tp->xhat && tp->cell && tp->perm;
+  for (int s = 0; s < n_steps && ok; ++s) {
+    ok = ok && cudaMalloc(&tp->x[s], sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->xhat[s], sizeof(float2) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->cell[s], sizeof(uint32_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->perm[s], sizeof(uint32_t) * cap) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&tp->n_dev, sizeof(uint32_t) * (n_steps + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->lam[0], sizeof(double) * d * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->lam[1], sizeof(double) * d * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_cell, sizeof(uint32_t) * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_key, sizeof(uint64_t) * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_t, sizeof(double) * d * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_w, sizeof(double) * d * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_perm, sizeof(uint32_t) * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_off, sizeof(uint32_t) * ((size_t)tp->C + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->sort_scratch, sort_scratch_bytes(rcap, tp->C)) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->partial, sizeof(double) * NE * (size_t)tp->C) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pic_destroy_tape(tp);
+    return (set_error("pic_advect_record: device allocation failed"), PIC_ERR_OOM);
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    const int c = parts->cur;
+    cudaError_t e = cudaMemcpyAsync(tp->x[s], parts->x[c], sizeof(double) * d * cap, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tp->xhat[s], parts->xhat[c], sizeof(float2) * d * cap, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tp->cell[s], parts->cell[c], sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(tp->n_dev + s, &parts->ctr->n_alive, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      pic_destroy_tape(tp);
+      return cuda_fail(e, "pic_advect_record: checkpoint");
+    }
+    pic_status r = pic_advect(parts, mesh, dt, integrator, PIC_FP64, 1, stream);
+    if (r != PIC_OK) {
+      pic_destroy_tape(tp);
+      return r;
+    }
+    e = cudaMemcpyAsync(tp->perm[s], parts->perm, sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      pic_destroy_tape(tp);
+      return cuda_fail(e, "pic_advect_record: permutation");
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(tp->n_dev + n_steps, &parts->ctr->n_alive, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) {
+    pic_destroy_tape(tp);
+    return cuda_fail(e, "pic_advect_record: count");
+  }
+  *out = tp;
+  return PIC_OK;
+}
+
+extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, double* dL_dU, double* dL_dx0,
+                                       void* stream) {
+  if (!tp || !dL_dxfinal || !dL_dU) return (set_error("pic_tape_adjoint: null argument"), PIC_ERR_ARG);
+  const pic_mesh_s* mesh = tp->mesh;
+  cudaStream_t st = (cudaStream_t)stream;
+  const MeshView m = mesh_view(mesh);
+  const size_t cap = tp->cap, d = (size_t)tp->dim, rcap = kRecPerParticle * cap;
+  PIC_CUDA(cudaMemsetAsync(dL_dU, 0, sizeof(double) * d * (size_t)mesh->nnodes, st));
+  PIC_CUDA(cudaMemsetAsync(tp->lam[0], 0, sizeof(double) * d * cap, st));
+  copy_in_kernel<<<grid_of(d * cap, 256), 256, 0, st>>>(dL_dxfinal, tp->lam[0], tp->n_dev + tp->n_steps, tp->dim, cap);
+  count_launches(1);
+  int cur = 0;
+  const SortScratch sc = sort_scratch_layout(tp->sort_scratch, rcap, tp->C);
+  for (int s = tp->n_steps - 1; s >= 0; --s) {
+    TapeStep ts;
+    ts.x = tp->x[s];
+    ts.xhat = tp->xhat[s];
+    ts.cell = tp->cell[s];
+    ts.perm = tp->perm[s];
+    ts.n_next = tp->n_dev + s + 1;
+    PIC_CUDA(cudaMemsetAsync(tp->lam[1 - cur], 0, sizeof(double) * d * cap, st));
+    PIC_CUDA(cudaMemsetAsync(tp->rec_cell, 0xFF, sizeof(uint32_t) * rcap, st));
+    const double* lin = tp->lam[cur];
+    double* lout = tp->lam[1 - cur];
+    if (tp->dim == 2) {
+      if (tp->integrator == 1) launch_reverse<2, 1>(tp, m, ts, lin, lout, st);
+      else if (tp->integrator == 2) launch_reverse<2, 2>(tp, m, ts, lin, lout, st);
+      else launch_reverse<2, 4>(tp, m, ts, lin, lout, st);
+    } else {
+      if (tp->integrator == 1) launch_reverse<3, 1>(tp, m, ts, lin, lout, st);
+      else if (tp->integrator == 2) launch_reverse<3, 2>(tp, m, ts, lin, lout, st);
+      else launch_reverse<3, 4>(tp, m, ts, lin, lout, st);
+    }
+    count_launches(1);
+    PIC_CUDA(cudaGetLastError());
+    pic_status r = sort_by_cell_run(rcap, tp->rec_cell, tp->rec_key, tp->C, tp->rec_perm, tp->rec_off, sc, st);
+    if (r != PIC_OK) return r;
+    const int gp = grid_of((size_t)tp->C * 32, 256);
+    const int gn = grid_of(d * (size_t)mesh->nnodes, 256);
+    if (tp->dim == 2) {
+      cell_partial_kernel<2><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, tp->rec_t, tp->rec_w, rcap, tp->partial);
+      node_reduce_kernel<2><<<gn, 256, 0, st>>>(m, tp->partial, dL_dU);
+    } else {
+      cell_partial_kernel<3><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, tp->rec_t, tp->rec_w, rcap, tp->partial);
+      node_reduce_kernel<3><<<gn, 256, 0, st>>>(m, tp->partial, dL_dU);
+    }
+    count_launches(2);
+    PIC_CUDA(cudaGetLastError());
+    cur = 1 - cur;
+  }
+  if (dL_dx0) {
+    copy_out_kernel<<<grid_of(d * cap, 256), 256, 0, st>>>(tp->lam[cur], dL_dx0, tp->n_dev, tp->dim, cap);
+    count_launches(1);
+    PIC_CUDA(cudaGetLastError());
+  }
+  return PIC_OK;
+}

@@ -35,6 +35,9 @@ SIGNATURES = {
     "pic_set_properties": (_I, [_P, _I, _P, _P]),
     "pic_advect": (_I, [_P, _P, _F64, _I, _I, _I, _P]),
     "pic_locate": (_I, [_P, _P, _P]),
+    "pic_advect_record": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
+    "pic_tape_adjoint": (_I, [_P, _P, _P, _P, _P]),
+    "pic_destroy_tape": (_I, [_P]),
     "pic_rebin": (_I, [_P, _P]),
     "pic_locate_points": (_I, [_P, _SZ, _P, _P, _P, _P, _P]),
     "pic_sort_by_cell": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
@@ -131,6 +134,22 @@ def pic_set_properties(h: int, prop: int, values, stream=None):
 def pic_advect(parts: int, mesh: int, dt: float, integrator: int, precision: int, n_steps: int, stream=None):
     _check(_lib.pic_advect(parts, mesh, float(dt), int(integrator), int(precision), int(n_steps), _stream(stream)),
            "pic_advect")
+
+
+def pic_advect_record(parts: int, mesh: int, dt: float, integrator: int, n_steps: int, stream=None) -> int:
+    out = C.c_void_p()
+    _check(_lib.pic_advect_record(parts, mesh, float(dt), int(integrator), int(n_steps), _stream(stream), C.byref(out)),
+           "pic_advect_record")
+    return out.value
+
+
+def pic_tape_adjoint(tape: int, dL_dxfinal, dL_dU, dL_dx0=None, stream=None):
+    _check(_lib.pic_tape_adjoint(tape, _ptr(dL_dxfinal), _ptr(dL_dU), _ptr(dL_dx0), _stream(stream)),
+           "pic_tape_adjoint")
+
+
+def pic_destroy_tape(tape: int):
+    _check(_lib.pic_destroy_tape(tape), "pic_destroy_tape")
 
 
 def pic_locate(parts: int, mesh: int, stream=None):
@@ -343,3 +362,53 @@ class Particles:
             self.close()
         except Exception:
             pass
+
+
+class _Tape:
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        try:
+            if self.h:
+                pic_destroy_tape(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+
+def _advect_function():
+    import torch
+
+    class AdvectFunction(torch.autograd.Function):
+        """x_final, ids = AdvectFunction.apply(U, parts, dt, integrator, n_steps)
+
+        Forward: sets the mesh velocity to U ([dim][nnodes] float64, CUDA) and
+        advances `parts` n_steps with a recorded tape; returns the final
+        positions [dim][N_final] and ids [N_final] in store order.
+        Backward: the adjoint sweep (pic_tape_adjoint) turns dL/dx_final into
+        dL/dU.  The particle store is advanced in place by the forward."""
+
+        @staticmethod
+        def forward(ctx, U, parts, dt, integrator, n_steps):
+            pic_set_velocity_dofs(parts.mesh.h, U.detach().contiguous())
+            tape = _Tape(pic_advect_record(parts.h, parts.mesh.h, dt, integrator, n_steps))
+            st = parts.export()
+            ctx.tape = tape
+            ctx.U_shape = U.shape
+            ctx.mark_non_differentiable(st["id"])
+            return st["x"], st["id"]
+
+        @staticmethod
+        def backward(ctx, grad_x, grad_ids):
+            dU = torch.empty(ctx.U_shape, dtype=torch.float64, device="cuda")
+            pic_tape_adjoint(ctx.tape.h, grad_x.contiguous(), dU)
+            return dU, None, None, None, None
+
+    return AdvectFunction
+
+
+def advect_differentiable(U, parts: "Particles", dt: float, integrator: int = PIC_RK4, n_steps: int = 1):
+    """Differentiable advection: returns (x_final [dim][N], ids [N]); gradients
+    flow from x_final back to the nodal velocities U."""
+    return _advect_function().apply(U, parts, dt, integrator, n_steps)
