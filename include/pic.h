@@ -52,6 +52,7 @@ extern "C" {
 typedef struct pic_mesh_s *pic_mesh;           /* owned by the library; pic_destroy_mesh */
 typedef struct pic_particles_s *pic_particles; /* owned by the library; pic_destroy_particles */
 typedef struct pic_tape_s *pic_tape;           /* owned by the library; pic_destroy_tape */
+typedef struct pic_ensemble_s *pic_ensemble;   /* owned by the library; pic_ensemble_destroy */
 
 typedef enum {
   PIC_OK = 0,
@@ -157,6 +158,59 @@ pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_
  * bit.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_tape_adjoint(pic_tape tape, const double *dL_dxfinal, double *dL_dU, double *dL_dx0, void *stream);
 pic_status pic_destroy_tape(pic_tape tape);
+
+/* Ensemble of independent problems advanced together (the imbalance
+ * discussion of Sec. 2.5 is the motivation: problems of uneven size share
+ * one device).  All problems have the same dimension; problem p uses
+ * meshes[p] (with its velocity set) and its own time step.
+ *   per_cell        [n_problems] pointers to device [n_cells_p] u32 counts, or
+ *                   NULL (then uniform_counts[p] particles in every cell)
+ *   seeds           [n_problems] generator seeds (ids count from 0 per problem)
+ * Problem p is seeded exactly as pic_seed_particles would seed it alone, and
+ * advances with the same per-particle arithmetic: each problem matches its
+ * solo run bit for bit.  Synchronises.  At most 128 problems.
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_ensemble_create(int n_problems, const pic_mesh *meshes, const uint32_t *const *per_cell,
+                               const uint32_t *uniform_counts, const uint64_t *seeds, int n_props, void *stream,
+                               pic_ensemble *out);
+pic_status pic_ensemble_destroy(pic_ensemble ens);
+
+/* Time step of every problem ([n_problems] host doubles).  Synchronises. */
+pic_status pic_ensemble_set_dt(pic_ensemble ens, const double *dts, void *stream);
+
+/* n_steps of every problem (advect with located stages + rebin).
+ *   mode 0: per step, the ensemble advect kernel and the rebin kernels
+ *   mode 1: one persistent cooperative kernel for all n_steps; phases are
+ *           separated by a grid barrier whose waits give up after a time
+ *           limit (then PIC_ERR_TIMEOUT); synchronises to read that status
+ *   use_graph: capture the launches once (per n_steps, mode, integrator and
+ *           buffer parity) into a CUDA graph and replay it
+ * Errors: PIC_ERR_ARG, PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
+pic_status pic_ensemble_run(pic_ensemble ens, pic_integrator integrator, int n_steps, int mode, int use_graph,
+                            void *stream);
+
+/* Autotuner of the persistent kernel: times one step for every (blocks per
+ * SM, tile of particles claimed at a time) candidate on a snapshot of the
+ * store, keeps the fastest for later runs and restores the store.
+ * Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
+pic_status pic_ensemble_tune(pic_ensemble ens, pic_integrator integrator, int *blocks_per_sm, int *tile,
+                             double *best_ms, void *stream);
+
+/* Totals over all problems (as pic_get_state).  Synchronises. */
+pic_status pic_ensemble_state(pic_ensemble ens, size_t *n_alive, size_t *n_lost, uint32_t *status_word);
+
+/* Problem `problem`'s particles in (cell, id) order: x, xhat [dim][n] FP64,
+ * id [n], cell [n] (cells of that problem's mesh); *n_out = n.  Any output
+ * may be NULL; device or host memory; size the arrays from a first call with
+ * all outputs NULL.  Synchronises. */
+pic_status pic_ensemble_export(pic_ensemble ens, int problem, double *x, double *xhat, uint64_t *id, uint32_t *cell,
+                               size_t *n_out, void *stream);
+
+/* Failure-detection self-test of the bounded grid barrier: runs it with one
+ * arrival fewer than it expects, so every wait must run out after timeout_s
+ * (0 < timeout_s <= 10).  Returns PIC_ERR_TIMEOUT when the barrier reported
+ * the timeout (the expected outcome); the context stays usable. */
+pic_status pic_barrier_selftest(double timeout_s, void *stream);
 
 /* Re-locate every particle at its current position, using its current cell
  * as the hint (Sec. 2.4), then rebuild the store as pic_rebin does.

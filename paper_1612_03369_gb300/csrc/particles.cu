@@ -4,55 +4,9 @@
 #include <cstring>
 
 #include "pic_internal.cuh"
+#include "seed.cuh"
 
 namespace pic {
-
-// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a counter-based
-// generator: output n of the stream seeded with `seed` is the finaliser
-// applied to seed + (n + 1) * 0x9E3779B97F4A7C15.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t n) {
-  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__global__ void fill_counts_kernel(const uint32_t* __restrict__ per_cell, uint32_t uniform, uint32_t* __restrict__ counts,
-                                   uint32_t C) {
-  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < C; K += gridDim.x * blockDim.x)
-    counts[K] = per_cell ? per_cell[K] : uniform;
-}
-
-// Remark "local generation" (Sec. 2.2): loop over cells in order and over
-// local coordinates inside each; only the forward map Phi_K is needed.
-template <int D>
-__global__ void seed_kernel(MeshView m, StoreView s, const uint32_t* __restrict__ cell_off, uint64_t seed,
-                            uint64_t first_id) {
-  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
-    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
-    if (end > s.cap) continue;
-    CellGeom<D> g;
-    load_cell<D>(m, K, g);
-    for (uint32_t q = beg; q < end; ++q) {
-      double t[D], x[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        const uint64_t r = splitmix64_at(seed, (uint64_t)q * D + j);
-        t[j] = (double)(r >> 11) * 0x1.0p-53;
-      }
-      map_point<D>(g, t, x);
-#pragma unroll
-      for (int j = 0; j < D; ++j) {
-        s.x[j * s.cap + q] = x[j];
-        const float hi = __double2float_rn(t[j]);
-        s.xhat[j * s.cap + q] = make_float2(hi, __double2float_rn(t[j] - (double)hi));
-      }
-      s.id[q] = first_id + q;
-      s.cell[q] = K;
-      for (int p = 0; p < s.n_props; ++p) s.props[p * s.cap + q] = 0.0;
-    }
-  }
-}
 
 // double-float reference coordinates -> FP64 (export)
 __global__ void xhat_to_double_kernel(const float2* __restrict__ src, double* __restrict__ dst, size_t cap, size_t n,
@@ -96,6 +50,52 @@ extern "C" pic_status pic_destroy_particles(pic_particles p) {
   free(p);
   return PIC_OK;
 }
+
+namespace pic {
+
+// A store of `capacity` particles over C cells (both rebin buffers and the
+// rebin scratch).  Takes ownership of cell_off.  NULL (error message set,
+// cell_off freed) if an allocation fails.
+pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, uint32_t* cell_off) {
+  pic_particles_s* p = (pic_particles_s*)calloc(1, sizeof(pic_particles_s));
+  if (!p) {
+    cudaFree(cell_off);
+    set_error("store_alloc: host allocation failed");
+    return nullptr;
+  }
+  p->dim = dim;
+  p->n_props = n_props;
+  p->C = C;
+  p->capacity = capacity > 0 ? capacity : 1;
+  p->cell_off = cell_off;
+  const size_t cap = p->capacity, d = (size_t)dim;
+  const uint32_t nb = scan_block_count(C);
+  bool ok = true;
+  for (int b = 0; b < 2 && ok; ++b) {
+    ok = ok && cudaMalloc(&p->x[b], sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->xhat[b], sizeof(float2) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->id[b], sizeof(uint64_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->cell[b], sizeof(uint32_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&p->props[b], sizeof(double) * (n_props > 0 ? n_props : 1) * cap) == cudaSuccess;
+  }
+  ok = ok && cudaMalloc(&p->cell_new, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->counts, sizeof(uint32_t) * C) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->cursor, sizeof(uint32_t) * C) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->block_sums, sizeof(uint32_t) * (nb + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->key_id, sizeof(uint64_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->key_src, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->perm, sizeof(uint32_t) * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->ctr, sizeof(DevCounters)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    pic_destroy_particles(p);
+    set_error("store_alloc: device allocation failed (capacity %zu)", cap);
+    return nullptr;
+  }
+  return p;
+}
+
+}  // namespace pic
 
 extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, uint64_t seed,
                                          uint64_t first_id, int n_props, size_t capacity, void* stream,
@@ -167,36 +167,10 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
     return r;
   }
 
-  pic_particles_s* p = (pic_particles_s*)calloc(1, sizeof(pic_particles_s));
-  p->dim = mesh->dim;
-  p->n_props = n_props;
-  p->C = C;
+  pic_particles_s* p = store_alloc(mesh->dim, n_props, C, capacity, off);
+  if (!p) return PIC_ERR_OOM;
   p->mesh = mesh;
-  p->capacity = capacity > 0 ? capacity : 1;
-  p->cell_off = off;
   p->stream = st;
-  const size_t cap = p->capacity, d = (size_t)mesh->dim;
-  bool ok = true;
-  for (int b = 0; b < 2 && ok; ++b) {
-    ok = ok && cudaMalloc(&p->x[b], sizeof(double) * d * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&p->xhat[b], sizeof(float2) * d * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&p->id[b], sizeof(uint64_t) * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&p->cell[b], sizeof(uint32_t) * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&p->props[b], sizeof(double) * (n_props > 0 ? n_props : 1) * cap) == cudaSuccess;
-  }
-  ok = ok && cudaMalloc(&p->cell_new, sizeof(uint32_t) * cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->counts, sizeof(uint32_t) * C) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->cursor, sizeof(uint32_t) * C) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->block_sums, sizeof(uint32_t) * (nb + 1)) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->key_id, sizeof(uint64_t) * cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->key_src, sizeof(uint32_t) * cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->perm, sizeof(uint32_t) * cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->ctr, sizeof(DevCounters)) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    pic_destroy_particles(p);
-    return (set_error("pic_seed_particles: device allocation failed (capacity %zu)", cap), PIC_ERR_OOM);
-  }
   DevCounters h{};
   h.n_alive = (uint32_t)N;
   h.n_next = (uint32_t)N;
@@ -208,9 +182,9 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
   const MeshView m = mesh_view(mesh);
   const int grid = (int)((C + 127) / 128 < 8192 ? (C + 127) / 128 : 8192);
   if (mesh->dim == 2)
-    seed_kernel<2><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id);
+    seed_kernel<2><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id, 0u);
   else
-    seed_kernel<3><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id);
+    seed_kernel<3><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id, 0u);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {

@@ -384,6 +384,8 @@ pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* blo
                     uint32_t* cursor_init, cudaStream_t s);
 uint32_t scan_block_count(uint32_t n);
 int num_sms();
+// Allocate a store (particles.cu); takes ownership of cell_off.
+pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, uint32_t* cell_off);
 // Stateless sort of items by (cell, id), used by pic_sort_by_cell.  Defined
 // in rebin.cu.
 struct SortScratch {

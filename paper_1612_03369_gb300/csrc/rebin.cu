@@ -13,112 +13,30 @@
 // The result is a function of the particle set alone (no dependence on the
 // order the atomics of the scatter were served in).
 #include "pic_internal.cuh"
+#include "rebin.cuh"
 
 namespace pic {
 
 constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
 constexpr uint32_t kScanTile = kScanThreads * kScanItems;
 
 uint32_t scan_block_count(uint32_t n) { return (n + kScanTile - 1) / kScanTile; }
 
-__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  return v;
-}
-
-// Block-wide exclusive scan of one value per thread; returns the exclusive
-// prefix and writes the block total to *total.
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t warp_sums[kScanThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t inc = warp_incl_scan(v);
-  if (lane == 31) warp_sums[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
-    uint32_t si = warp_incl_scan(s);
-    if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = si - s;
-    if (lane == 31) *total = si;
-  }
-  __syncthreads();
-  const uint32_t r = warp_sums[w] + inc - v;
-  __syncthreads();
-  return r;
-}
-
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n,
                                                                    uint32_t* __restrict__ block_sums) {
-  const uint32_t base = blockIdx.x * kScanTile;
-  uint32_t s = 0;
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    const uint32_t i = base + q * kScanThreads + threadIdx.x;
-    if (i < n) s += in[i];
-  }
-  s = __reduce_add_sync(0xffffffffu, s);
-  __shared__ uint32_t ws[kScanThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t t = ws[threadIdx.x];
-    t = __reduce_add_sync(0xffffffffu, t);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = t;
-  }
+  scan_phase_reduce(in, n, block_sums, blockIdx.x, gridDim.x);
 }
 
-// Single block: exclusive scan of the block sums in place.
 __global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __restrict__ sums, uint32_t nb) {
-  __shared__ uint32_t carry_s;
-  __shared__ uint32_t tot;
-  if (threadIdx.x == 0) carry_s = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < nb; base += kScanThreads) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < nb ? sums[i] : 0u;
-    const uint32_t ex = block_excl_scan(v, &tot);
-    const uint32_t carry = carry_s;
-    if (i < nb) sums[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = carry + tot;
-    __syncthreads();
-  }
+  scan_phase_sums(sums, nb);
 }
 
-// Each block scans its tile, adds its block offset, writes out[] (and the
-// cursor copy); the last element writes out[n] and the total.
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t n,
                                                                   const uint32_t* __restrict__ block_sums,
                                                                   uint32_t* __restrict__ out,
                                                                   uint32_t* __restrict__ cursor,
                                                                   uint32_t* __restrict__ total_dev) {
-  __shared__ uint32_t tot;
-  const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-  uint32_t v[kScanItems], s = 0;
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    v[q] = (base + q < n) ? in[base + q] : 0u;
-    s += v[q];
-  }
-  uint32_t ex = block_excl_scan(s, &tot) + block_sums[blockIdx.x];
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    const uint32_t i = base + q;
-    if (i < n) {
-      out[i] = ex;
-      if (cursor) cursor[i] = ex;
-    }
-    ex += v[q];
-    if (i + 1 == n) {
-      out[n] = ex;
-      if (total_dev) *total_dev = ex;
-    }
-  }
+  scan_phase_apply(in, n, block_sums, out, cursor, total_dev, blockIdx.x, gridDim.x);
 }
 
 pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,
@@ -140,80 +58,27 @@ __global__ void __launch_bounds__(256) scatter_keys_kernel(const uint32_t* __res
                                                            uint64_t* __restrict__ key_id, uint32_t* __restrict__ key_src,
                                                            uint32_t C, size_t cap, const uint32_t* __restrict__ n_dev,
                                                            unsigned int* __restrict__ status) {
-  const uint32_t n = *n_dev;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t K = cell_new[i];
-    if (K == PIC_LOST) continue;
-    if (K >= C) {
-      atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
-    }
-    const uint32_t slot = atomicAdd(cursor + K, 1u);
-    if (slot >= cap) {
-      atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
-    }
-    key_id[slot] = id[i];
-    key_src[slot] = i;
-  }
+  scatter_phase(cell_new, id, cursor, key_id, key_src, C, cap, *n_dev, status, blockIdx.x * blockDim.x + threadIdx.x,
+                gridDim.x * blockDim.x);
 }
 
-// Warp per cell: the new slot of each element of the cell's segment is the
-// segment start plus the number of elements with a smaller id (ids are
-// unique).  cell_out may be NULL.  When publish_dst is given, block 0 copies
-// *publish_src there (the new particle count of the store).
+// Warp per cell rank by id.  cell_out may be NULL.  When publish_dst is
+// given, block 0 copies *publish_src there (the new particle count).
 __global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
                                                          const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,
                                                          uint32_t* __restrict__ cell_out, uint32_t C, size_t cap,
                                                          unsigned int* __restrict__ status, uint32_t* publish_dst,
                                                          const uint32_t* publish_src) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   if (publish_dst && blockIdx.x == 0 && threadIdx.x == 0) *publish_dst = *publish_src;
-  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
-    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
-    if (end > cap || beg > end) {
-      if (lane == 0) atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
-    }
-    const uint32_t n = end - beg;
-    for (uint32_t e0 = 0; e0 < n; e0 += 32) {
-      const uint32_t e = e0 + lane;
-      const uint64_t my = e < n ? key_id[beg + e] : ~0ull;
-      uint32_t rank = 0;
-      for (uint32_t f0 = 0; f0 < n; f0 += 32) {
-        const uint64_t other = (f0 + lane < n) ? key_id[beg + f0 + lane] : ~0ull;
-        const uint32_t lim = (n - f0) < 32u ? (n - f0) : 32u;
-        for (uint32_t q = 0; q < lim; ++q) {
-          const uint64_t o = __shfl_sync(0xffffffffu, other, q);
-          rank += (o < my) ? 1u : 0u;
-        }
-      }
-      if (e < n) {
-        perm[beg + rank] = key_src[beg + e];
-        if (cell_out) cell_out[beg + rank] = K;
-      }
-    }
-  }
+  rank_phase(cell_off, key_id, key_src, perm, cell_out, C, cap, status, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+             (gridDim.x * blockDim.x) >> 5);
 }
 
 // Copy every field from the old slot perm[j] to the new slot j.
 __global__ void __launch_bounds__(256) gather_kernel(StoreView src, StoreView dst, const uint32_t* __restrict__ perm, int dim,
                                                      DevCounters* __restrict__ ctr) {
-  const uint32_t n = ctr->n_alive;
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t s = perm[j];
-    if (s >= src.cap) {
-      latch_status(ctr, PIC_STATUS_BOUNDS);
-      continue;
-    }
-    for (int a = 0; a < dim; ++a) {
-      dst.x[a * dst.cap + j] = src.x[a * src.cap + s];
-      dst.xhat[a * dst.cap + j] = src.xhat[a * src.cap + s];
-    }
-    dst.id[j] = src.id[s];
-    for (int q = 0; q < src.n_props; ++q) dst.props[q * dst.cap + j] = src.props[q * src.cap + s];
-  }
+  gather_phase(src, dst, perm, dim, ctr->n_alive, &ctr->status, blockIdx.x * blockDim.x + threadIdx.x,
+               gridDim.x * blockDim.x);
 }
 
 int num_sms() {

@@ -1,0 +1,196 @@
+// rebin.cuh -- the phases of the rebin (Sec. 2.1 store sorted by cell,
+// Sec. 2.4 batched re-insertion) as device functions over a "virtual grid"
+// (block index bid of nb blocks), so that the stand-alone kernels of
+// rebin.cu and the persistent ensemble kernel run the same code.
+//
+//   scan   exclusive prefix sum of per-cell counts in tiles of
+//          blockDim.x * kScanItems cells: tile sums, one block scans them,
+//          then every tile applies its offset
+//   scatter (id, old slot) of each particle to a free slot of its new cell
+//   rank   warp per cell: new slot = segment start + rank of the id
+//   gather every field copied from its old slot to its new slot
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr int kScanItems = 4;
+constexpr int kMaxBlockThreads = 1024;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total to *total (shared memory).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[kMaxBlockThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0u;
+    uint32_t si = warp_incl_scan(s);
+    if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = si - s;
+    if (lane == 31) *total = si;
+  }
+  __syncthreads();
+  const uint32_t r = warp_sums[w] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ uint32_t scan_tile_size() { return blockDim.x * kScanItems; }
+
+// Tile sums of in[0..n) for tiles bid, bid + nb, ...
+__device__ __forceinline__ void scan_phase_reduce(const uint32_t* __restrict__ in, uint32_t n,
+                                                  uint32_t* __restrict__ tile_sums, uint32_t bid, uint32_t nb) {
+  __shared__ uint32_t tot;
+  const uint32_t T = scan_tile_size(), ntiles = (n + T - 1) / T;
+  for (uint32_t t = bid; t < ntiles; t += nb) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      const uint32_t i = t * T + q * blockDim.x + threadIdx.x;
+      if (i < n) s += in[i];
+    }
+    (void)block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) tile_sums[t] = tot;
+    __syncthreads();
+  }
+}
+
+// One block: exclusive scan of the tile sums in place.
+__device__ __forceinline__ void scan_phase_sums(uint32_t* __restrict__ sums, uint32_t ntiles) {
+  __shared__ uint32_t carry_s, tot;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < ntiles ? sums[i] : 0u;
+    const uint32_t ex = block_excl_scan(v, &tot);
+    const uint32_t carry = carry_s;
+    if (i < ntiles) sums[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+  }
+}
+
+// out[i] = exclusive prefix of in (and cursor[i] when given); out[n] and
+// *total_dev get the total.
+__device__ __forceinline__ void scan_phase_apply(const uint32_t* __restrict__ in, uint32_t n,
+                                                 const uint32_t* __restrict__ tile_sums, uint32_t* __restrict__ out,
+                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ total_dev,
+                                                 uint32_t bid, uint32_t nb) {
+  __shared__ uint32_t tot;
+  const uint32_t T = scan_tile_size(), ntiles = (n + T - 1) / T;
+  for (uint32_t t = bid; t < ntiles; t += nb) {
+    const uint32_t base = t * T + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      v[q] = (base + q < n) ? in[base + q] : 0u;
+      s += v[q];
+    }
+    uint32_t ex = block_excl_scan(s, &tot) + tile_sums[t];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+      const uint32_t i = base + q;
+      if (i < n) {
+        out[i] = ex;
+        if (cursor) cursor[i] = ex;
+      }
+      ex += v[q];
+      if (i + 1 == n) {
+        out[n] = ex;
+        if (total_dev) *total_dev = ex;
+      }
+    }
+  }
+}
+
+// (id, old slot) of every located particle i < n into a free slot of its new cell.
+__device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_new, const uint64_t* __restrict__ id,
+                                              uint32_t* __restrict__ cursor, uint64_t* __restrict__ key_id,
+                                              uint32_t* __restrict__ key_src, uint32_t C, size_t cap, uint32_t n,
+                                              unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
+  for (uint32_t i = first; i < n; i += stride) {
+    const uint32_t K = cell_new[i];
+    if (K == PIC_LOST) continue;
+    if (K >= C) {
+      atomicOr(status, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    const uint32_t slot = atomicAdd(cursor + K, 1u);
+    if (slot >= cap) {
+      atomicOr(status, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    key_id[slot] = id[i];
+    key_src[slot] = i;
+  }
+}
+
+// Warp per cell (warp w of nw): new slot = segment start + number of smaller
+// ids in the segment (ids are unique within a cell).
+__device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
+                                           const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,
+                                           uint32_t* __restrict__ cell_out, uint32_t C, size_t cap,
+                                           unsigned int* __restrict__ status, uint32_t w, uint32_t nw) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t K = w; K < C; K += nw) {
+    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
+    if (end > cap || beg > end) {
+      if (lane == 0) atomicOr(status, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    const uint32_t n = end - beg;
+    for (uint32_t e0 = 0; e0 < n; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const uint64_t my = e < n ? key_id[beg + e] : ~0ull;
+      uint32_t rank = 0;
+      for (uint32_t f0 = 0; f0 < n; f0 += 32) {
+        const uint64_t other = (f0 + lane < n) ? key_id[beg + f0 + lane] : ~0ull;
+        const uint32_t lim = (n - f0) < 32u ? (n - f0) : 32u;
+        for (uint32_t q = 0; q < lim; ++q) {
+          const uint64_t o = __shfl_sync(0xffffffffu, other, q);
+          rank += (o < my) ? 1u : 0u;
+        }
+      }
+      if (e < n) {
+        perm[beg + rank] = key_src[beg + e];
+        if (cell_out) cell_out[beg + rank] = K;
+      }
+    }
+  }
+}
+
+// Copy every field from old slot perm[j] to new slot j, j < n.
+__device__ __forceinline__ void gather_phase(const StoreView& src, const StoreView& dst,
+                                             const uint32_t* __restrict__ perm, int dim, uint32_t n,
+                                             unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
+  for (uint32_t j = first; j < n; j += stride) {
+    const uint32_t s = perm[j];
+    if (s >= src.cap) {
+      atomicOr(status, PIC_STATUS_BOUNDS);
+      continue;
+    }
+    for (int a = 0; a < dim; ++a) {
+      dst.x[a * dst.cap + j] = src.x[a * src.cap + s];
+      dst.xhat[a * dst.cap + j] = src.xhat[a * src.cap + s];
+    }
+    dst.id[j] = src.id[s];
+    for (int q = 0; q < src.n_props; ++q) dst.props[q * dst.cap + j] = src.props[q * src.cap + s];
+  }
+}
+
+}  // namespace pic

@@ -51,6 +51,14 @@ SIGNATURES = {
     "pic_timing_enable": (_I, [_P, _I]),
     "pic_timing_read": (_I, [_P, _P, _P, _P]),
     "pic_kernel_launches": (_U64, []),
+    "pic_ensemble_create": (_I, [_I, _P, _P, _P, _P, _I, _P, _P]),
+    "pic_ensemble_destroy": (_I, [_P]),
+    "pic_ensemble_set_dt": (_I, [_P, _P, _P]),
+    "pic_ensemble_run": (_I, [_P, _I, _I, _I, _I, _P]),
+    "pic_ensemble_tune": (_I, [_P, _I, _P, _P, _P, _P]),
+    "pic_ensemble_state": (_I, [_P, _P, _P, _P]),
+    "pic_ensemble_export": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "pic_barrier_selftest": (_I, [_F64, _P]),
     "pic_last_error": (C.c_char_p, []),
     "pic_version": (C.c_char_p, []),
 }
@@ -412,3 +420,94 @@ def advect_differentiable(U, parts: "Particles", dt: float, integrator: int = PI
     """Differentiable advection: returns (x_final [dim][N], ids [N]); gradients
     flow from x_final back to the nodal velocities U."""
     return _advect_function().apply(U, parts, dt, integrator, n_steps)
+
+
+# ------------------------------------------------------------- ensemble --
+
+
+def pic_barrier_selftest(timeout_s: float, stream=None) -> int:
+    """Returns the status (PIC_ERR_TIMEOUT is the expected outcome)."""
+    return int(_lib.pic_barrier_selftest(float(timeout_s), _stream(stream)))
+
+
+class Ensemble:
+    """Independent problems advanced together (pic_ensemble_*)."""
+
+    def __init__(self, meshes, per_cell=None, uniform_counts=None, seeds=None, n_props=0, stream=None):
+        import torch
+
+        self.meshes = list(meshes)
+        self.P = len(self.meshes)
+        self.dim = self.meshes[0].dim
+        hs = (C.c_void_p * self.P)(*[m.h for m in self.meshes])
+        self._pc_tensors = []
+        pc_arr = None
+        if per_cell is not None:
+            ptrs = []
+            for a in per_cell:
+                if a is None:
+                    ptrs.append(None)
+                else:
+                    t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.uint32).view(np.int32), device="cuda")
+                    self._pc_tensors.append(t)
+                    ptrs.append(t.data_ptr())
+            pc_arr = (C.c_void_p * self.P)(*ptrs)
+        uc = None
+        if uniform_counts is not None:
+            uc = (C.c_uint32 * self.P)(*[int(v) for v in uniform_counts])
+        sd = (C.c_uint64 * self.P)(*[int(v) & (2**64 - 1) for v in (seeds or [0] * self.P)])
+        out = C.c_void_p()
+        _check(_lib.pic_ensemble_create(self.P, hs, pc_arr, uc, sd, int(n_props), _stream(stream), C.byref(out)),
+               "pic_ensemble_create")
+        self.h = out.value
+
+    def set_dt(self, dts, stream=None):
+        a = (C.c_double * self.P)(*[float(v) for v in dts])
+        _check(_lib.pic_ensemble_set_dt(self.h, a, _stream(stream)), "pic_ensemble_set_dt")
+
+    def run(self, integrator=PIC_RK4, n_steps=1, mode=1, use_graph=True, stream=None):
+        _check(_lib.pic_ensemble_run(self.h, int(integrator), int(n_steps), int(mode), int(bool(use_graph)),
+                                     _stream(stream)), "pic_ensemble_run")
+
+    def tune(self, integrator=PIC_RK4, stream=None):
+        b, t, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(_lib.pic_ensemble_tune(self.h, int(integrator), C.byref(b), C.byref(t), C.byref(ms), _stream(stream)),
+               "pic_ensemble_tune")
+        return int(b.value), int(t.value), float(ms.value)
+
+    def state(self):
+        na, nl, st = C.c_size_t(), C.c_size_t(), C.c_uint32()
+        _check(_lib.pic_ensemble_state(self.h, C.byref(na), C.byref(nl), C.byref(st)), "pic_ensemble_state")
+        return int(na.value), int(nl.value), int(st.value)
+
+    def export(self, problem, stream=None):
+        import torch
+
+        n = C.c_size_t()
+        _check(_lib.pic_ensemble_export(self.h, int(problem), None, None, None, None, C.byref(n), _stream(stream)),
+               "pic_ensemble_export")
+        n = int(n.value)
+        x = torch.empty((self.dim, max(n, 1)), dtype=torch.float64, device="cuda")
+        xh = torch.empty((self.dim, max(n, 1)), dtype=torch.float64, device="cuda")
+        ids = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        cell = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        m = C.c_size_t()
+        _check(_lib.pic_ensemble_export(self.h, int(problem), _ptr(x), _ptr(xh), _ptr(ids), _ptr(cell), C.byref(m),
+                                        _stream(stream)), "pic_ensemble_export")
+        torch.cuda.synchronize()
+        return {"x": x[:, :n], "xhat": xh[:, :n], "id": ids[:n], "cell": cell[:n]}
+
+    def close(self):
+        if getattr(self, "h", None):
+            pic_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pic_ensemble_destroy(h):
+    _check(_lib.pic_ensemble_destroy(h), "pic_ensemble_destroy")
