@@ -10,7 +10,12 @@ particle (advect with located stages, final locate, rebin into the
 so no L2 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config c2|c1|c3]
+                  [--config c2|c1|c3|c4|c5]
+
+c3 is the precision form (FP32 basis) at 128^3; c4 times the adjoint
+(recorded forward + reverse sweep) at 32^3 x 32 per cell over 20 steps; c5
+times the 64-problem ensemble (10 steps per persistent graph launch).  The
+driver's default is c2.
 
 Under torchrun (N > 1) every rank advances its own replica of the workload
 (independent problems, no data-path collective: weak scaling); the time is
@@ -255,6 +260,125 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+def run_adjoint(args):
+    """c4: the adjoint (pic_advect_record + pic_tape_adjoint) against the
+    plain FP64-form forward of the same run, on one GPU."""
+    import torch
+    from paper_1612_03369_gb300 import pic as P
+
+    wl = W.c4()
+    steps = wl.n_steps
+    mesh = P.Mesh(wl.n, wl.X, wl.U)
+    N = wl.n_particles
+
+    def fresh():
+        return P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fwd_ms, adj_ms, rec_ms = [], [], []
+    for rep in range(args.warmup + args.steps):
+        p = fresh()
+        torch.cuda.synchronize()
+        e0.record()
+        p.advect(wl.dt, 4, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        f = e0.elapsed_time(e1)
+        p.close()
+        p = fresh()
+        torch.cuda.synchronize()
+        e0.record()
+        tape = P.pic_advect_record(p.h, mesh.h, wl.dt, 4, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        r = e0.elapsed_time(e1)
+        st = p.export()
+        lam = 2.0 * (st["x"] - 0.5).contiguous()
+        dU = torch.empty((3, wl.U.shape[1]), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0.record()
+        P.pic_tape_adjoint(tape, lam, dU)
+        e1.record()
+        torch.cuda.synchronize()
+        a = e0.elapsed_time(e1)
+        P.pic_destroy_tape(tape)
+        p.close()
+        if rep >= args.warmup:
+            fwd_ms.append(f)
+            rec_ms.append(r)
+            adj_ms.append(a)
+    f, r, a = statistics.median(fwd_ms), statistics.median(rec_ms), statistics.median(adj_ms)
+    psteps = N * steps
+    return {
+        "metric": "adjoint particle-steps/s (recorded forward + reverse sweep), 3D Q2 mesh",
+        "value": psteps / ((r + a) / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (r + a), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "particles": N, "time_steps": steps, "integrator": "RK4",
+                   "one_benchmark_step": "one full gradient: %d recorded steps + reverse sweep" % steps},
+        "forward_plain_ms": f, "record_ms": r, "reverse_ms": a,
+        "forward_plain_particle_steps_per_s": psteps / (f / 1e3),
+        "accuracy": "dL/dU within 1e-11 of max|dL/dU| of the oracle's reverse mode (tests/test_gpu_adjoint.py)",
+    }
+
+
+def run_ensemble(args):
+    """c5: 64 problems advanced 10 steps per launch of the persistent kernel
+    (replayed graph), against the per-step graph and against the problems
+    advanced one after another with pic_advect."""
+    import torch
+    from paper_1612_03369_gb300 import pic as P
+
+    wls = W.c5()
+    steps = wls[0].n_steps
+    meshes = [P.Mesh(w.n, w.X, w.U) for w in wls]
+    ens = P.Ensemble(meshes, per_cell=[w.per_cell for w in wls], seeds=[w.pseed for w in wls])
+    ens.set_dt([w.dt for w in wls])
+    tuned = ens.tune(4)
+    N = sum(w.n_particles for w in wls)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(mode):
+        for _ in range(args.warmup):
+            ens.run(4, steps, mode=mode, use_graph=True)
+        torch.cuda.synchronize()
+        n0 = ens.state()[0]
+        e0.record()
+        for _ in range(args.steps):
+            ens.run(4, steps, mode=mode, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, n0
+
+    persist_ms, n_alive = timed(1)
+    multi_ms, _ = timed(0)
+    # plain: the problems one after another
+    solos = [P.Particles(m, per_cell=w.per_cell, seed=w.pseed) for m, w in zip(meshes, wls)]
+    for _ in range(args.warmup):
+        for p, w in zip(solos, wls):
+            p.advect(w.dt, 4, steps)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for p, w in zip(solos, wls):
+            p.advect(w.dt, 4, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    solo_ms = e0.elapsed_time(e1) / args.steps
+    return {
+        "metric": "ensemble RK4 particle-steps/s (advect+locate+rebin), 64 2D Q2 problems, one persistent launch",
+        "value": n_alive * steps / (persist_ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": persist_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c5_ensemble_64", "problems": len(wls), "particles": N,
+                   "sides": [w.n[0] for w in wls], "time_steps_per_launch": steps,
+                   "one_benchmark_step": "%d time steps of every problem" % steps},
+        "autotuned": {"blocks_per_sm": tuned[0], "tile": tuned[1], "one_step_ms": tuned[2]},
+        "per_step_graph_particle_steps_per_s": n_alive * steps / (multi_ms / 1e3),
+        "sequential_solo_particle_steps_per_s": n_alive * steps / (solo_ms / 1e3),
+    }
+
+
 def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
     """The oracle as it stands, single thread, on a bounded random sample of
     the workload's particles advanced one time step at a time."""
@@ -318,7 +442,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -331,6 +455,10 @@ def main():
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res), flush=True)
+        return
+    if args.config in ("c4", "c5"):
+        res = run_adjoint(args) if args.config == "c4" else run_ensemble(args)
+        print(json.dumps(res), flush=True)
         return
     if world > 1:
         import torch
