@@ -302,6 +302,12 @@ __device__ __noinline__ uint32_t lowest_owner_df_slow(const MeshView& m, const d
 template <int D>
 __device__ __forceinline__ uint32_t lowest_owner_df(const MeshView& m, const df y[D], uint32_t found, df t[D],
                                                     int& iters, unsigned& flags) {
+  // band test first (cheap); the cell's (i,j,k), which needs integer
+  // divisions, only when some coordinate is near a facet
+  bool near = false;
+#pragma unroll
+  for (int a = 0; a < D; ++a) near = near || t[a].hi < (float)kTieBand || t[a].hi > 1.0f - (float)kTieBand;
+  if (!near) return found;
   int c[3];
   cell_ijk<D>(m, found, c);
   bool any = false;
@@ -392,10 +398,8 @@ __device__ __forceinline__ void lagrange2_df(df t, df l[3]) {
 
 template <int D>
 __device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
-  int c[3];
-  cell_ijk<D>(m, K, c);
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
   df L0[3], L1[3], L2[3];
   lagrange2_df(t[0], L0);
   lagrange2_df(t[1], L1);
@@ -456,10 +460,8 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const 
 // FP32 basis and contraction (precision form): only the high parts.
 template <int D>
 __device__ __forceinline__ void q2_eval_f32(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
-  int c[3];
-  cell_ijk<D>(m, K, c);
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+  const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
   float L[D][3];
 #pragma unroll
   for (int a = 0; a < D; ++a) lagrange2<float>(t[a].hi, L[a]);

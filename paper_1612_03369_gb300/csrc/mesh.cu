@@ -74,6 +74,16 @@ __global__ void cell_block_kernel(MeshView m, float2* __restrict__ blk) {
   }
 }
 
+// Index of node (2i, 2j, 2k), the first Q2 node of cell (i, j, k).
+template <int D>
+__global__ void cell_qbase_kernel(MeshView m, uint32_t* __restrict__ qbase) {
+  for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
+    int c[3];
+    cell_ijk<D>(m, K, c);
+    qbase[K] = (uint32_t)(2 * (int64_t)c[0] + (int64_t)m.nq[0] * (2 * c[1] + (D == 3 ? (int64_t)m.nq[1] * 2 * c[2] : 0)));
+  }
+}
+
 // U [comp][node] FP64 -> U2 [node][comp] double-float.
 __global__ void to_df_nodes_kernel(const double* __restrict__ U, float2* __restrict__ U2, int dim, size_t nnodes) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nnodes * dim; i += (size_t)gridDim.x * blockDim.x) {
@@ -104,7 +114,7 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
     nv *= (uint64_t)n_cells[a] + 1;
     nq *= 2 * (uint64_t)n_cells[a] + 1;
   }
-  if (C >= (1ull << 31) || nq >= (1ull << 40))
+  if (C >= (1ull << 31) || nq >= (1ull << 32))
     return (set_error("pic_create_mesh: mesh too large (%llu cells)", (unsigned long long)C), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   pic_mesh_s* m = (pic_mesh_s*)calloc(1, sizeof(pic_mesh_s));
@@ -125,7 +135,8 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   const size_t blk_f4 = dim == 3 ? 12 : 4;
   if (cudaMalloc(&m->X, sizeof(double) * dim * nv) != cudaSuccess ||
       cudaMalloc(&m->bbox, sizeof(double) * 6 * C) != cudaSuccess ||
-      cudaMalloc(&m->blk, sizeof(float4) * blk_f4 * C) != cudaSuccess) {
+      cudaMalloc(&m->blk, sizeof(float4) * blk_f4 * C) != cudaSuccess ||
+      cudaMalloc(&m->qbase, sizeof(uint32_t) * C) != cudaSuccess) {
     cudaGetLastError();
     set_error("pic_create_mesh: device allocation failed");
     return fail(PIC_ERR_OOM);
@@ -163,9 +174,11 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   if (dim == 2) {
     cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox);
     cell_block_kernel<2><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+    cell_qbase_kernel<2><<<grid, 256, 0, st>>>(mv, m->qbase);
   } else {
     cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox);
     cell_block_kernel<3><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+    cell_qbase_kernel<3><<<grid, 256, 0, st>>>(mv, m->qbase);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -181,6 +194,7 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->U32);
   cudaFree(m->bbox);
   cudaFree(m->blk);
+  cudaFree(m->qbase);
   cudaFree(m->U2);
   free(m);
   return PIC_OK;

@@ -62,6 +62,7 @@ struct pic_mesh_s {
   float* U32;    // [dim][nnodes] FP32 copy for the FP32-basis form
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
+  uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
   float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo)
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
@@ -121,6 +122,7 @@ struct MeshView {
   const float* U32;
   const double* bbox;
   const float4* blk;
+  const uint32_t* qbase;
   const float2* U2;
   double dlo[3], dhi[3];
 };
@@ -142,6 +144,7 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.U32 = m->U32;
   v.bbox = m->bbox;
   v.blk = m->blk;
+  v.qbase = m->qbase;
   v.U2 = m->U2;
   return v;
 }
