@@ -43,6 +43,7 @@ def _load():
     lib.orc_mesh_create.restype = P
     lib.orc_mesh_create.argtypes = [C.c_int, P, P]
     lib.orc_mesh_set_velocity.argtypes = [P, P]
+    lib.orc_mesh_set_velocity_next.argtypes = [P, P]
     lib.orc_mesh_destroy.argtypes = [P]
     lib.orc_phi.argtypes = [P, i64, P, P]
     lib.orc_newton.restype = C.c_int
@@ -62,6 +63,7 @@ def _load():
     lib.orc_advect.argtypes = [P, i64, P, P, P, P, P, C.c_int, f64, C.c_int, C.c_int, P]
     lib.orc_locate_points.argtypes = [P, i64, P, P, P, C.c_int]
     lib.orc_cell_average.argtypes = [i64, i64, P, P, f64, P, P]
+    lib.orc_cell_average_kind.argtypes = [i64, i64, P, P, C.c_int, f64, P, P]
     lib.orc_advect_adjoint.restype = f64
     lib.orc_advect_adjoint.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P, P]
     lib.orc_advect_loss.restype = f64
@@ -93,6 +95,16 @@ class Mesh:
         self.U = np.ascontiguousarray(U, dtype=np.float64)
         assert self.U.shape == (self.dim, int(np.prod([2 * v + 1 for v in self.n])))
         _load().orc_mesh_set_velocity(self._h, _p(self.U))
+
+    def set_velocity_next(self, Un=None):
+        """Field at the end of every step (time interpolation), or None."""
+        if Un is None:
+            self.Unext = None
+            _load().orc_mesh_set_velocity_next(self._h, None)
+            return
+        self.Unext = np.ascontiguousarray(Un, dtype=np.float64)
+        assert self.Unext.shape == self.U.shape
+        _load().orc_mesh_set_velocity_next(self._h, _p(self.Unext))
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -208,14 +220,15 @@ def advect(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: in
     return out
 
 
-def cell_average(ncells: int, cell, value, empty_fill: float = 0.0):
-    """Arithmetic per-cell average, left fold in store order (Sec. 2.7 (ii))."""
+def cell_average(ncells: int, cell, value, empty_fill: float = 0.0, kind: int = 0):
+    """Per-cell average (Sec. 2.7 (ii)): kind 0 arithmetic, 1 geometric,
+    2 harmonic; left folds in store order."""
     cell = np.ascontiguousarray(cell, dtype=np.int64)
     value = np.ascontiguousarray(value, dtype=np.float64)
     avg = np.zeros(ncells)
     cnt = np.zeros(ncells, dtype=np.int64)
-    _load().orc_cell_average(int(ncells), int(cell.shape[0]), _p(cell), _p(value), float(empty_fill), _p(avg),
-                             _p(cnt))
+    _load().orc_cell_average_kind(int(ncells), int(cell.shape[0]), _p(cell), _p(value), int(kind), float(empty_fill),
+                                  _p(avg), _p(cnt))
     return avg, cnt
 
 

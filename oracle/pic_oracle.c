@@ -39,6 +39,7 @@ typedef struct {
   int64_t ncells, nverts, nnodes;
   double *X; /* [dim][nverts] */
   double *U; /* [dim][nnodes], NULL until set */
+  double *Unext; /* [dim][nnodes] velocity at the end of the step, or NULL (steady) */
   /* exact bounding-box filter for the owner search: a cell can only contain
    * x if its (padded) bounding box contains x, so testing only those cells is
    * the brute-force search of Sec. 2.2 (prescribed positions) with a filter
@@ -103,10 +104,21 @@ void orc_mesh_set_velocity(orc_mesh *m, const double *U) {
   memcpy(m->U, U, sizeof(double) * m->dim * m->nnodes);
 }
 
+/* Velocity at the end of every time step (Sec. 2.3, eq. position-ode-approx:
+ * u-tilde_h interpolates u_h^n and u_h^{n+1} in time); NULL = steady field. */
+void orc_mesh_set_velocity_next(orc_mesh *m, const double *Un) {
+  free(m->Unext);
+  m->Unext = NULL;
+  if (!Un) return;
+  m->Unext = (double *)malloc(sizeof(double) * m->dim * m->nnodes);
+  memcpy(m->Unext, Un, sizeof(double) * m->dim * m->nnodes);
+}
+
 void orc_mesh_destroy(orc_mesh *m) {
   if (!m) return;
   free(m->X);
   free(m->U);
+  free(m->Unext);
   free(m->bb_lo);
   free(m->bb_hi);
   free(m->bin_start);
@@ -431,14 +443,29 @@ int64_t orc_seed(const orc_mesh *m, const uint32_t *per_cell, uint32_t uniform_c
 
 /* -------------------------------------------- advection (Sec. 2.3/2.4) --- */
 
+/* u-tilde_h at stage time t^n + theta dt in cell K (R6): linear in time
+ * between the two nodal fields, (1 - theta) u_h^n + theta u_h^{n+1}; the
+ * steady field when no second field is set. */
+static void velocity_at(const orc_mesh *m, int64_t K, const double *xhat, double theta, double *u) {
+  orc_q2_eval(m, K, xhat, u);
+  if (!m->Unext) return;
+  double un[3] = {0, 0, 0};
+  orc_mesh *mm = (orc_mesh *)m;
+  double *keep = mm->U;
+  mm->U = mm->Unext;
+  orc_q2_eval(mm, K, xhat, un);
+  mm->U = keep;
+  for (int j = 0; j < m->dim; ++j) u[j] = (1.0 - theta) * u[j] + theta * un[j];
+}
+
 /* Velocity at a stage point: locate it (R7: every sub-step is followed by a
- * determination of the containing cell, Sec. 2.4), then evaluate u_h there.
- * Returns 0 if the point has no owner (the particle is lost, option 3). */
-static int stage_velocity(const orc_mesh *m, const double *y, double *u) {
+ * determination of the containing cell, Sec. 2.4), then evaluate u-tilde_h
+ * there.  Returns 0 if the point has no owner (the particle is lost). */
+static int stage_velocity(const orc_mesh *m, const double *y, double theta, double *u) {
   double t[3];
   int64_t K = orc_owner(m, y, t);
   if (K < 0) return 0;
-  orc_q2_eval(m, K, t, u);
+  velocity_at(m, K, t, theta, u);
   return 1;
 }
 
@@ -447,30 +474,32 @@ static int stage_velocity(const orc_mesh *m, const double *y, double *u) {
  *   RK2  : k1 = dt u(x);             x' = x + dt u(x + k1/2)      (midpoint)
  *   RK4  : k1 = dt u(x), k2 = dt u(x + k1/2), k3 = dt u(x + k2/2),
  *          k4 = dt u(x + k3);        x' = x + (k1 + 2k2 + 2k3 + k4)/6
- * The first stage uses the stored (cell, x-hat) (Remark 2.1).  Then x' is
- * located (Sec. 2.4); no owner -> lost (option 3, R7). */
+ * The first stage uses the stored (cell, x-hat) (Remark 2.1).  Stage s is
+ * evaluated at time t^n + c_s dt with c = (0, 1/2, 1/2, 1) (RK4), (0, 1/2)
+ * (RK2), (0) (Euler) when two fields are set (R6).  Then x' is located
+ * (Sec. 2.4); no owner -> lost (option 3, R7). */
 static void step_particle(const orc_mesh *m, orc_particle *p, double dt, int integrator) {
   int d = m->dim;
   double u[3] = {0, 0, 0}, k1[3] = {0, 0, 0}, k2[3] = {0, 0, 0}, k3[3] = {0, 0, 0}, k4[3] = {0, 0, 0};
   double y[3] = {0, 0, 0}, xn[3] = {0, 0, 0};
-  orc_q2_eval(m, p->cell, p->xhat, u);
+  velocity_at(m, p->cell, p->xhat, 0.0, u);
   for (int j = 0; j < d; ++j) k1[j] = dt * u[j];
   if (integrator == 1) {
     for (int j = 0; j < d; ++j) xn[j] = p->x[j] + k1[j];
   } else if (integrator == 2) {
     for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k1[j];
-    if (!stage_velocity(m, y, u)) goto lost;
+    if (!stage_velocity(m, y, 0.5, u)) goto lost;
     for (int j = 0; j < d; ++j) k2[j] = dt * u[j];
     for (int j = 0; j < d; ++j) xn[j] = p->x[j] + k2[j];
   } else {
     for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k1[j];
-    if (!stage_velocity(m, y, u)) goto lost;
+    if (!stage_velocity(m, y, 0.5, u)) goto lost;
     for (int j = 0; j < d; ++j) k2[j] = dt * u[j];
     for (int j = 0; j < d; ++j) y[j] = p->x[j] + 0.5 * k2[j];
-    if (!stage_velocity(m, y, u)) goto lost;
+    if (!stage_velocity(m, y, 0.5, u)) goto lost;
     for (int j = 0; j < d; ++j) k3[j] = dt * u[j];
     for (int j = 0; j < d; ++j) y[j] = p->x[j] + k3[j];
-    if (!stage_velocity(m, y, u)) goto lost;
+    if (!stage_velocity(m, y, 1.0, u)) goto lost;
     for (int j = 0; j < d; ++j) k4[j] = dt * u[j];
     for (int j = 0; j < d; ++j) xn[j] = p->x[j] + (k1[j] + 2.0 * k2[j] + 2.0 * k3[j] + k4[j]) / 6.0;
   }
@@ -791,4 +820,41 @@ double orc_advect_loss(const orc_mesh *m, int64_t N, const double *x, const doub
     }
   }
   return loss;
+}
+
+/* Sec. 2.7 (ii) also names the geometric and harmonic averages of the
+ * particles of a cell:
+ *   geometric  exp( (1/n_K) sum log v )      (defined for v > 0)
+ *   harmonic   n_K / sum (1 / v)             (defined for v > 0)
+ * A cell holding a value <= 0 gets NaN (reading R14: the paper is silent);
+ * empty cells get empty_fill (R10).  kind: 0 arithmetic, 1 geometric,
+ * 2 harmonic.  Left folds in store order. */
+void orc_cell_average_kind(int64_t ncells, int64_t N, const int64_t *cell, const double *value, int kind,
+                           double empty_fill, double *avg, int64_t *count) {
+  if (kind == 0) {
+    orc_cell_average(ncells, N, cell, value, empty_fill, avg, count);
+    return;
+  }
+  double *sum = (double *)calloc(ncells > 0 ? ncells : 1, sizeof(double));
+  int *bad = (int *)calloc(ncells > 0 ? ncells : 1, sizeof(int));
+  for (int64_t K = 0; K < ncells; ++K) count[K] = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    int64_t K = cell[i];
+    double v = value[i];
+    if (!(v > 0.0)) bad[K] = 1;
+    sum[K] = sum[K] + (kind == 1 ? log(v) : 1.0 / v);
+    count[K] += 1;
+  }
+  for (int64_t K = 0; K < ncells; ++K) {
+    if (count[K] == 0)
+      avg[K] = empty_fill;
+    else if (bad[K])
+      avg[K] = NAN;
+    else if (kind == 1)
+      avg[K] = exp(sum[K] / (double)count[K]);
+    else
+      avg[K] = (double)count[K] / sum[K];
+  }
+  free(sum);
+  free(bad);
 }

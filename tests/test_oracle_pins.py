@@ -371,3 +371,49 @@ def test_cell_average_pins(oracle_mod):
             assert abs(avg[K] - exact) <= len(sel) * 2.0**-53 * np.abs(sel).max()
         else:
             assert avg[K] == 0.0 and cnt[K] == 0
+
+
+def test_geometric_and_harmonic_average_pins(oracle_mod):
+    """Sec. 2.7 (ii): geometric exp(mean log v) and harmonic n / sum(1/v)."""
+    cell = np.array([0, 0, 1, 1, 1, 3, 3], dtype=np.int64)
+    v = np.array([2.0, 8.0, 1.0, 3.0, 9.0, 0.5, 4.0])
+    g, cnt = oracle_mod.cell_average(4, cell, v, empty_fill=-1.0, kind=1)
+    h, _ = oracle_mod.cell_average(4, cell, v, empty_fill=-1.0, kind=2)
+    a, _ = oracle_mod.cell_average(4, cell, v, empty_fill=-1.0, kind=0)
+    np.testing.assert_allclose(g, [4.0, 3.0, -1.0, math.sqrt(2.0)], rtol=4e-16)     # sqrt(16), cbrt(27), sqrt(2)
+    np.testing.assert_allclose(h, [3.2, 27.0 / 13.0, -1.0, 8.0 / 9.0], rtol=4e-16)  # 2ab/(a+b), 3/(1+1/3+1/9)
+    assert (a[[0, 1, 3]] >= g[[0, 1, 3]]).all() and (g[[0, 1, 3]] >= h[[0, 1, 3]]).all()  # AM >= GM >= HM
+    # a constant cell averages to the constant; a non-positive value gives NaN
+    g2, _ = oracle_mod.cell_average(2, np.array([0, 0, 0, 1, 1]), np.array([7.5, 7.5, 7.5, 2.0, -1.0]), kind=1)
+    assert abs(g2[0] - 7.5) <= 2 * np.spacing(7.5) and math.isnan(g2[1])
+    h2, _ = oracle_mod.cell_average(1, np.array([0, 0]), np.array([0.0, 2.0]), kind=2)
+    assert math.isnan(h2[0])
+
+
+@pytest.mark.parametrize("integrator", [1, 2, 4])
+def test_time_interpolated_field(oracle_mod, integrator):
+    """Sec. 2.3: u-tilde_h interpolates u_h^n and u_h^{n+1} linearly in time
+    (reading R6).  (a) U^{n+1} = U^n gives the steady result bit for bit;
+    (b) spatially uniform fields c0 -> c1 move every particle by exactly
+    dt (c0 + c1) / 2 per step (RK2 and RK4 integrate a linear-in-time
+    velocity exactly), forward Euler by dt c0."""
+    n = (3, 3, 3)
+    X = W.jittered_vertices(n, 17)
+    U = W.curl_potential_field(W.q2_node_coords(n, X), 5)[0]
+    m = oracle_mod.Mesh(n, X, U)
+    p0 = oracle_mod.seed_particles(m, uniform_count=4, seed=2)
+    steady = oracle_mod.advect(m, p0, 0.02, integrator, 3)
+    m.set_velocity_next(U)
+    same = oracle_mod.advect(m, p0, 0.02, integrator, 3)
+    np.testing.assert_array_equal(same.x, steady.x)
+    np.testing.assert_array_equal(same.id, steady.id)
+    c0, c1 = np.array([0.2, -0.1, 0.3]), np.array([-0.3, 0.25, 0.1])
+    m.set_velocity(_const_U(n, c0))
+    m.set_velocity_next(_const_U(n, c1))
+    dt, steps = 0.01, 3
+    p = oracle_mod.advect(m, p0, dt, integrator, steps)
+    per = dt * c0 if integrator == 1 else dt * 0.5 * (c0 + c1)
+    want = {int(i): x + steps * per for i, x in zip(p0.id, p0.x)}
+    assert p.n > p0.n // 2
+    for i, x in zip(p.id, p.x):
+        np.testing.assert_allclose(x, want[int(i)], rtol=0, atol=1e-15)
