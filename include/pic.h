@@ -67,7 +67,7 @@ typedef enum {
 
 typedef enum { PIC_EULER = 1, PIC_RK2 = 2, PIC_RK4 = 4 } pic_integrator;
 typedef enum { PIC_FP64 = 0, PIC_FP32_BASIS = 1 } pic_precision;
-typedef enum { PIC_AVG_ARITHMETIC = 0 } pic_average;
+typedef enum { PIC_AVG_ARITHMETIC = 0, PIC_AVG_GEOMETRIC = 1, PIC_AVG_HARMONIC = 2 } pic_average;
 
 /* Bits of the device status word (pic_get_state). */
 #define PIC_STATUS_NEWTON_NONCONV 0x1u /* Newton hit its iteration cap in some candidate cell */
@@ -77,7 +77,7 @@ typedef enum { PIC_AVG_ARITHMETIC = 0 } pic_average;
 
 /* Mesh of (bi/tri)linear cells with a Q2 velocity field (Sec. 2.1, 2.3).
  *   dim       2 or 3
- *   n_cells   [dim] cells per axis, each >= 1; total cells < 2^31
+ *   n_cells   [dim] cells per axis, each >= 1; total cells < 2^31, Q2 nodes < 2^32
  *   vertices  [dim][nverts] FP64 positions, nverts = prod(n_cells[a]+1);
  *             on the device if vertices_on_device, else host memory
  *   stream    stream for the upload and the per-cell set-up kernels
@@ -91,9 +91,14 @@ pic_status pic_destroy_mesh(pic_mesh mesh);
 
 /* Q2 nodal velocity u_h (Sec. 2.3: the finite-element field whose evaluation
  * at particle positions is "the primary expense").
- *   U       [dim][nnodes] FP64 on the device, nnodes = prod(2*n_cells[a]+1)
- *   U_next  must be NULL (time interpolation between two fields is not built)
- * The library copies U (stream-ordered); the caller may reuse U afterwards.
+ *   U       [dim][nnodes] FP64, device or host, nnodes = prod(2*n_cells[a]+1):
+ *           the field at the start of a time step, u_h^n
+ *   U_next  NULL for a steady field, or the field at the end of the step,
+ *           u_h^{n+1}: every step of pic_advect then evaluates stage s at
+ *           t^n + c_s dt with u-tilde_h = (1 - c_s) u_h^n + c_s u_h^{n+1}
+ *           (Sec. 2.3, eq. position-ode-approx; c = 0, 1/2, 1/2, 1 for RK4,
+ *           0, 1/2 for RK2, 0 for Euler).  Not supported by the adjoint.
+ * The library copies the fields (stream-ordered); the caller may reuse them.
  * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_set_velocity_dofs(pic_mesh mesh, const double *U, const double *U_next, void *stream);
 
@@ -168,7 +173,8 @@ pic_status pic_destroy_tape(pic_tape tape);
  *   seeds           [n_problems] generator seeds (ids count from 0 per problem)
  * Problem p is seeded exactly as pic_seed_particles would seed it alone, and
  * advances with the same per-particle arithmetic: each problem matches its
- * solo run bit for bit.  Synchronises.  At most 128 problems.
+ * solo run bit for bit.  Synchronises.  At most 128 problems; steady fields
+ * only (the views of the meshes are taken at creation).
  * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
 pic_status pic_ensemble_create(int n_problems, const pic_mesh *meshes, const uint32_t *const *per_cell,
                                const uint32_t *uniform_counts, const uint64_t *seeds, int n_props, void *stream,
@@ -268,9 +274,12 @@ pic_status pic_sort_by_cell(size_t n, const uint32_t *cell, const uint64_t *id, 
 pic_status pic_sort_by_cell_noalloc(size_t n, const uint32_t *cell, const uint64_t *id, uint32_t n_cells,
                                     uint32_t *perm, uint32_t *cell_off, void *stream);
 
-/* Particle -> cell transfer (Sec. 2.7, scheme (ii), arithmetic average):
- * avg[K] = (sum of property `prop` over the particles of K) / n_K, summed in
- * a fixed order (deterministic); count[K] = n_K; empty cells get empty_fill.
+/* Particle -> cell transfer (Sec. 2.7, scheme (ii)): over the particles of
+ * cell K, in store order (deterministic),
+ *   PIC_AVG_ARITHMETIC  sum v / n_K
+ *   PIC_AVG_GEOMETRIC   exp(sum log v / n_K)  (NaN if the cell holds a v <= 0)
+ *   PIC_AVG_HARMONIC    n_K / sum(1 / v)      (NaN if the cell holds a v <= 0)
+ * count[K] = n_K; empty cells get empty_fill.
  *   avg    [n_cells] FP64 device;  count  [n_cells] u32 device (may be NULL)
  * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_interpolate_to_cells(pic_particles parts, pic_mesh mesh, int prop, pic_average kind, double *avg,

@@ -417,6 +417,8 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   if (integrator != PIC_EULER && integrator != PIC_RK2 && integrator != PIC_RK4)
     return (set_error("pic_advect_record: unknown integrator"), PIC_ERR_ARG);
   if (!mesh->has_velocity) return (set_error("pic_advect_record: velocity not set"), PIC_ERR_ARG);
+  if (mesh->has_next)
+    return (set_error("pic_advect_record: the adjoint supports a steady field only (no U_next)"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   pic_tape_s* tp = (pic_tape_s*)calloc(1, sizeof(pic_tape_s));
   tp->parts = parts;

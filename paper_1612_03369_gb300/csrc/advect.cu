@@ -11,7 +11,7 @@
 
 namespace pic {
 
-template <int D, int RK, bool F32B>
+template <int D, int RK, bool F32B, bool TWO>
 __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(MeshView m, StoreView s, df dt,
                                                                           uint32_t* __restrict__ cell_new,
                                                                           uint32_t* __restrict__ counts,
@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(Mesh
     unsigned flags = 0, lost = 0, steps = 0;
     if (i < n) {
       steps = 1;
-      const uint32_t Kn = advect_particle<D, RK, F32B>(m, s, i, s.cell[i], dt, iters, flags);
+      const uint32_t Kn = advect_particle<D, RK, F32B, TWO>(m, s, i, s.cell[i], dt, iters, flags);
       cell_new[i] = Kn;
       if (Kn != PIC_LOST)
         atomicAdd(counts + Kn, 1u);
@@ -113,8 +113,12 @@ template <int D, int RK, bool F32B>
 static void launch_advect(pic_particles_s* p, const MeshView& m, double dt, cudaStream_t st) {
   const float hi = (float)dt;
   const df dtd = {hi, (float)(dt - (double)hi)};
-  advect_kernel<D, RK, F32B><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd, p->cell_new,
-                                                                         p->counts, p->ctr);
+  if (m.has_next)
+    advect_kernel<D, RK, F32B, true><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd,
+                                                                                 p->cell_new, p->counts, p->ctr);
+  else
+    advect_kernel<D, RK, F32B, false><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd,
+                                                                                  p->cell_new, p->counts, p->ctr);
   count_launches(1);
 }
 

@@ -38,14 +38,34 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
   }
 }
 
-// Velocity at double-float reference coordinates t of cell K: the Q2
-// contraction in double-float, or in FP32 for the precision form.
-template <int D, bool F32B>
-__device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
-  if constexpr (F32B)
-    q2_eval_f32<D>(m, K, t, u);
-  else
-    q2_eval_df<D>(m, K, t, u);
+// u-tilde_h at double-float reference coordinates t of cell K and stage time
+// t^n + theta dt, theta = 0, 1/2, 1 for tcode = 0, 1, 2: the steady field,
+// or with a second field set, (1 - theta) u_h^n + theta u_h^{n+1} (reading
+// of the time interpolation of Sec. 2.3; theta = 1/2 is the exact average).
+// The Q2 contraction is in double-float, or FP32 for the precision form; it
+// sits in a rolled loop over the (one or two) fields so the kernel holds one
+// copy of it.
+template <int D, bool F32B, bool TWO>
+__device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const df t[D], int tcode, df u[D]) {
+  if constexpr (!TWO) {
+    if constexpr (F32B)
+      q2_eval_f32<D>(m, m.U2, K, t, u);
+    else
+      q2_eval_df<D>(m, m.U2, K, t, u);
+    return;
+  }
+  const bool two = m.has_next && tcode == 1;
+  const float2* first = (m.has_next && tcode == 2) ? m.U2n : m.U2;
+#pragma unroll 1
+  for (int f = 0; f < (two ? 2 : 1); ++f) {
+    df v[D];
+    if constexpr (F32B)
+      q2_eval_f32<D>(m, f == 0 ? first : m.U2n, K, t, v);
+    else
+      q2_eval_df<D>(m, f == 0 ? first : m.U2n, K, t, v);
+#pragma unroll
+    for (int a = 0; a < D; ++a) u[a] = (f == 0) ? v[a] : df_scale2(df_add(u[a], v[a]), 0.5f);
+  }
 }
 
 // One time step for every particle of the store (in place), recording the
@@ -74,6 +94,7 @@ struct Tableau;
 template <>
 struct Tableau<1> {  // forward Euler
   static constexpr int S = 1;
+  __device__ static int tcode(int) { return 0; }  // stage time: 0 -> t^n, 1 -> t^n + dt/2, 2 -> t^{n+1}
   __device__ static float c(int) { return 0.f; }
   __device__ static float w(int) { return 1.f; }
   __device__ static bool divide6() { return false; }
@@ -81,6 +102,7 @@ struct Tableau<1> {  // forward Euler
 template <>
 struct Tableau<2> {  // midpoint rule
   static constexpr int S = 2;
+  __device__ static int tcode(int p) { return p == 0 ? 0 : 1; }
   __device__ static float c(int p) { return 0.5f; }  // y_1 = x + k_0 / 2
   __device__ static float w(int p) { return p == 0 ? 0.f : 1.f; }
   __device__ static bool divide6() { return false; }
@@ -88,6 +110,7 @@ struct Tableau<2> {  // midpoint rule
 template <>
 struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x + k2
   static constexpr int S = 4;
+  __device__ static int tcode(int p) { return p == 0 ? 0 : (p == 3 ? 2 : 1); }
   __device__ static float c(int p) { return p == 3 ? 1.f : 0.5f; }
   __device__ static float w(int p) { return (p == 0 || p == 3) ? 1.f : 2.f; }  // then / 6
   __device__ static bool divide6() { return true; }
@@ -100,9 +123,10 @@ struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x +
 #endif
 
 // One time step of particle i of store s in mesh m, starting in cell K.
+// TWO: the mesh carries a second field (time interpolation).
 // Writes the new x and x-hat in place when the particle survives and returns
 // its new cell, or PIC_LOST.
-template <int D, int RK, bool F32B>
+template <int D, int RK, bool F32B, bool TWO = false>
 __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const StoreView& s, uint32_t i, uint32_t K,
                                                     df dt, int& iters, unsigned& flags) {
   using TB = Tableau<RK>;
@@ -137,7 +161,7 @@ __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const Sto
       if (p == TB::S) break;
     }
     df u[D];
-    velocity<D, F32B>(m, Ks, ts, u);
+    velocity<D, F32B, TWO>(m, Ks, ts, TB::tcode(p), u);
     const float w = TB::w(p);
 #pragma unroll
     for (int a = 0; a < D; ++a) {

@@ -5,10 +5,14 @@
 
 namespace pic {
 
-// Thread per cell: the particles of a cell are summed in store order (a left
-// fold, the order of the definition), then divided by their number.  The
-// threads of a warp read neighbouring segments, so every sector fetched from
-// HBM is used by the following iterations through L1.
+// Thread per cell: the particles of a cell are folded in store order (the
+// order of the definition), then combined with their number.  The threads of
+// a warp read neighbouring segments, so every sector fetched from HBM is used
+// by the following iterations through L1.  Kinds (Sec. 2.7 (ii)):
+//   0 arithmetic  sum v / n
+//   1 geometric   exp(sum log v / n)   (NaN if the cell holds a v <= 0)
+//   2 harmonic    n / sum (1 / v)      (NaN if the cell holds a v <= 0)
+template <int KIND>
 __global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __restrict__ cell_off,
                                                            const double* __restrict__ prop, uint32_t C, size_t cap,
                                                            double empty_fill, double* __restrict__ avg,
@@ -20,9 +24,27 @@ __global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __res
       continue;
     }
     double s = 0.0;
-    for (uint32_t i = beg; i < end; ++i) s += prop[i];
+    bool bad = false;
+    for (uint32_t i = beg; i < end; ++i) {
+      const double v = prop[i];
+      if constexpr (KIND == 0) {
+        s += v;
+      } else {
+        bad = bad || !(v > 0.0);
+        s += (KIND == 1) ? log(v) : 1.0 / v;
+      }
+    }
     const uint32_t n = end - beg;
-    avg[K] = n ? s / (double)n : empty_fill;
+    double r = empty_fill;
+    if (n) {
+      if constexpr (KIND == 0)
+        r = s / (double)n;
+      else if (bad)
+        r = __longlong_as_double(0x7ff8000000000000ll);
+      else
+        r = (KIND == 1) ? exp(s / (double)n) : (double)n / s;
+    }
+    avg[K] = r;
     if (count) count[K] = n;
   }
 }
@@ -37,13 +59,20 @@ extern "C" pic_status pic_interpolate_to_cells(pic_particles p, pic_mesh mesh, i
   if (p->mesh != mesh) return (set_error("pic_interpolate_to_cells: mesh mismatch"), PIC_ERR_ARG);
   if (prop < 0 || prop >= p->n_props)
     return (set_error("pic_interpolate_to_cells: property %d out of range", prop), PIC_ERR_ARG);
-  if (kind != PIC_AVG_ARITHMETIC) return (set_error("pic_interpolate_to_cells: unknown average %d", (int)kind), PIC_ERR_ARG);
+  if (kind != PIC_AVG_ARITHMETIC && kind != PIC_AVG_GEOMETRIC && kind != PIC_AVG_HARMONIC)
+    return (set_error("pic_interpolate_to_cells: unknown average %d", (int)kind), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   size_t grid = ((size_t)p->C + 255) / 256;
   const size_t cap = (size_t)num_sms() * 16;
   if (grid > cap) grid = cap;
-  cell_average_kernel<<<(int)(grid ? grid : 1), 256, 0, st>>>(p->cell_off, p->props[p->cur] + (size_t)prop * p->capacity,
-                                                              p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  const int g = (int)(grid ? grid : 1);
+  const double* pv = p->props[p->cur] + (size_t)prop * p->capacity;
+  if (kind == PIC_AVG_ARITHMETIC)
+    cell_average_kernel<0><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  else if (kind == PIC_AVG_GEOMETRIC)
+    cell_average_kernel<1><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  else
+    cell_average_kernel<2><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
   count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;

@@ -311,6 +311,9 @@ extern "C" pic_status pic_ensemble_create(int n_problems, const pic_mesh* meshes
     if (!meshes[p] || meshes[p]->dim != dim)
       return (set_error("pic_ensemble_create: mesh %d missing or of another dimension", p), PIC_ERR_ARG);
     if (!meshes[p]->has_velocity) return (set_error("pic_ensemble_create: mesh %d has no velocity", p), PIC_ERR_ARG);
+    if (meshes[p]->has_next)
+      return (set_error("pic_ensemble_create: mesh %d has a second field; the ensemble runs steady fields", p),
+              PIC_ERR_ARG);
   }
   cudaStream_t st = (cudaStream_t)stream;
   pic_ensemble_s* e = new pic_ensemble_s();

@@ -397,7 +397,8 @@ __device__ __forceinline__ void lagrange2_df(df t, df l[3]) {
 }
 
 template <int D>
-__device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
+__device__ __forceinline__ void q2_eval_df(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
+                                           df u[D]) {
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
   const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
   df L0[3], L1[3], L2[3];
@@ -417,7 +418,7 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const 
     for (int comp = 0; comp < D; ++comp) mid[comp] = acc_zero();
 #pragma unroll 1
     for (int b = 0; b < 3; ++b) {
-      const float2* row = m.U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
+      const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
       float2 nd[3 * D];
 #pragma unroll
       for (int q = 0; q < 3 * D; ++q) nd[q] = __ldg(row + q);
@@ -459,7 +460,8 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, uint32_t K, const 
 
 // FP32 basis and contraction (precision form): only the high parts.
 template <int D>
-__device__ __forceinline__ void q2_eval_f32(const MeshView& m, uint32_t K, const df t[D], df u[D]) {
+__device__ __forceinline__ void q2_eval_f32(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
+                                            df u[D]) {
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
   const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
   float L[D][3];
@@ -475,7 +477,7 @@ __device__ __forceinline__ void q2_eval_f32(const MeshView& m, uint32_t K, const
     for (int comp = 0; comp < D; ++comp) mid[comp] = 0.f;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const float2* row = m.U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
+      const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
 #pragma unroll
       for (int comp = 0; comp < D; ++comp) {
         const float s = fmaf(L[0][2], __ldg(row + 2 * D + comp).x,

@@ -196,14 +196,15 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->blk);
   cudaFree(m->qbase);
   cudaFree(m->U2);
+  cudaFree(m->Un);
+  cudaFree(m->U32n);
+  cudaFree(m->U2n);
   free(m);
   return PIC_OK;
 }
 
 extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const double* U_next, void* stream) {
   if (!m || !U) return (set_error("pic_set_velocity_dofs: null argument"), PIC_ERR_ARG);
-  if (U_next)
-    return (set_error("pic_set_velocity_dofs: time interpolation between two fields is not supported"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)m->dim * (size_t)m->nnodes;
   if (!m->U) {
@@ -213,11 +214,24 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
-  PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
+  if (U_next && !m->Un) {
+    if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32n, sizeof(float) * n) != cudaSuccess ||
+        cudaMalloc(&m->U2n, sizeof(float2) * n) != cudaSuccess) {
+      cudaGetLastError();
+      return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
+    }
+  }
   const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
   to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
   to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  if (U_next) {
+    PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
+    to_f32_kernel<<<g, 256, 0, st>>>(m->Un, m->U32n, n);
+    to_df_nodes_kernel<<<g, 256, 0, st>>>(m->Un, m->U2n, m->dim, (size_t)m->nnodes);
+  }
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
+  m->has_next = U_next ? 1 : 0;
   return PIC_OK;
 }

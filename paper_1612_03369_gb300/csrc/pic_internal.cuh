@@ -64,6 +64,10 @@ struct pic_mesh_s {
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
   uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
   float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo)
+  double* Un;    // the same three copies of the field at the end of the step
+  float* U32n;   // (time interpolation), allocated when a second field is set
+  float2* U2n;
+  int has_next;
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
 };
@@ -124,6 +128,8 @@ struct MeshView {
   const float4* blk;
   const uint32_t* qbase;
   const float2* U2;
+  const float2* U2n;  // field at the end of the step, when has_next
+  int has_next;
   double dlo[3], dhi[3];
 };
 
@@ -146,6 +152,8 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.blk = m->blk;
   v.qbase = m->qbase;
   v.U2 = m->U2;
+  v.U2n = m->U2n;
+  v.has_next = m->has_next;
   return v;
 }
 

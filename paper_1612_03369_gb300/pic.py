@@ -20,7 +20,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CAPACITY, PIC_ERR_CUDA, PIC_ERR_NOT_CO
     PIC_ERR_STATE = range(8)
 PIC_EULER, PIC_RK2, PIC_RK4 = 1, 2, 4
 PIC_FP64, PIC_FP32_BASIS = 0, 1
-PIC_AVG_ARITHMETIC = 0
+PIC_AVG_ARITHMETIC, PIC_AVG_GEOMETRIC, PIC_AVG_HARMONIC = 0, 1, 2
 PIC_STATUS_NEWTON_NONCONV, PIC_STATUS_CAPACITY, PIC_STATUS_GLOBAL_SEARCH, PIC_STATUS_BOUNDS = 1, 2, 4, 8
 LOST = 0xFFFFFFFF
 
@@ -119,8 +119,8 @@ def pic_destroy_mesh(h: int):
     _check(_lib.pic_destroy_mesh(h), "pic_destroy_mesh")
 
 
-def pic_set_velocity_dofs(h: int, U, stream=None):
-    _check(_lib.pic_set_velocity_dofs(h, _ptr(U), None, _stream(stream)), "pic_set_velocity_dofs")
+def pic_set_velocity_dofs(h: int, U, stream=None, U_next=None):
+    _check(_lib.pic_set_velocity_dofs(h, _ptr(U), _ptr(U_next), _stream(stream)), "pic_set_velocity_dofs")
 
 
 def pic_seed_particles(mesh: int, per_cell=None, uniform_count: int = 0, seed: int = 0, first_id: int = 0,
@@ -278,11 +278,14 @@ class Mesh:
         if U is not None:
             self.set_velocity(U, stream)
 
-    def set_velocity(self, U, stream=None):
+    def set_velocity(self, U, stream=None, U_next=None):
         import torch
 
         self.U = torch.as_tensor(np.ascontiguousarray(U, dtype=np.float64), device="cuda")
-        pic_set_velocity_dofs(self.h, self.U, stream)
+        self.U_next = None
+        if U_next is not None:
+            self.U_next = torch.as_tensor(np.ascontiguousarray(U_next, dtype=np.float64), device="cuda")
+        pic_set_velocity_dofs(self.h, self.U, stream, self.U_next)
 
     def locate_points(self, x, hint=None, stream=None):
         return pic_locate_points(self.h, x, hint, stream=stream)
@@ -332,12 +335,12 @@ class Particles:
     def stats(self):
         return pic_get_counters(self.h)
 
-    def average(self, prop, empty_fill=0.0, stream=None):
+    def average(self, prop, empty_fill=0.0, kind=PIC_AVG_ARITHMETIC, stream=None):
         import torch
 
         avg = torch.empty(self.mesh.ncells, dtype=torch.float64, device="cuda")
         cnt = torch.empty(self.mesh.ncells, dtype=torch.int32, device="cuda")
-        pic_interpolate_to_cells(self.h, self.mesh.h, prop, avg, cnt, empty_fill, stream=stream)
+        pic_interpolate_to_cells(self.h, self.mesh.h, prop, avg, cnt, empty_fill, kind=kind, stream=stream)
         return avg, cnt
 
     def export(self, stream=None):

@@ -205,3 +205,51 @@ def test_edge_cases(P, oracle_mod):
         parts.advect(float("nan"), 4, 1)
     with pytest.raises(P.PicError):
         parts.set_property(7, torch.zeros(1, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_geometric_harmonic_averages(P, oracle_mod, kind):
+    """Sec. 2.7 (ii) geometric and harmonic averages after a few steps, on a
+    positive property (1 + x0 + y0) and on one with non-positive values."""
+    import torch
+
+    wl = W.curl_cube(8, 5, 2, 7)
+    mesh, parts = H.gpu_seed(wl)
+    st = parts.export()
+    pos = (1.0 + st["x"][0] + st["x"][1]).contiguous()
+    parts.set_property(0, pos)
+    parts.set_property(1, (st["x"][2] - 0.5).contiguous())  # changes sign
+    parts.advect(wl.dt, 4, 2)
+    g = H.gpu_state(parts)
+    for prop in (0, 1):
+        ga, gc = parts.average(prop, empty_fill=-9.0, kind=kind)
+        oa, oc = oracle_mod.cell_average(wl.ncells, g["cell"], g["props"][:, prop], empty_fill=-9.0, kind=kind)
+        ga = ga.cpu().numpy()
+        np.testing.assert_array_equal(gc.cpu().numpy().astype(np.int64), oc)
+        np.testing.assert_array_equal(np.isnan(ga), np.isnan(oa))
+        ok = ~np.isnan(oa)
+        assert np.abs(ga[ok] - oa[ok]).max() <= 1e-13 * np.abs(oa[ok]).max()
+
+
+@pytest.mark.parametrize("integrator", [4, 2, 1])
+def test_time_interpolated_velocity(P, oracle_mod, integrator):
+    """Two fields u_h^n, u_h^{n+1}: stage s at t^n + c_s dt uses
+    (1 - c_s) u_h^n + c_s u_h^{n+1} (reading R6)."""
+    wl = W.curl_cube(7, 6, 3, 11)
+    Un = W.zero_wall_normal(wl.n, W.normalise_max(W.curl_potential_field(W.q2_node_coords(wl.n, wl.X), 12)[0]))
+    mesh, parts = H.gpu_seed(wl)
+    mesh.set_velocity(wl.U, U_next=Un)
+    parts.advect(wl.dt, integrator, 3)
+    om, op = H.oracle_seed(oracle_mod, wl)
+    om.set_velocity_next(Un)
+    op = oracle_mod.advect(om, op, wl.dt, integrator, 3)
+    H.assert_same_store(H.gpu_state(parts), op, wl)
+    # U_next = U is the steady field bit for bit
+    m1, p1 = H.gpu_seed(wl)
+    m2, p2 = H.gpu_seed(wl)
+    m2.set_velocity(wl.U, U_next=wl.U)
+    p1.advect(wl.dt, integrator, 3)
+    p2.advect(wl.dt, integrator, 3)
+    a, b = H.gpu_state(p1), H.gpu_state(p2)
+    np.testing.assert_array_equal(a["x"], b["x"])
+    np.testing.assert_array_equal(a["id"], b["id"])
