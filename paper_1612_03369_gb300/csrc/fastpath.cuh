@@ -189,6 +189,17 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
       mx = fmaxf(mx, fabsf(dt[a]));
     }
     if (!(mx <= 1e3f)) return kCellFail;  // diverging or NaN
+    // Clearly outside: the iterate lies outside [0,1] by much more than the
+    // last update (Newton is in its quadratic regime once the update is
+    // small), so the root is outside too.  Stop here; t32 tells the walk
+    // where to go.  A wrong call only costs time: the walk then falls back
+    // to the FP64 search, and ownership is still the lowest-index rule.
+    if (mx < 0.05f) {
+      float out = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) out = fmaxf(out, fmaxf(-t32[a], t32[a] - 1.0f));
+      if (out > 4.f * mx + 1e-3f) return kCellOut;
+    }
     if (mx <= (accurate ? kSettle32 : kSettle32Tight)) {
       settled = true;
       break;

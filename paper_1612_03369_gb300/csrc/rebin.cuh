@@ -174,22 +174,58 @@ __device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off
   }
 }
 
-// Copy every field from old slot perm[j] to new slot j, j < n.
+// Copy every field from old slot perm[j] to new slot j, j < n.  Each thread
+// takes four slots per pass and issues their loads before their stores
+// (memory-level parallelism when the grid is small, as in a persistent
+// kernel).
 __device__ __forceinline__ void gather_phase(const StoreView& src, const StoreView& dst,
                                              const uint32_t* __restrict__ perm, int dim, uint32_t n,
                                              unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
-  for (uint32_t j = first; j < n; j += stride) {
-    const uint32_t s = perm[j];
-    if (s >= src.cap) {
-      atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
+  constexpr int U = 4;
+  for (uint32_t j0 = first; j0 < n; j0 += U * stride) {
+    uint32_t sidx[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t j = j0 + u * stride;
+      sidx[u] = j < n ? perm[j] : 0u;
+      ok[u] = j < n && sidx[u] < src.cap;
+      if (j < n && !ok[u]) atomicOr(status, PIC_STATUS_BOUNDS);
     }
     for (int a = 0; a < dim; ++a) {
-      dst.x[a * dst.cap + j] = src.x[a * src.cap + s];
-      dst.xhat[a * dst.cap + j] = src.xhat[a * src.cap + s];
+      double xv[U];
+      float2 tv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) {
+          xv[u] = src.x[a * src.cap + sidx[u]];
+          tv[u] = src.xhat[a * src.cap + sidx[u]];
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) {
+          dst.x[a * dst.cap + j0 + u * stride] = xv[u];
+          dst.xhat[a * dst.cap + j0 + u * stride] = tv[u];
+        }
     }
-    dst.id[j] = src.id[s];
-    for (int q = 0; q < src.n_props; ++q) dst.props[q * dst.cap + j] = src.props[q * src.cap + s];
+    {
+      uint64_t iv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) iv[u] = src.id[sidx[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) dst.id[j0 + u * stride] = iv[u];
+    }
+    for (int q = 0; q < src.n_props; ++q) {
+      double pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) pv[u] = src.props[q * src.cap + sidx[u]];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) dst.props[q * dst.cap + j0 + u * stride] = pv[u];
+    }
   }
 }
 
