@@ -18,6 +18,8 @@
 // point atomics, so the gradient is bit-for-bit reproducible.
 #include <cstdlib>
 
+#include "advect.cuh"
+#include "fastpath.cuh"
 #include "locate.cuh"
 #include "pic_internal.cuh"
 
@@ -37,8 +39,8 @@ struct pic_tape_s {
   double* lam[2];      // [dim][cap]
   uint32_t* rec_cell;  // [4 cap]
   uint64_t* rec_key;   // [4 cap]
-  double* rec_t;       // [dim][4 cap]
-  double* rec_w;       // [dim][4 cap]
+  float2* rec_t;       // [dim][4 cap] double-float x-hat of the stage
+  float2* rec_w;       // [dim][4 cap] double-float dt lambda_k
   uint32_t* rec_perm;  // [4 cap]
   uint32_t* rec_off;   // [C + 1]
   void* sort_scratch;
@@ -104,11 +106,11 @@ __device__ __forceinline__ void q2_value_grad(const MeshView& m, uint32_t K, con
 template <int D>
 __device__ __forceinline__ void invert(const double J[D][D], double Ji[D][D]) {
   if constexpr (D == 2) {
-    const double det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    Ji[0][0] = J[1][1] / det;
-    Ji[0][1] = -J[0][1] / det;
-    Ji[1][0] = -J[1][0] / det;
-    Ji[1][1] = J[0][0] / det;
+    const double inv = 1.0 / (J[0][0] * J[1][1] - J[0][1] * J[1][0]);
+    Ji[0][0] = J[1][1] * inv;
+    Ji[0][1] = -J[0][1] * inv;
+    Ji[1][0] = -J[1][0] * inv;
+    Ji[1][1] = J[0][0] * inv;
   } else {
     double c[3][3];
     c[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
@@ -120,11 +122,11 @@ __device__ __forceinline__ void invert(const double J[D][D], double Ji[D][D]) {
     c[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
     c[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
     c[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    const double det = J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2];
+    const double inv = 1.0 / (J[0][0] * c[0][0] + J[0][1] * c[0][1] + J[0][2] * c[0][2]);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) Ji[r][q] = c[q][r] / det;
+      for (int q = 0; q < 3; ++q) Ji[r][q] = c[q][r] * inv;
   }
 }
 
@@ -158,17 +160,22 @@ struct TapeStep {
 };
 
 // One reverse step for every particle alive after it (thread per new slot j).
+// The stages are recomputed exactly as the forward computed them (double-
+// float locate and Q2 contraction, so the stage cells are the forward's);
+// G = du/dx at each stage is evaluated in FP64 (it carries lambda).
 template <int D, int RK>
 __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep tp, size_t cap, double dt,
                                                            const double* __restrict__ lam_in,
                                                            double* __restrict__ lam_out,
                                                            uint32_t* __restrict__ rec_cell,
-                                                           uint64_t* __restrict__ rec_key, double* __restrict__ rec_t,
-                                                           double* __restrict__ rec_w, DevCounters* __restrict__ ctr) {
+                                                           uint64_t* __restrict__ rec_key, float2* __restrict__ rec_t,
+                                                           float2* __restrict__ rec_w, DevCounters* __restrict__ ctr) {
   using TB = AdjTableau<RK>;
   constexpr int S = TB::S;
   const uint32_t n = *tp.n_next;
   const size_t rcap = kRecPerParticle * cap;
+  const float dthi = (float)dt;
+  const df dtd = df_make(dthi, (float)(dt - (double)dthi));
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const uint32_t i = tp.perm[j];
     if (i >= cap) {
@@ -176,43 +183,54 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
       continue;
     }
     double x[D], lam[D];
-    double ts[S][D], G[S][D][D];
+    df xd[D], ts[S][D];
+    double G[S][D][D];
     uint32_t Ks[S];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       x[a] = tp.x[a * cap + i];
       const float2 v = tp.xhat[a * cap + i];
-      ts[0][a] = (double)v.x + (double)v.y;
+      ts[0][a] = df_make(v.x, v.y);
       lam[a] = lam_in[a * cap + j];
+      xd[a] = df_from_double(x[a]);
     }
     Ks[0] = tp.cell[i];
     bool ok = Ks[0] < m.C;
-    double k[D];
-    // forward recomputation of the stages, with du/dx at each
+    df k[D];
+    int iters = 0;
+    unsigned flags = 0;
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if (!ok) break;
       if (s > 0) {
-        double y[D];
+        df y[D];
+        float hint[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) y[a] = x[a] + TB::a(s) * k[a];
-        int iters = 0;
-        unsigned flags = 0;
-        Ks[s] = locate<D>(m, y, Ks[s - 1], ts[s - 1], ts[s], iters, flags);
+        for (int a = 0; a < D; ++a) {
+          y[a] = df_add(xd[a], df_scale2(k[a], (float)TB::a(s)));
+          hint[a] = ts[s - 1][a].hi;
+        }
+        Ks[s] = locate_df<D>(m, y, Ks[s - 1], hint, ts[s], iters, flags);
         if (Ks[s] == PIC_LOST) {
           ok = false;
           break;
         }
       }
-      double u[D], Gu[D][D], J[D][D], Ji[D][D], phi[D];
-      q2_value_grad<D>(m, Ks[s], ts[s], u, Gu);
+      df u[D];
+      q2_eval_df<D>(m, m.U2, Ks[s], ts[s], u);
+      double t64[D], ud[D], Gu[D][D], J[D][D], Ji[D][D], phi[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        k[a] = df_mul(dtd, u[a]);
+        t64[a] = df_to_double(ts[s][a]);
+      }
+      q2_value_grad<D>(m, Ks[s], t64, ud, Gu);
       CellGeom<D> g;
       load_cell<D>(m, Ks[s], g);
-      map_and_jacobian<D>(g, ts[s], phi, J);
+      map_and_jacobian<D>(g, t64, phi, J);
       invert<D>(J, Ji);
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        k[c] = dt * u[c];
+      for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int q = 0; q < D; ++q) {
           double acc = 0.0;
@@ -220,7 +238,6 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
           for (int jj = 0; jj < D; ++jj) acc += Gu[c][jj] * Ji[jj][q];
           G[s][c][q] = acc;
         }
-      }
     }
     if (!ok) {
       // cannot happen for a particle that survived the step; keep it harmless
@@ -246,8 +263,9 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
       rec_key[r] = r;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        rec_t[a * rcap + r] = ts[s][a];
-        rec_w[a * rcap + r] = dt * lk[a];
+        rec_t[a * rcap + r] = make_float2(ts[s][a].hi, ts[s][a].lo);
+        const df w = df_from_double(dt * lk[a]);
+        rec_w[a * rcap + r] = make_float2(w.hi, w.lo);
       }
 #pragma unroll
       for (int q = 0; q < D; ++q) {
@@ -267,48 +285,61 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
 
 // Warp per cell: the records of the cell, in (cell, key) order, summed into
 // the cell's 3^D x D block of nodal gradient entries (lane e owns entries e,
-// e+32, ...).  Every cell is written, empty ones with zeros.
+// e+32, ...), in double-float on the FP32 pipe; every cell is written (FP64),
+// empty ones with zeros.
 template <int D>
 __global__ void __launch_bounds__(256) cell_partial_kernel(uint32_t C, const uint32_t* __restrict__ rec_off,
                                                            const uint32_t* __restrict__ rec_perm,
-                                                           const double* __restrict__ rec_t,
-                                                           const double* __restrict__ rec_w, size_t rcap,
+                                                           const float2* __restrict__ rec_t,
+                                                           const float2* __restrict__ rec_w, size_t rcap,
                                                            double* __restrict__ partial) {
   constexpr int NN = (D == 3 ? 27 : 9);
   constexpr int NE = NN * D;
   constexpr int PER = (NE + 31) / 32;
   const int lane = threadIdx.x & 31;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
-    double acc[PER];
+  // the (a, b, c, comp) of this lane's entries
+  int ea[PER], eb[PER], ec[PER], ecomp[PER];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) acc[q] = 0.0;
+  for (int q = 0; q < PER; ++q) {
+    const int ent = lane + 32 * q;
+    const int node = ent / D;
+    ecomp[q] = ent % D;
+    ea[q] = node % 3;
+    eb[q] = (node / 3) % 3;
+    ec[q] = node / 9;
+  }
+  for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
+    df_acc acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = acc_zero();
     const uint32_t beg = rec_off[K], end = rec_off[K + 1];
     for (uint32_t e = beg; e < end; ++e) {
       const uint32_t r = rec_perm[e];
-      double t[D], w[D], l[D][3];
+      df l[D][3], w[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        t[a] = rec_t[a * rcap + r];
-        w[a] = rec_w[a * rcap + r];
-        lagrange2<double>(t[a], l[a]);
+        const float2 tv = rec_t[a * rcap + r], wv = rec_w[a * rcap + r];
+        lagrange2_df(df_make(tv.x, tv.y), l[a]);
+        w[a] = df_make(wv.x, wv.y);
       }
 #pragma unroll
       for (int q = 0; q < PER; ++q) {
         const int ent = lane + 32 * q;
         if (ent < NE) {
-          const int node = ent / D, comp = ent % D;
-          const int na = node % 3, nb = (node / 3) % 3, nc = node / 9;
-          double phi = l[0][na] * l[1][nb];
-          if constexpr (D == 3) phi *= l[2][nc];
-          acc[q] += w[comp] * phi;
+          df phi = df_mul(l[0][ea[q]], l[1][eb[q]]);
+          if constexpr (D == 3) phi = df_mul(phi, l[2][ec[q]]);
+          acc_mad(acc[q], w[ecomp[q]], phi);
         }
       }
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int ent = lane + 32 * q;
-      if (ent < NE) partial[(size_t)K * NE + ent] = acc[q];
+      if (ent < NE) {
+        const df v = acc_result(acc[q]);
+        partial[(size_t)K * NE + ent] = df_to_double(v);
+      }
     }
   }
 }
@@ -447,8 +478,8 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   ok = ok && cudaMalloc(&tp->lam[1], sizeof(double) * d * cap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_cell, sizeof(uint32_t) * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_key, sizeof(uint64_t) * rcap) == cudaSuccess;
-  ok = ok && cudaMalloc(&tp->rec_t, sizeof(double) * d * rcap) == cudaSuccess;
-  ok = ok && cudaMalloc(&tp->rec_w, sizeof(double) * d * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_t, sizeof(float2) * d * rcap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->rec_w, sizeof(float2) * d * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_perm, sizeof(uint32_t) * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_off, sizeof(uint32_t) * ((size_t)tp->C + 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->sort_scratch, sort_scratch_bytes(rcap, tp->C)) == cudaSuccess;
