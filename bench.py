@@ -15,11 +15,12 @@ so no L2 flush is needed between steps.
 c3 is the precision form (FP32 basis) at 128^3; c4 times the adjoint
 (recorded forward + reverse sweep) at 32^3 x 32 per cell over 20 steps; c5
 times the 64-problem ensemble (10 steps per persistent graph launch).  The
-driver's default is c2.
+default is c2.
 
-Under torchrun (N > 1) every rank advances its own replica of the workload
-(independent problems, no data-path collective: weak scaling); the time is
-the maximum over ranks.  --impl reference times the CPU oracle on the host
+Under torchrun (N > 1) every rank advances its own replica of c1-c3
+(independent problems, no data-path collective: weak scaling), and the 64
+members of c5 are dealt out to the ranks by particle count (strong
+scaling); the time is the maximum over ranks.  --impl reference times the CPU oracle on the host
 cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -39,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_1612_03369_gb300 import workloads as W  # noqa: E402
+from paper_1612_03369_gb300 import shard  # noqa: E402
 
 # Algorithmic bytes per particle-step of the whole step and of the advect
 # kernel (FP64 form, 3D, P properties, u64 ids): each particle's state is
@@ -203,18 +205,8 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e_psteps = parts.stats()["particle_steps"] - stats_e0["particle_steps"]
 
-    tmax = ms
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax, e2e_s = float(t[0]), float(t[1])
-        ps = torch.tensor([psteps, e2e_psteps], device=dev, dtype=torch.float64)
-        dist.all_reduce(ps)
-        psteps_all, e2e_all = float(ps[0]), float(ps[1])
-    else:
-        psteps_all, e2e_all = float(psteps), float(e2e_psteps)
+    (tmax, e2e_s), (psteps_all, e2e_all) = shard.reduce_timing([ms, e2e_s], [psteps, e2e_psteps],
+                                                               device=dev if world > 1 else None)
 
     hbm, peak_kind = load_peaks()
     ppc = float(wl.ppc)
@@ -330,15 +322,24 @@ def run_adjoint(args):
     }
 
 
-def run_ensemble(args):
+def run_ensemble(args, rank=0, world=1, local_rank=0):
     """c5: 64 problems advanced 10 steps per launch of the persistent kernel
     (replayed graph), against the per-step graph and against the problems
-    advanced one after another with pic_advect."""
+    advanced one after another with pic_advect.  Under torchrun the members
+    are dealt out to the ranks by particle count (no collective on the data
+    path; the total work is fixed, so the scaling is strong)."""
     import torch
     from paper_1612_03369_gb300 import pic as P
 
-    wls = W.c5()
-    steps = wls[0].n_steps
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wls_all = W.c5()
+    mine = shard.partition_by_weight([w.n_particles for w in wls_all], world)[rank]
+    wls = [wls_all[i] for i in mine]
+    steps = wls_all[0].n_steps
+    if not wls:  # more ranks than members: this rank idles through the protocol
+        shard.reduce_timing([0.0, 0.0, 0.0], [0.0], device=dev if world > 1 else None)
+        return None
     meshes = [P.Mesh(w.n, w.X, w.U) for w in wls]
     ens = P.Ensemble(meshes, per_cell=[w.per_cell for w in wls], seeds=[w.pseed for w in wls])
     ens.set_dt([w.dt for w in wls])
@@ -373,15 +374,20 @@ def run_ensemble(args):
     e1.record()
     torch.cuda.synchronize()
     solo_ms = e0.elapsed_time(e1) / args.steps
+    (persist_ms, multi_ms, solo_ms), (n_alive,) = shard.reduce_timing([persist_ms, multi_ms, solo_ms], [n_alive],
+                                                                      device=dev if world > 1 else None)
     return {
         "metric": "ensemble RK4 particle-steps/s (advect+locate+rebin), 64 2D Q2 problems, one persistent launch",
-        "value": n_alive * steps / (persist_ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+        "value": n_alive * steps / (persist_ms / 1e3), "unit": "particle-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": persist_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "c5_ensemble_64", "problems": len(wls), "particles": N,
-                   "sides": [w.n[0] for w in wls], "time_steps_per_launch": steps,
-                   "one_benchmark_step": "%d time steps of every problem" % steps},
-        "autotuned": {"blocks_per_sm": tuned[0], "tile": tuned[1], "one_step_ms": tuned[2]},
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c5_ensemble_64", "problems": len(wls_all),
+                   "particles": sum(w.n_particles for w in wls_all),
+                   "sides": [w.n[0] for w in wls_all], "time_steps_per_launch": steps,
+                   "one_benchmark_step": "%d time steps of every problem" % steps,
+                   "parallelism": ("members dealt to %d ranks by particle count" % world) if world > 1
+                   else "single GPU"},
+        "autotuned_rank0": {"blocks_per_sm": tuned[0], "tile": tuned[1], "one_step_ms": tuned[2]},
         "per_step_graph_particle_steps_per_s": n_alive * steps / (multi_ms / 1e3),
         "sequential_solo_particle_steps_per_s": n_alive * steps / (solo_ms / 1e3),
     }
@@ -476,17 +482,16 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local_rank = shard.rank_env()
     if args.impl == "reference":
         res = run_reference(args, rank, world)
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.config in ("c4", "c5"):
-        res = run_adjoint(args) if args.config == "c4" else run_ensemble(args)
-        print(json.dumps(res), flush=True)
+    if args.config == "c4":
+        # one problem with one gradient: rank 0 alone runs it
+        if rank == 0:
+            print(json.dumps(run_adjoint(args)), flush=True)
         return
     if world > 1:
         import torch
@@ -494,7 +499,10 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
+    if args.config == "c5":
+        res = run_ensemble(args, rank, world, local_rank)
+    else:
+        res = run_ours(args, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -258,6 +258,16 @@ def c4(n: int = 32, ppc: int = 32, n_steps: int = 20, seed: int = 4) -> Workload
     return curl_cube(n, ppc, n_steps, seed, name="c4_3d_adjoint")
 
 
+def member_per_cell(side: int, seed: int, sigma: float = 1.0, median: float = 8.0, max_ppc: int = 128) -> np.ndarray:
+    """Particles per cell of one ensemble member (log-normal, R13)."""
+    z = rng(seed, SUB_ENSEMBLE).standard_normal(side * side)
+    return np.minimum(max_ppc, np.rint(np.exp(math.log(median) + sigma * z))).astype(np.uint32)
+
+
+def c5_member_seed(p: int, seed: int = 5) -> int:
+    return seed * 1000 + p
+
+
 def c5_member(side: int, seed: int, sigma: float = 1.0, median: float = 8.0, max_ppc: int = 128,
               n_steps: int = 10) -> Workload:
     """One ensemble member: jittered side^2 quads, stream-function field,
@@ -265,8 +275,7 @@ def c5_member(side: int, seed: int, sigma: float = 1.0, median: float = 8.0, max
     dims = (side, side)
     X = jittered_vertices(dims, seed)
     U = zero_wall_normal(dims, normalise_max(stream_function_field(q2_node_coords(dims, X), seed)))
-    z = rng(seed, SUB_ENSEMBLE).standard_normal(side * side)
-    per_cell = np.minimum(max_ppc, np.rint(np.exp(math.log(median) + sigma * z))).astype(np.uint32)
+    per_cell = member_per_cell(side, seed, sigma, median, max_ppc)
     dt = cfl_dt(dims, X, U, 0.5)
     return Workload("c5_member_%d^2" % side, 2, dims, X, U, None, per_cell, 1, 4, dt, n_steps, seed,
                     particle_seed(seed))
@@ -283,7 +292,7 @@ def c5(n_problems: int = 64, seed: int = 5, scale: float = 1.0) -> list[Workload
     out = []
     for p, s in enumerate(sides):
         s = max(2, int(round(s * scale)))
-        out.append(c5_member(s, seed * 1000 + p))
+        out.append(c5_member(s, c5_member_seed(p, seed)))
     return out
 
 
