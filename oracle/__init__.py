@@ -66,6 +66,9 @@ def _load():
     lib.orc_cell_average_kind.argtypes = [i64, i64, P, P, C.c_int, f64, P, P]
     lib.orc_advect_adjoint.restype = f64
     lib.orc_advect_adjoint.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P, P]
+    lib.orc_advect_properties.restype = i64
+    lib.orc_advect_properties.argtypes = [P, i64, P, P, P, P, P, C.c_int, f64, C.c_int, C.c_int, C.c_int, f64, f64,
+                                          C.c_int, P]
     lib.orc_advect_loss.restype = f64
     lib.orc_advect_loss.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P]
     _lib = lib
@@ -215,6 +218,25 @@ def advect(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: in
     lost = C.c_int64(0)
     n = _load().orc_advect(mesh._h, p.n, _p(p.x), _p(p.xhat), _p(p.cell), _p(p.id), _p(p.props), nprops,
                            float(dt), int(integrator), int(n_steps), C.byref(lost))
+    out = Particles(p.x[:n], p.xhat[:n], p.cell[:n], p.id[:n], p.props[:n])
+    out.n_lost = parts.n_lost + int(lost.value)
+    return out
+
+
+def advect_properties(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, damage: int = -1,
+                      alpha: float = 0.0, beta: float = 0.0, defgrad: int = -1) -> Particles:
+    """advect() with the Sec. 2.6 property ODEs integrated along the paths:
+    property `damage` holds d (d' = alpha |sym grad u| - beta d), properties
+    defgrad .. defgrad + dim^2 - 1 hold F row-major (F' = grad u F); -1 = off."""
+    p = parts.copy()
+    d = mesh.dim
+    nprops = p.props.shape[1] if p.props.ndim == 2 else 0
+    lost = C.c_int64(0)
+    n = _load().orc_advect_properties(mesh._h, p.n, _p(p.x), _p(p.xhat), _p(p.cell), _p(p.id), _p(p.props), nprops,
+                                      float(dt), int(integrator), int(n_steps), int(damage), float(alpha),
+                                      float(beta), int(defgrad), C.byref(lost))
+    if n < 0:
+        raise ValueError("advect_properties: the steady field only")
     out = Particles(p.x[:n], p.xhat[:n], p.cell[:n], p.id[:n], p.props[:n])
     out.n_lost = parts.n_lost + int(lost.value)
     return out

@@ -13,7 +13,7 @@
  * blocking, fusion or reordering: each function follows the paper's
  * statement of the step it computes, and its comment names the section or
  * equation.  Where the paper is silent or its printed formulas are garbled,
- * the reading taken is named R1..R13 (the list of readings is kept with the
+ * the reading taken is named R1..R16 (the list of readings is kept with the
  * design notes of the repository).
  *
  * Layouts (chosen for the oracle alone):
@@ -857,4 +857,156 @@ void orc_cell_average_kind(int64_t ncells, int64_t N, const int64_t *cell, const
   }
   free(sum);
   free(bad);
+}
+
+/* ------------------------------- property ODEs on particles (Sec. 2.6) --- */
+
+/* Right-hand side of the particle system z = (x, d, F) at a located point
+ * (cell K, reference coordinates xhat), Sec. 2.6:
+ *   x' = u_h
+ *   d' = alpha |eps-dot| - beta d,   eps-dot = (G + G^T) / 2,
+ *        |.| the Frobenius norm (reading R15)
+ *   F' = G F                          (F(0) = I, the total deformation)
+ * with G = grad u_h at the point (cell held fixed, as for the adjoint).
+ * z is laid out [x_0..x_{dim-1}, d, F_00, F_01, .., F_{dim-1,dim-1}]. */
+static void props_rhs(const orc_mesh *m, int64_t K, const double *xhat, const double *z, int use_damage,
+                      double alpha, double beta, int use_defgrad, double *f) {
+  int d = m->dim;
+  double u[3] = {0, 0, 0}, G[3][3] = {{0}};
+  orc_q2_eval(m, K, xhat, u);
+  for (int j = 0; j < d; ++j) f[j] = u[j];
+  f[d] = 0.0;
+  for (int q = 0; q < d * d; ++q) f[d + 1 + q] = 0.0;
+  if (!use_damage && !use_defgrad) return;
+  velocity_jacobian(m, K, xhat, G);
+  if (use_damage) {
+    double s = 0.0;
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        double e = 0.5 * (G[r][c] + G[c][r]);
+        s = s + e * e;
+      }
+    f[d] = alpha * sqrt(s) - beta * z[d];
+  }
+  if (use_defgrad) {
+    const double *F = z + d + 1;
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        double acc = 0.0;
+        for (int q = 0; q < d; ++q) acc = acc + G[r][q] * F[q * d + c];
+        f[d + 1 + r * d + c] = acc;
+      }
+  }
+}
+
+/* One step of the coupled system with the integrators of step_particle
+ * (reading R5), every stage point located before the right-hand side is
+ * evaluated there (R7).  The position part is the same arithmetic as
+ * step_particle.  Returns 0 if the particle is lost. */
+static int step_particle_props(const orc_mesh *m, orc_particle *p, double *z_in, double dt, int integrator,
+                               int use_damage, double alpha, double beta, int use_defgrad) {
+  int d = m->dim, nz = d + 1 + d * d;
+  double z[13], y[13], f[13], k1[13], k2[13], k3[13], k4[13], zn[13], t[3] = {0, 0, 0};
+  for (int q = 0; q < nz; ++q) z[q] = z_in[q];
+  for (int j = 0; j < d; ++j) z[j] = p->x[j];
+  props_rhs(m, p->cell, p->xhat, z, use_damage, alpha, beta, use_defgrad, f);
+  for (int q = 0; q < nz; ++q) k1[q] = dt * f[q];
+  if (integrator == 1) {
+    for (int q = 0; q < nz; ++q) zn[q] = z[q] + k1[q];
+  } else if (integrator == 2) {
+    int64_t K;
+    for (int q = 0; q < nz; ++q) y[q] = z[q] + 0.5 * k1[q];
+    if ((K = orc_owner(m, y, t)) < 0) return 0;
+    props_rhs(m, K, t, y, use_damage, alpha, beta, use_defgrad, f);
+    for (int q = 0; q < nz; ++q) k2[q] = dt * f[q];
+    for (int q = 0; q < nz; ++q) zn[q] = z[q] + k2[q];
+  } else {
+    int64_t K;
+    for (int q = 0; q < nz; ++q) y[q] = z[q] + 0.5 * k1[q];
+    if ((K = orc_owner(m, y, t)) < 0) return 0;
+    props_rhs(m, K, t, y, use_damage, alpha, beta, use_defgrad, f);
+    for (int q = 0; q < nz; ++q) k2[q] = dt * f[q];
+    for (int q = 0; q < nz; ++q) y[q] = z[q] + 0.5 * k2[q];
+    if ((K = orc_owner(m, y, t)) < 0) return 0;
+    props_rhs(m, K, t, y, use_damage, alpha, beta, use_defgrad, f);
+    for (int q = 0; q < nz; ++q) k3[q] = dt * f[q];
+    for (int q = 0; q < nz; ++q) y[q] = z[q] + k3[q];
+    if ((K = orc_owner(m, y, t)) < 0) return 0;
+    props_rhs(m, K, t, y, use_damage, alpha, beta, use_defgrad, f);
+    for (int q = 0; q < nz; ++q) k4[q] = dt * f[q];
+    for (int q = 0; q < nz; ++q) zn[q] = z[q] + (k1[q] + 2.0 * k2[q] + 2.0 * k3[q] + k4[q]) / 6.0;
+  }
+  int64_t K = orc_owner(m, zn, t);
+  if (K < 0) return 0;
+  for (int j = 0; j < d; ++j) {
+    p->x[j] = zn[j];
+    p->xhat[j] = t[j];
+  }
+  p->cell = K;
+  for (int q = d; q < nz; ++q) z_in[q] = zn[q];
+  return 1;
+}
+
+/* orc_advect with the Sec. 2.6 property ODEs integrated along the particle
+ * paths: property slot `damage` holds d (or -1 = none), slots
+ * defgrad .. defgrad + dim^2 - 1 hold F row-major (or defgrad = -1).  Other
+ * properties ride along unchanged.  The steady field only (a second field
+ * set returns -1).  Returns the number alive; *n_lost_out gets the rest. */
+int64_t orc_advect_properties(const orc_mesh *m, int64_t N, double *x, double *xhat, int64_t *cell, uint64_t *id,
+                              double *props, int n_props, double dt, int integrator, int n_steps, int damage,
+                              double alpha, double beta, int defgrad, int64_t *n_lost_out) {
+  if (m->Unext) return -1;
+  int d = m->dim;
+  int use_damage = damage >= 0, use_defgrad = defgrad >= 0;
+  orc_particle *P = (orc_particle *)calloc(N > 0 ? N : 1, sizeof(orc_particle));
+  double *pool = (double *)malloc(sizeof(double) * (N * n_props + 1));
+  for (int64_t i = 0; i < N; ++i) {
+    P[i].id = id[i];
+    P[i].cell = cell[i];
+    for (int j = 0; j < d; ++j) {
+      P[i].x[j] = x[i * d + j];
+      P[i].xhat[j] = xhat[i * d + j];
+    }
+    P[i].props = pool + i * n_props;
+    for (int q = 0; q < n_props; ++q) P[i].props[q] = props[i * n_props + q];
+  }
+  int64_t n = N, lost = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    for (int64_t i = 0; i < n; ++i) {
+      double z[13] = {0};
+      if (use_damage) z[d] = P[i].props[damage];
+      if (use_defgrad)
+        for (int q = 0; q < d * d; ++q) z[d + 1 + q] = P[i].props[defgrad + q];
+      if (!step_particle_props(m, &P[i], z, dt, integrator, use_damage, alpha, beta, use_defgrad)) {
+        P[i].cell = -1;
+        continue;
+      }
+      if (use_damage) P[i].props[damage] = z[d];
+      if (use_defgrad)
+        for (int q = 0; q < d * d; ++q) P[i].props[defgrad + q] = z[d + 1 + q];
+    }
+    int64_t w = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (P[i].cell < 0) {
+        ++lost;
+        continue;
+      }
+      P[w++] = P[i];
+    }
+    n = w;
+    qsort(P, (size_t)n, sizeof(orc_particle), cmp_cell_id);
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    id[i] = P[i].id;
+    cell[i] = P[i].cell;
+    for (int j = 0; j < d; ++j) {
+      x[i * d + j] = P[i].x[j];
+      xhat[i * d + j] = P[i].xhat[j];
+    }
+    for (int q = 0; q < n_props; ++q) props[i * n_props + q] = P[i].props[q];
+  }
+  free(pool);
+  free(P);
+  if (n_lost_out) *n_lost_out = lost;
+  return n;
 }
