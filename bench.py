@@ -14,8 +14,8 @@ so no L2 flush is needed between steps.
 
 c3 is the precision form (FP32 basis) at 128^3; c4 times the adjoint
 (recorded forward + reverse sweep) at 32^3 x 32 per cell over 20 steps; c5
-times the 64-problem ensemble (10 steps per persistent graph launch).  The
-default is c2.
+times the 64-problem ensemble (10 steps per persistent graph launch); c2p
+times c2 with the damage and deformation-gradient ODEs.  The default is c2.
 
 Under torchrun (N > 1) every rank advances its own replica of c1-c3
 (independent problems, no data-path collective: weak scaling), and the 64
@@ -393,6 +393,46 @@ def run_ensemble(args, rank=0, world=1, local_rank=0):
     }
 
 
+def run_props(args):
+    """c2 with the Sec. 2.6 property ODEs: every step also integrates the
+    damage variable and the 3x3 deformation gradient (FP64 velocity gradient
+    at every stage) on top of advect+locate+rebin."""
+    import torch
+    from paper_1612_03369_gb300 import pic as P
+
+    wl = W.c2()
+    mesh = P.Mesh(wl.n, wl.X, wl.U)
+    n_props = 3 + 1 + 9
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=n_props)
+    N = parts.state()[0]
+    st = parts.export()
+    for q in range(3):
+        parts.set_property(q, st["x"][q].contiguous())
+    del st
+    eye = np.eye(3).reshape(-1)
+    for q in range(9):
+        parts.set_property(4 + q, torch.full((N,), float(eye[q]), dtype=torch.float64, device="cuda"))
+    odes = dict(damage=3, alpha=1.0, beta=0.5, deformation=4)
+    parts.advect_properties(wl.dt, wl.integrator, args.warmup, **odes)
+    torch.cuda.synchronize()
+    s0 = parts.stats()["particle_steps"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    parts.advect_properties(wl.dt, wl.integrator, args.steps, **odes)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ps = parts.stats()["particle_steps"] - s0
+    return {
+        "metric": "RK4 particle-steps/s with damage + deformation-gradient ODEs (advect+ODEs+locate+rebin), 3D Q2",
+        "value": ps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "c2_props_64^3", "particles": N, "n_props": n_props,
+                   "odes": "damage (slot 3), F row-major (slots 4-12)"},
+    }
+
+
 def roofline_object(args, adv_avg_ms, particles, adv_bytes, hbm_achieved, hbm, peak_kind, rebin_ms):
     """The advect kernel's roofline.  It is bound by FP32 issue (double-float
     arithmetic), so its roofline is the FP32 ALU peak; its HBM fraction is
@@ -476,7 +516,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2p"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -488,10 +528,10 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.config == "c4":
-        # one problem with one gradient: rank 0 alone runs it
+    if args.config in ("c4", "c2p"):
+        # one problem: rank 0 alone runs it
         if rank == 0:
-            print(json.dumps(run_adjoint(args)), flush=True)
+            print(json.dumps(run_adjoint(args) if args.config == "c4" else run_props(args)), flush=True)
         return
     if world > 1:
         import torch

@@ -140,6 +140,33 @@ pic_status pic_set_properties(pic_particles parts, int prop, const double *value
 pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
                       pic_precision precision, int n_steps, void *stream);
 
+/* Property ODEs integrated along the particle paths (Sec. 2.6):
+ *   damage               d' = alpha |eps-dot| - beta d,  eps-dot = (G + G^T)/2,
+ *                        |.| the Frobenius norm
+ *   deformation gradient F' = G F  (start from F = I with pic_set_properties)
+ * with G = grad u_h at the particle.  Both ride on the position as one
+ * system, stepped by the same integrator over the same located stage points,
+ * so positions, cells and order are exactly those of pic_advect (FP64 form);
+ * G is evaluated in FP64 at every stage.
+ *   damage       property slot of d, or -1
+ *   alpha, beta  material parameters of the damage law (finite)
+ *   deformation  first of dim*dim consecutive property slots holding F
+ *                row-major (F_ij in slot deformation + i*dim + j), or -1 */
+typedef struct {
+  int damage;
+  double alpha, beta;
+  int deformation;
+} pic_property_odes;
+
+/* n_steps of pic_advect (FP64 form) that also advance the properties of
+ * `odes` (host struct, read during the call).  Other properties ride along.
+ * Errors: PIC_ERR_ARG (as pic_advect; a slot outside the store's properties;
+ * damage overlapping the deformation slots), PIC_ERR_STATE (the mesh carries
+ * a second velocity field: the property ODEs take the steady field),
+ * PIC_ERR_CUDA. */
+pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                                 int n_steps, const pic_property_odes *odes, void *stream);
+
 /* Adjoint (gradients with respect to the velocity field).
  * pic_advect_record: n_steps of pic_advect (FP64 form) that also keep, for
  * every step, the store at the start of the step (x, x-hat, cell) and the

@@ -122,13 +122,22 @@ struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x +
 #define PIC_ADVECT_MIN_BLOCKS 5
 #endif
 
+// Per-stage work riding on the position integration: hook.stage(p, K, t) is
+// called at every evaluation point p < S with its located cell and double-
+// float reference coordinates.  The plain advection passes NoHook, which
+// compiles to nothing.
+struct NoHook {
+  template <int D>
+  __device__ __forceinline__ void stage(int, uint32_t, const df*) {}
+};
+
 // One time step of particle i of store s in mesh m, starting in cell K.
 // TWO: the mesh carries a second field (time interpolation).
 // Writes the new x and x-hat in place when the particle survives and returns
 // its new cell, or PIC_LOST.
-template <int D, int RK, bool F32B, bool TWO = false>
+template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>
 __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const StoreView& s, uint32_t i, uint32_t K,
-                                                    df dt, int& iters, unsigned& flags) {
+                                                    df dt, int& iters, unsigned& flags, Hook&& hook = Hook()) {
   using TB = Tableau<RK>;
   const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);  // 1/6 = hi + lo
   if (K >= m.C) {
@@ -160,6 +169,7 @@ __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const Sto
       if (Ks == PIC_LOST) return PIC_LOST;
       if (p == TB::S) break;
     }
+    hook.template stage<D>(p, Ks, ts);
     df u[D];
     velocity<D, F32B, TWO>(m, Ks, ts, TB::tcode(p), u);
     const float w = TB::w(p);

@@ -34,6 +34,7 @@ SIGNATURES = {
     "pic_destroy_particles": (_I, [_P]),
     "pic_set_properties": (_I, [_P, _I, _P, _P]),
     "pic_advect": (_I, [_P, _P, _F64, _I, _I, _I, _P]),
+    "pic_advect_properties": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
     "pic_locate": (_I, [_P, _P, _P]),
     "pic_advect_record": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
     "pic_tape_adjoint": (_I, [_P, _P, _P, _P, _P]),
@@ -142,6 +143,18 @@ def pic_set_properties(h: int, prop: int, values, stream=None):
 def pic_advect(parts: int, mesh: int, dt: float, integrator: int, precision: int, n_steps: int, stream=None):
     _check(_lib.pic_advect(parts, mesh, float(dt), int(integrator), int(precision), int(n_steps), _stream(stream)),
            "pic_advect")
+
+
+class PropertyOdes(C.Structure):
+    """pic_property_odes: damage slot (or -1), alpha, beta, first deformation slot (or -1)."""
+    _fields_ = [("damage", C.c_int), ("alpha", C.c_double), ("beta", C.c_double), ("deformation", C.c_int)]
+
+
+def pic_advect_properties(parts: int, mesh: int, dt: float, integrator: int, n_steps: int, damage: int = -1,
+                          alpha: float = 0.0, beta: float = 0.0, deformation: int = -1, stream=None):
+    odes = PropertyOdes(int(damage), float(alpha), float(beta), int(deformation))
+    _check(_lib.pic_advect_properties(parts, mesh, float(dt), int(integrator), int(n_steps), C.byref(odes),
+                                      _stream(stream)), "pic_advect_properties")
 
 
 def pic_advect_record(parts: int, mesh: int, dt: float, integrator: int, n_steps: int, stream=None) -> int:
@@ -316,6 +329,11 @@ class Particles:
         if per_cell is not None:
             pc = torch.as_tensor(np.ascontiguousarray(per_cell, dtype=np.uint32).view(np.int32), device="cuda")
         self.h = pic_seed_particles(mesh.h, pc, uniform_count, seed, first_id, n_props, capacity, stream)
+
+    def advect_properties(self, dt, integrator=PIC_RK4, n_steps=1, damage=-1, alpha=0.0, beta=0.0, deformation=-1,
+                          stream=None):
+        """advect() that also integrates the damage and deformation-gradient ODEs (Sec. 2.6)."""
+        pic_advect_properties(self.h, self.mesh.h, dt, integrator, n_steps, damage, alpha, beta, deformation, stream)
 
     def advect(self, dt, integrator=PIC_RK4, n_steps=1, precision=PIC_FP64, stream=None):
         pic_advect(self.h, self.mesh.h, dt, integrator, precision, n_steps, stream)
