@@ -69,6 +69,8 @@ def _load():
     lib.orc_advect_properties.restype = i64
     lib.orc_advect_properties.argtypes = [P, i64, P, P, P, P, P, C.c_int, f64, C.c_int, C.c_int, C.c_int, f64, f64,
                                           C.c_int, P]
+    lib.orc_vertex_average.argtypes = [P, i64, P, P, P, f64, P, P]
+    lib.orc_cell_lsq_linear.argtypes = [P, i64, P, P, P, f64, P, P]
     lib.orc_advect_loss.restype = f64
     lib.orc_advect_loss.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P]
     _lib = lib
@@ -252,6 +254,32 @@ def cell_average(ncells: int, cell, value, empty_fill: float = 0.0, kind: int = 
     _load().orc_cell_average_kind(int(ncells), int(cell.shape[0]), _p(cell), _p(value), int(kind), float(empty_fill),
                                   _p(avg), _p(cnt))
     return avg, cnt
+
+
+def vertex_average(mesh: Mesh, cell, xhat, value, empty_fill: float = 0.0):
+    """Sec. 2.7 (iv): shape-function-weighted average at the mesh vertices
+    (R17).  Returns (avg [nverts], weight sum [nverts])."""
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    xhat = np.ascontiguousarray(xhat, dtype=np.float64)
+    value = np.ascontiguousarray(value, dtype=np.float64)
+    nv = mesh.X.shape[1]
+    avg, w = np.zeros(nv), np.zeros(nv)
+    _load().orc_vertex_average(mesh._h, int(cell.shape[0]), _p(cell), _p(xhat), _p(value), float(empty_fill), _p(avg),
+                               _p(w))
+    return avg, w
+
+
+def cell_lsq_linear(mesh: Mesh, cell, xhat, value, empty_fill: float = 0.0):
+    """Sec. 2.7 (v): per-cell linear least squares in reference coordinates
+    (R18).  Returns (coef [ncells][dim+1], count [ncells])."""
+    cell = np.ascontiguousarray(cell, dtype=np.int64)
+    xhat = np.ascontiguousarray(xhat, dtype=np.float64)
+    value = np.ascontiguousarray(value, dtype=np.float64)
+    coef = np.zeros((mesh.ncells, mesh.dim + 1))
+    cnt = np.zeros(mesh.ncells, dtype=np.int64)
+    _load().orc_cell_lsq_linear(mesh._h, int(cell.shape[0]), _p(cell), _p(xhat), _p(value), float(empty_fill),
+                                _p(coef), _p(cnt))
+    return coef, cnt
 
 
 def advect_adjoint(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, targets):

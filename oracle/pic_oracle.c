@@ -1010,3 +1010,112 @@ int64_t orc_advect_properties(const orc_mesh *m, int64_t N, double *x, double *x
   if (n_lost_out) *n_lost_out = lost;
   return n;
 }
+
+/* ------------------ particle -> field transfer, Sec. 2.7 (iv) and (v) --- */
+
+/* (iv) Shape-function-weighted averaging (reading R17): the value at mesh
+ * vertex v is
+ *     p_v = sum_i phi_v(x_i) p_i / sum_i phi_v(x_i)
+ * over the particles i in the support of phi_v, the (bi/tri)linear nodal
+ * basis function of v.  In the particle's cell K, phi_v(x_i) is the map's
+ * weight of v's local vertex at the particle's reference coordinates.  Both
+ * sums are left folds over the particles in store order (cell, then id).
+ * A vertex whose weights sum to 0 gets empty_fill; weight[v] is that sum. */
+void orc_vertex_average(const orc_mesh *m, int64_t N, const int64_t *cell, const double *xhat, const double *value,
+                        double empty_fill, double *avg, double *weight) {
+  int d = m->dim;
+  double *num = (double *)calloc(m->nverts > 0 ? m->nverts : 1, sizeof(double));
+  for (int64_t v = 0; v < m->nverts; ++v) weight[v] = 0.0;
+  for (int64_t p = 0; p < N; ++p) {
+    int64_t i, j, k;
+    cell_ijk(m, cell[p], &i, &j, &k);
+    for (int lv = 0; lv < (1 << d); ++lv) {
+      int64_t vi = i + (lv & 1), vj = j + ((lv >> 1) & 1), vk = k + (d == 3 ? ((lv >> 2) & 1) : 0);
+      int64_t v = vi + m->nv[0] * (vj + m->nv[1] * vk);
+      double w = vertex_weight(d, lv, xhat + p * d);
+      num[v] = num[v] + w * value[p];
+      weight[v] = weight[v] + w;
+    }
+  }
+  for (int64_t v = 0; v < m->nverts; ++v) avg[v] = weight[v] > 0.0 ? num[v] / weight[v] : empty_fill;
+  free(num);
+}
+
+/* (v) Linear least-squares projection (reading R18): in every cell, the
+ * function f(xhat) = c_0 + sum_j c_{j+1} (xhat_j - 1/2), linear in the
+ * reference coordinates, that minimises sum_{i in K} (f(xhat_i) - p_i)^2.
+ * The minimiser solves the normal equations (A^T A) c = A^T p, A the cell's
+ * design matrix with rows (1, xhat_i - 1/2); A^T A and A^T p are left folds
+ * in store order, and the system is solved by Gaussian elimination with
+ * partial pivoting.  A cell with at most dim particles, or whose elimination
+ * meets a pivot <= 1e-12 times the largest diagonal entry of A^T A, gets the
+ * arithmetic mean (c_0 = mean, slopes 0); an empty cell gets c_0 =
+ * empty_fill.  coef is [ncells][dim+1]; count[K] is the cell's particles. */
+void orc_cell_lsq_linear(const orc_mesh *m, int64_t N, const int64_t *cell, const double *xhat, const double *value,
+                         double empty_fill, double *coef, int64_t *count) {
+  int d = m->dim, nb = d + 1;
+  int64_t C = m->ncells;
+  double *M = (double *)calloc((size_t)(C > 0 ? C : 1) * 16, sizeof(double));
+  double *b = (double *)calloc((size_t)(C > 0 ? C : 1) * 4, sizeof(double));
+  double *sum = (double *)calloc((size_t)(C > 0 ? C : 1), sizeof(double));
+  for (int64_t K = 0; K < C; ++K) count[K] = 0;
+  for (int64_t p = 0; p < N; ++p) {
+    int64_t K = cell[p];
+    double a[4];
+    a[0] = 1.0;
+    for (int j = 0; j < d; ++j) a[j + 1] = xhat[p * d + j] - 0.5;
+    for (int r = 0; r < nb; ++r) {
+      for (int c = 0; c < nb; ++c) M[K * 16 + r * 4 + c] = M[K * 16 + r * 4 + c] + a[r] * a[c];
+      b[K * 4 + r] = b[K * 4 + r] + a[r] * value[p];
+    }
+    sum[K] = sum[K] + value[p];
+    count[K] += 1;
+  }
+  for (int64_t K = 0; K < C; ++K) {
+    double *c = coef + K * nb;
+    for (int r = 0; r < nb; ++r) c[r] = 0.0;
+    if (count[K] == 0) {
+      c[0] = empty_fill;
+      continue;
+    }
+    int ok = count[K] > d;
+    double A[4][5];
+    double dmax = 0.0;
+    for (int r = 0; r < nb; ++r) {
+      for (int q = 0; q < nb; ++q) A[r][q] = M[K * 16 + r * 4 + q];
+      A[r][nb] = b[K * 4 + r];
+      if (A[r][r] > dmax) dmax = A[r][r];
+    }
+    for (int col = 0; col < nb && ok; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < nb; ++r)
+        if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+      if (!(fabs(A[piv][col]) > 1e-12 * dmax)) {
+        ok = 0;
+        break;
+      }
+      if (piv != col)
+        for (int q = 0; q <= nb; ++q) {
+          double t = A[col][q];
+          A[col][q] = A[piv][q];
+          A[piv][q] = t;
+        }
+      for (int r = col + 1; r < nb; ++r) {
+        double f = A[r][col] / A[col][col];
+        for (int q = col; q <= nb; ++q) A[r][q] = A[r][q] - f * A[col][q];
+      }
+    }
+    if (!ok) {
+      c[0] = sum[K] / (double)count[K];
+      continue;
+    }
+    for (int r = nb - 1; r >= 0; --r) {
+      double s = A[r][nb];
+      for (int q = r + 1; q < nb; ++q) s = s - A[r][q] * c[q];
+      c[r] = s / A[r][r];
+    }
+  }
+  free(M);
+  free(b);
+  free(sum);
+}
