@@ -181,6 +181,22 @@ def run_ours(args, rank, world, local_rank):
     psteps = stats1["particle_steps"] - stats0["particle_steps"]
     n1, nlost, status = parts.state()
 
+    # ---- the other particle -> field transfers (Sec. 2.7), timed on their
+    # own after the step loop: shape-function-weighted vertex averages (iv)
+    # and the per-cell linear least squares (v) of property 0
+    xfer = {}
+    for name, fn in (("cell_average_ms", lambda: parts.average(0)),
+                     ("vertex_average_ms", lambda: parts.vertex_average(0)),
+                     ("project_linear_ms", lambda: parts.project_linear(0))):
+        for _ in range(3):
+            fn()
+        e0.record(stream)
+        for _ in range(10):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xfer[name] = e0.elapsed_time(e1) / 10
+
     # ---- end to end through the C ABI with host buffers: every step copies
     # the step's velocity DOFs host->device (a flow solver hands over a new
     # field each step), advances one step, averages the properties per cell
@@ -238,6 +254,7 @@ def run_ours(args, rank, world, local_rank):
         "step_algorithmic_bytes_per_particle_step": sbytes,
         "roofline": roofline_object(args, adv_avg_ms, per_launch_particles, adv_bytes, achieved, hbm, peak_kind,
                                     reb_ms / max(nsteps, 1)),
+        "transfers_one_property": xfer,
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": e2e_all / e2e_s, "unit": "particle-steps/s",

@@ -312,6 +312,35 @@ pic_status pic_sort_by_cell_noalloc(size_t n, const uint32_t *cell, const uint64
 pic_status pic_interpolate_to_cells(pic_particles parts, pic_mesh mesh, int prop, pic_average kind, double *avg,
                                     uint32_t *count, double empty_fill, void *stream);
 
+/* Particle -> field transfer (Sec. 2.7, scheme (iv)): shape-function-weighted
+ * averages at the mesh vertices,
+ *   avg[v] = sum_i phi_v(x_i) p_i / sum_i phi_v(x_i)
+ * over the particles i of the cells around vertex v, phi_v the (bi/tri)linear
+ * nodal basis function of v (in a particle's cell: the map weight of v's
+ * corner at the stored x-hat).  Each cell's particles are summed in store
+ * order, then the cells' sums in increasing cell index (deterministic).  The
+ * value at a quadrature point is the Q1 interpolation of avg.  The first
+ * call allocates 2^(dim+4) bytes per cell of scratch, kept with the store.
+ *   avg     [nverts] FP64 device, vertex (i,j,k) at i + (n0+1)(j + (n1+1)k)
+ *   weight  [nverts] FP64 device, the sum of the weights, or NULL
+ * A vertex whose weights sum to 0 gets empty_fill.
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_interpolate_to_vertices(pic_particles parts, pic_mesh mesh, int prop, double *avg, double *weight,
+                                       double empty_fill, void *stream);
+
+/* Particle -> field transfer (Sec. 2.7, scheme (v)): per cell, the linear
+ * least-squares fit in reference coordinates,
+ *   f(x-hat) = c_0 + sum_j c_{j+1} (x-hat_j - 1/2)
+ * minimising sum over the cell's particles of (f(x-hat_i) - p_i)^2.  Solved
+ * from the normal equations (folded in store order) by Gaussian elimination
+ * with partial pivoting.  A cell with at most dim particles, or a pivot
+ * <= 1e-12 times the largest diagonal entry, gets the mean (c_0 = mean,
+ * slopes 0); an empty cell gets c_0 = empty_fill.
+ *   coef   [dim+1][n_cells] FP64 device;  count  [n_cells] u32 device or NULL
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_project_linear(pic_particles parts, pic_mesh mesh, int prop, double *coef, uint32_t *count,
+                              double empty_fill, void *stream);
+
 /* Synchronises the particle stream and reads the state: alive particles,
  * particles lost since seeding, and the device status word (bits above).
  * Any output pointer may be NULL. */

@@ -44,6 +44,8 @@ SIGNATURES = {
     "pic_sort_by_cell": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
     "pic_sort_by_cell_noalloc": (_I, [_SZ, _P, _P, _U32, _P, _P, _P]),
     "pic_interpolate_to_cells": (_I, [_P, _P, _I, _I, _P, _P, _F64, _P]),
+    "pic_interpolate_to_vertices": (_I, [_P, _P, _I, _P, _P, _F64, _P]),
+    "pic_project_linear": (_I, [_P, _P, _I, _P, _P, _F64, _P]),
     "pic_get_state": (_I, [_P, _P, _P, _P]),
     "pic_get_stats": (_I, [_P, _P, _P, _P, _P]),
     "pic_get_counters": (_I, [_P, _P, _I]),
@@ -226,6 +228,17 @@ def pic_interpolate_to_cells(parts: int, mesh: int, prop: int, avg, count=None, 
                                          _stream(stream)), "pic_interpolate_to_cells")
 
 
+def pic_interpolate_to_vertices(parts: int, mesh: int, prop: int, avg, weight=None, empty_fill: float = 0.0,
+                                stream=None):
+    _check(_lib.pic_interpolate_to_vertices(parts, mesh, int(prop), _ptr(avg), _ptr(weight), float(empty_fill),
+                                            _stream(stream)), "pic_interpolate_to_vertices")
+
+
+def pic_project_linear(parts: int, mesh: int, prop: int, coef, count=None, empty_fill: float = 0.0, stream=None):
+    _check(_lib.pic_project_linear(parts, mesh, int(prop), _ptr(coef), _ptr(count), float(empty_fill),
+                                   _stream(stream)), "pic_project_linear")
+
+
 def pic_get_state(parts: int):
     na, nl, st = C.c_size_t(), C.c_size_t(), C.c_uint32()
     _check(_lib.pic_get_state(parts, C.byref(na), C.byref(nl), C.byref(st)), "pic_get_state")
@@ -360,6 +373,25 @@ class Particles:
         cnt = torch.empty(self.mesh.ncells, dtype=torch.int32, device="cuda")
         pic_interpolate_to_cells(self.h, self.mesh.h, prop, avg, cnt, empty_fill, kind=kind, stream=stream)
         return avg, cnt
+
+    def vertex_average(self, prop, empty_fill=0.0, stream=None):
+        """Sec. 2.7 (iv): shape-function-weighted averages at the vertices -> (avg, weight sums)."""
+        import torch
+
+        nv = int(np.prod([k + 1 for k in self.mesh.n]))
+        avg = torch.empty(nv, dtype=torch.float64, device="cuda")
+        w = torch.empty(nv, dtype=torch.float64, device="cuda")
+        pic_interpolate_to_vertices(self.h, self.mesh.h, prop, avg, w, empty_fill, stream)
+        return avg, w
+
+    def project_linear(self, prop, empty_fill=0.0, stream=None):
+        """Sec. 2.7 (v): per-cell linear least squares -> (coef [dim+1][C], counts)."""
+        import torch
+
+        coef = torch.empty((self.mesh.dim + 1, self.mesh.ncells), dtype=torch.float64, device="cuda")
+        cnt = torch.empty(self.mesh.ncells, dtype=torch.int32, device="cuda")
+        pic_project_linear(self.h, self.mesh.h, prop, coef, cnt, empty_fill, stream)
+        return coef, cnt
 
     def export(self, stream=None):
         """Store contents as torch device tensors in (cell, id) order."""
