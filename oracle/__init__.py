@@ -71,6 +71,12 @@ def _load():
                                           C.c_int, P]
     lib.orc_vertex_average.argtypes = [P, i64, P, P, P, f64, P, P]
     lib.orc_cell_lsq_linear.argtypes = [P, i64, P, P, P, f64, P, P]
+    lib.orc_cell_weights.argtypes = [P, P, P]
+    lib.orc_draw_cell_counts.argtypes = [i64, P, i64, u64, P]
+    lib.orc_seed_mh.restype = i64
+    lib.orc_seed_mh.argtypes = [P, P, P, u32, u64, u64, P, P, P, P]
+    lib.orc_import.restype = i64
+    lib.orc_import.argtypes = [P, i64, P, u64, P, P, P, P]
     lib.orc_advect_loss.restype = f64
     lib.orc_advect_loss.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P]
     _lib = lib
@@ -209,6 +215,49 @@ def seed_particles(mesh: Mesh, per_cell=None, uniform_count: int = 0, seed: int 
                          _p(x), _p(xh), _p(cell), _p(ids))
     assert n == N
     return Particles(x, xh, cell, ids, np.zeros((N, n_props)))
+
+
+def cell_weights(mesh: Mesh, rho) -> np.ndarray:
+    """Sec. 2.2: w_K = int_K rho_h dx for a (bi/tri)linear density given at the vertices."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    assert rho.shape == (mesh.X.shape[1],)
+    w = np.zeros(mesh.ncells)
+    _load().orc_cell_weights(mesh._h, _p(rho), _p(w))
+    return w
+
+
+def draw_cell_counts(w, n_particles: int, seed: int) -> np.ndarray:
+    """Sec. 2.2 listing: n_particles draws over the accumulated weights (R19)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    counts = np.zeros(w.shape[0], dtype=np.int64)
+    _load().orc_draw_cell_counts(int(w.shape[0]), _p(w), int(n_particles), C.c_uint64(seed & (2**64 - 1)),
+                                 _p(counts))
+    return counts
+
+
+def seed_particles_mh(mesh: Mesh, per_cell, rho, thinning: int, seed: int, first_id: int = 0,
+                      n_props: int = 0) -> Particles:
+    """Sec. 2.2 in-cell Metropolis-Hastings generation with density rho (R20)."""
+    pc = np.ascontiguousarray(per_cell, dtype=np.uint32)
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    N = int(pc.sum())
+    d = mesh.dim
+    x, xh = np.zeros((N, d)), np.zeros((N, d))
+    cell, ids = np.zeros(N, dtype=np.int64), np.zeros(N, dtype=np.uint64)
+    n = _load().orc_seed_mh(mesh._h, _p(pc), _p(rho), int(thinning), C.c_uint64(seed & (2**64 - 1)),
+                            C.c_uint64(first_id), _p(x), _p(xh), _p(cell), _p(ids))
+    assert n == N
+    return Particles(x, xh, cell, ids, np.zeros((N, n_props)))
+
+
+def import_points(mesh: Mesh, x, first_id: int = 0, n_props: int = 0) -> Particles:
+    """Sec. 2.2 prescribed locations: owner search for every point, ids in input order."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, mesh.dim)
+    n, d = x.shape
+    xo, xh = np.zeros((n, d)), np.zeros((n, d))
+    cell, ids = np.zeros(n, dtype=np.int64), np.zeros(n, dtype=np.uint64)
+    c = _load().orc_import(mesh._h, n, _p(x), C.c_uint64(first_id), _p(xo), _p(xh), _p(cell), _p(ids))
+    return Particles(xo[:c], xh[:c], cell[:c], ids[:c], np.zeros((c, n_props)))
 
 
 def advect(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int) -> Particles:

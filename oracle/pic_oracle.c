@@ -1119,3 +1119,180 @@ void orc_cell_lsq_linear(const orc_mesh *m, int64_t N, const int64_t *cell, cons
   free(b);
   free(sum);
 }
+
+/* ----------------------- generation with a density rho(x), Sec. 2.2 --- */
+
+/* Global index of local vertex v of cell K. */
+static int64_t cell_vertex_index(const orc_mesh *m, int64_t K, int v) {
+  int64_t i, j, k;
+  cell_ijk(m, K, &i, &j, &k);
+  return (i + (v & 1)) + m->nv[0] * ((j + ((v >> 1) & 1)) + m->nv[1] * (k + ((v >> 2) & 1)));
+}
+
+/* det J by cofactors of the first row, summed left to right:
+ *   2D  J00 J11 - J01 J10
+ *   3D  J00 (J11 J22 - J12 J21) + J01 (J12 J20 - J10 J22) + J02 (J10 J21 - J11 J20) */
+static double det_small(int d, double J[3][3]) {
+  if (d == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  double c0 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  double c1 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  double c2 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  return J[0][0] * c0 + J[0][1] * c1 + J[0][2] * c2;
+}
+
+/* The density pulled back to the reference cell (Sec. 2.2, MH paragraph):
+ *   rho-hat(xhat) = rho_h(Phi_K(xhat)) |det grad-hat Phi_K(xhat)|
+ * with rho_h the (bi/tri)linear interpolant of the vertex values, which on
+ * cell K is sum_v rho_{K,v} w_v(xhat).  Written operation order (the GPU
+ * evaluates the same sequence of IEEE operations, so that the acceptance
+ * decisions agree exactly): rho_h summed over local vertices v = 0..2^d-1
+ * with w_v the product over axes in order (vertex_weight); J_ij summed over v
+ * in order of X_{K,v,i} * dw_v/dt_j (phi_jacobian); det by det_small. */
+static double rho_hat(const orc_mesh *m, int64_t K, const double *rho, const double *t) {
+  int d = m->dim;
+  double r = 0.0, J[3][3] = {{0}};
+  for (int v = 0; v < (1 << d); ++v) r = r + rho[cell_vertex_index(m, K, v)] * vertex_weight(d, v, t);
+  phi_jacobian(m, K, t, J);
+  return r * fabs(det_small(d, J));
+}
+
+/* Cell weights w_K = int_K rho_h dx (first loop of the Sec. 2.2 listing),
+ * by the tensor 2-point Gauss rule on the reference cell: nodes
+ * 1/2 -+ 1/(2 sqrt 3), weights 1/2 per axis.  rho_h |det J| has degree <= 3
+ * in each reference coordinate on (bi/tri)linear cells, so the rule is
+ * exact.  rho is [nverts]; w is [ncells]. */
+void orc_cell_weights(const orc_mesh *m, const double *rho, double *w) {
+  int d = m->dim;
+  double g[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+  for (int64_t K = 0; K < m->ncells; ++K) {
+    double s = 0.0;
+    for (int q = 0; q < (1 << d); ++q) {
+      double t[3] = {g[q & 1], g[(q >> 1) & 1], g[(q >> 2) & 1]};
+      double wq = 1.0;
+      for (int j = 0; j < d; ++j) wq = wq * 0.5;
+      s = s + wq * rho_hat(m, K, rho, t);
+    }
+    w[K] = s;
+  }
+}
+
+/* Particles per cell from cell weights (the second and third parts of the
+ * Sec. 2.2 listing, on one process): acc_K = w_0 + ... + w_K as a left fold,
+ * W = acc_{C-1}; draw i = 0..N-1 takes u_i = top 53 bits of SplitMix64
+ * output i times 2^-53, r_i = W u_i, and goes to the first cell with
+ * acc_K > r_i (reading R19: "first accumulated weight above r" rather than
+ * "not below", so that a cell of zero weight is never chosen), or, if fl(W
+ * u_i) rounded up to W, to the last cell of positive weight.  Weights must be
+ * finite and >= 0 with W > 0.  counts is [ncells]. */
+void orc_draw_cell_counts(int64_t C, const double *w, int64_t N, uint64_t seed, int64_t *counts) {
+  double *acc = (double *)malloc(sizeof(double) * (size_t)(C > 0 ? C : 1));
+  double s = 0.0;
+  int64_t last = -1;
+  for (int64_t K = 0; K < C; ++K) {
+    s = s + w[K];
+    acc[K] = s;
+    counts[K] = 0;
+    if (w[K] > 0.0) last = K;
+  }
+  double W = s;
+  for (int64_t i = 0; i < N; ++i) {
+    double u = (double)(orc_splitmix64(seed, (uint64_t)i) >> 11) * 0x1.0p-53;
+    double r = W * u;
+    int64_t lo = 0, hi = C; /* first K in [lo, hi) with acc[K] > r */
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (acc[mid] > r)
+        hi = mid;
+      else
+        lo = mid + 1;
+    }
+    counts[lo < C ? lo : last] += 1;
+  }
+  free(acc);
+}
+
+/* In-cell Metropolis-Hastings generation (Sec. 2.2, MH paragraph): in cell
+ * K with n_K particles, a chain on the reference cell with target rho-hat
+ * and uniform proposals, started at the cell centre, of length J n_K
+ * (J = thinning); every J-th state (states J, 2J, ..) becomes a particle.
+ * Step s of the chain (global step g = J * first_K + s, first_K the number
+ * of particles of the cells before K) draws SplitMix64 outputs
+ * g (dim+1) + j: j < dim the proposal's coordinates (top 53 bits times
+ * 2^-53), j = dim the acceptance uniform u.  The proposal y is accepted
+ * when u rho-hat(current) < rho-hat(y) (reading R20: the fixed thinning J
+ * stands for the paper's "J larger than the longest run of equal samples").
+ * x = Phi_K(xhat), ids first_id + (creation index).  Outputs particle-major
+ * as in orc_seed.  Returns N. */
+int64_t orc_seed_mh(const orc_mesh *m, const uint32_t *per_cell, const double *rho, uint32_t thinning,
+                    uint64_t seed, uint64_t first_id, double *x, double *xhat, int64_t *cell, uint64_t *id) {
+  int d = m->dim;
+  int64_t g = 0;
+  for (int64_t K = 0; K < m->ncells; ++K) {
+    uint32_t nk = per_cell[K];
+    if (nk == 0) continue;
+    double cur[3] = {0.5, 0.5, 0.5};
+    double rc = rho_hat(m, K, rho, cur);
+    uint64_t step0 = (uint64_t)thinning * (uint64_t)g;
+    for (uint64_t s = 0; s < (uint64_t)thinning * nk; ++s) {
+      uint64_t gs = step0 + s;
+      double y[3] = {0.5, 0.5, 0.5};
+      for (int j = 0; j < d; ++j)
+        y[j] = (double)(orc_splitmix64(seed, gs * (uint64_t)(d + 1) + (uint64_t)j) >> 11) * 0x1.0p-53;
+      double u = (double)(orc_splitmix64(seed, gs * (uint64_t)(d + 1) + (uint64_t)d) >> 11) * 0x1.0p-53;
+      double ry = rho_hat(m, K, rho, y);
+      if (u * rc < ry) {
+        for (int j = 0; j < d; ++j) cur[j] = y[j];
+        rc = ry;
+      }
+      if ((s + 1) % thinning == 0) {
+        double p[3] = {0, 0, 0};
+        orc_phi(m, K, cur, p);
+        for (int j = 0; j < d; ++j) {
+          x[g * d + j] = p[j];
+          xhat[g * d + j] = cur[j];
+        }
+        cell[g] = K;
+        id[g] = first_id + (uint64_t)g;
+        ++g;
+      }
+    }
+  }
+  return g;
+}
+
+/* Prescribed particle locations (Sec. 2.2, second listing): for k = 0..n-1
+ * in order, the point x_k becomes a particle of its owner cell (the lowest-
+ * index cell holding it, reading R4) with xhat = Phi_K^{-1}(x_k) and the
+ * next id; points in no cell are skipped.  The result is ordered by
+ * (cell, id) (R9).  x is [n][dim]; outputs particle-major; returns the
+ * number created. */
+int64_t orc_import(const orc_mesh *m, int64_t n, const double *x, uint64_t first_id, double *xo, double *xhato,
+                   int64_t *cello, uint64_t *ido) {
+  int d = m->dim;
+  orc_particle *P = (orc_particle *)calloc(n > 0 ? n : 1, sizeof(orc_particle));
+  int64_t c = 0;
+  uint64_t next_id = first_id;
+  for (int64_t k = 0; k < n; ++k) {
+    double t[3] = {0, 0, 0};
+    int64_t K = orc_owner(m, x + k * d, t);
+    if (K < 0) continue;
+    P[c].id = next_id++;
+    P[c].cell = K;
+    for (int j = 0; j < d; ++j) {
+      P[c].x[j] = x[k * d + j];
+      P[c].xhat[j] = t[j];
+    }
+    ++c;
+  }
+  qsort(P, (size_t)c, sizeof(orc_particle), cmp_cell_id);
+  for (int64_t i = 0; i < c; ++i) {
+    for (int j = 0; j < d; ++j) {
+      xo[i * d + j] = P[i].x[j];
+      xhato[i * d + j] = P[i].xhat[j];
+    }
+    cello[i] = P[i].cell;
+    ido[i] = P[i].id;
+  }
+  free(P);
+  return c;
+}
