@@ -118,6 +118,61 @@ pic_status pic_seed_particles(pic_mesh mesh, const uint32_t *per_cell, uint32_t 
                               uint64_t first_id, int n_props, size_t capacity, void *stream, pic_particles *out);
 pic_status pic_destroy_particles(pic_particles parts);
 
+/* Generation with a density rho(x) (Sec. 2.2, the listing for N particles
+ * and the Metropolis-Hastings paragraph).  rho is given by its values at the
+ * mesh vertices, [nverts] FP64 device, >= 0; rho_h is its (bi/tri)linear
+ * interpolant.
+ *
+ * pic_cell_weights: w[K] = int_K rho_h dx ([n_cells] FP64 device), by the
+ * tensor 2-point Gauss rule on the reference cell, exact for these fields.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_cell_weights(pic_mesh mesh, const double *rho, double *w, void *stream);
+
+/* pic_draw_cell_counts: particles per cell for n_particles draws.  The
+ * accumulated weights acc_K = w_0 + .. + w_K form one left fold; draw i takes
+ * u_i = (SplitMix64 output i of `seed`) >> 11 times 2^-53 and goes to the
+ * first cell with acc_K > W u_i, W = acc_{n_cells-1} (or to the last cell of
+ * positive weight if W u_i rounded up to W).  Zero-weight cells get none.
+ *   w       [n_cells] FP64 device, finite and >= 0, positive sum
+ *   counts  [n_cells] u32 device (overwritten); usable as pic_seed_particles'
+ *           or pic_seed_particles_mh's per_cell
+ * The fold runs on one warp (one-time set-up cost, about 5 ns per cell).
+ * Synchronises `stream` to check the weights.
+ * Errors: PIC_ERR_ARG (bad weights), PIC_ERR_CAPACITY (n_particles >= 2^32),
+ * PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_draw_cell_counts(uint32_t n_cells, const double *w, uint64_t n_particles, uint64_t seed,
+                                uint32_t *counts, void *stream);
+
+/* pic_seed_particles_mh: like pic_seed_particles, but the reference
+ * coordinates in cell K come from a Metropolis-Hastings chain with target
+ * rho-hat(x-hat) = rho_h(Phi_K(x-hat)) |det grad-hat Phi_K(x-hat)| and
+ * uniform proposals on the reference cell, started at its centre; the chain
+ * runs thinning * per_cell[K] steps and every thinning-th state becomes a
+ * particle.  Step s of cell K's chain is global step g = thinning * (particles
+ * of the cells before K) + s and uses SplitMix64 outputs g (dim+1) + a for
+ * proposal coordinate a and g (dim+1) + dim for the acceptance uniform u; the
+ * proposal y is accepted when u rho-hat(current) < rho-hat(y).  rho-hat is a
+ * fixed sequence of correctly rounded operations (documented in
+ * csrc/generate.cu), so the chains do not depend on the device.
+ * Ids first_id + creation index; properties 0.  Synchronises `stream`.
+ *   per_cell  [n_cells] u32 device;  rho  [nverts] FP64 device;  thinning >= 1
+ * Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY, PIC_ERR_OOM, PIC_ERR_CUDA. */
+pic_status pic_seed_particles_mh(pic_mesh mesh, const uint32_t *per_cell, const double *rho, uint32_t thinning,
+                                 uint64_t seed, uint64_t first_id, int n_props, size_t capacity, void *stream,
+                                 pic_particles *out);
+
+/* Prescribed particle locations (Sec. 2.2, second listing): every point is
+ * located by the all-cells search of pic_locate_points (lowest index on
+ * shared faces); points in no cell are skipped.  The k-th point found, in
+ * input order, gets id first_id + k; the store is sorted by (cell, id).
+ *   x          [dim][n] FP64 device positions
+ *   capacity   store capacity (0 = the number found)
+ *   n_outside  receives the number skipped (may be NULL)
+ * Synchronises `stream`.  Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY, PIC_ERR_OOM,
+ * PIC_ERR_CUDA. */
+pic_status pic_import_particles(pic_mesh mesh, size_t n, const double *x, uint64_t first_id, int n_props,
+                                size_t capacity, void *stream, pic_particles *out, size_t *n_outside);
+
 /* Property p of every particle from values [N] (device, store order).
  * Sec. 2.6: a run-time number of scalars per particle. */
 pic_status pic_set_properties(pic_particles parts, int prop, const double *values, void *stream);

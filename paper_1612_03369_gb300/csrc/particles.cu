@@ -98,17 +98,18 @@ pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, 
 
 }  // namespace pic
 
-extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, uint64_t seed,
-                                         uint64_t first_id, int n_props, size_t capacity, void* stream,
-                                         pic_particles* out) {
-  if (!out) return (set_error("pic_seed_particles: out is NULL"), PIC_ERR_ARG);
+namespace pic {
+
+// The part of seeding shared by every generator: per-cell numbers (device
+// array, or `uniform_count` everywhere) -> cell offsets -> an allocated store
+// of `capacity` (0 = exactly the number created) whose counters say N
+// particles.  The generator's kernel then fills slots cell_off[K] ..
+// cell_off[K+1]-1 of buffer 0.
+pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,
+                        cudaStream_t st, const char* who, pic_particles_s** out, size_t* n_out) {
   *out = nullptr;
-  if (!mesh) return (set_error("pic_seed_particles: null mesh"), PIC_ERR_ARG);
-  if (n_props < 0 || n_props > kMaxProps)
-    return (set_error("pic_seed_particles: n_props must be in [0, %d]", kMaxProps), PIC_ERR_ARG);
-  cudaStream_t st = (cudaStream_t)stream;
+  if (n_props < 0 || n_props > kMaxProps) return (set_error("%s: n_props must be in [0, %d]", who, kMaxProps), PIC_ERR_ARG);
   const uint32_t C = mesh->C;
-  // Count first (per-cell numbers may live on the device).
   uint32_t *counts = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
   const uint32_t nb = scan_block_count(C);
   if (cudaMalloc(&counts, sizeof(uint32_t) * C) != cudaSuccess || cudaMalloc(&off, sizeof(uint32_t) * (C + 1)) != cudaSuccess ||
@@ -118,7 +119,7 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
     cudaFree(off);
     cudaFree(sums);
     cudaFree(total);
-    return (set_error("pic_seed_particles: device allocation failed"), PIC_ERR_OOM);
+    return (set_error("%s: device allocation failed", who), PIC_ERR_OOM);
   }
   auto cleanup_tmp = [&]() {
     cudaFree(counts);
@@ -130,13 +131,13 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
   uint64_t total64 = 0;
   if (per_cell) {
     uint32_t* h = (uint32_t*)malloc(sizeof(uint32_t) * C);
-    cudaError_t e = cudaMemcpyAsync(h, per_cell, sizeof(uint32_t) * C, cudaMemcpyDefault, st);
+    cudaError_t e = h ? cudaMemcpyAsync(h, per_cell, sizeof(uint32_t) * C, cudaMemcpyDefault, st) : cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       free(h);
       cleanup_tmp();
       cudaFree(off);
-      return cuda_fail(e, "pic_seed_particles: reading per_cell");
+      return cuda_fail(e, who);
     }
     for (uint32_t K = 0; K < C; ++K) total64 += h[K];
     free(h);
@@ -146,20 +147,19 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
   if (total64 >= 0xFFFFFFF0ull) {
     cleanup_tmp();
     cudaFree(off);
-    return (set_error("pic_seed_particles: %llu particles exceed the 32-bit store", (unsigned long long)total64),
-            PIC_ERR_CAPACITY);
+    return (set_error("%s: %llu particles exceed the 32-bit store", who, (unsigned long long)total64), PIC_ERR_CAPACITY);
   }
   const size_t N = (size_t)total64;
   if (capacity == 0) capacity = N;
   if (capacity < N) {
     cleanup_tmp();
     cudaFree(off);
-    return (set_error("pic_seed_particles: capacity %zu < %zu particles", capacity, N), PIC_ERR_CAPACITY);
+    return (set_error("%s: capacity %zu < %zu particles", who, capacity, N), PIC_ERR_CAPACITY);
   }
   if (capacity >= 0xFFFFFFF0ull) {
     cleanup_tmp();
     cudaFree(off);
-    return (set_error("pic_seed_particles: capacity exceeds the 32-bit store"), PIC_ERR_CAPACITY);
+    return (set_error("%s: capacity exceeds the 32-bit store", who), PIC_ERR_CAPACITY);
   }
   pic_status r = scan_u32(counts, off, C, sums, total, nullptr, st);
   cleanup_tmp();
@@ -167,7 +167,6 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
     cudaFree(off);
     return r;
   }
-
   pic_particles_s* p = store_alloc(mesh->dim, n_props, C, capacity, off);
   if (!p) return PIC_ERR_OOM;
   p->mesh = mesh;
@@ -178,21 +177,40 @@ extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell
   cudaError_t e = cudaMemcpyAsync(p->ctr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     pic_destroy_particles(p);
-    return cuda_fail(e, "pic_seed_particles: counters");
+    return cuda_fail(e, who);
   }
+  p->cur = 0;
+  *out = p;
+  *n_out = N;
+  return PIC_OK;
+}
+
+}  // namespace pic
+
+extern "C" pic_status pic_seed_particles(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, uint64_t seed,
+                                         uint64_t first_id, int n_props, size_t capacity, void* stream,
+                                         pic_particles* out) {
+  if (!out) return (set_error("pic_seed_particles: out is NULL"), PIC_ERR_ARG);
+  *out = nullptr;
+  if (!mesh) return (set_error("pic_seed_particles: null mesh"), PIC_ERR_ARG);
+  cudaStream_t st = (cudaStream_t)stream;
+  pic_particles_s* p = nullptr;
+  size_t N = 0;
+  pic_status r = seed_prepare(mesh, per_cell, uniform_count, n_props, capacity, st, "pic_seed_particles", &p, &N);
+  if (r != PIC_OK) return r;
+  const uint32_t C = mesh->C;
   const MeshView m = mesh_view(mesh);
   const int grid = (int)((C + 127) / 128 < 8192 ? (C + 127) / 128 : 8192);
   if (mesh->dim == 2)
-    seed_kernel<2><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id, 0u);
+    seed_kernel<2><<<grid, 128, 0, st>>>(m, store_view(p, 0), p->cell_off, seed, first_id, 0u);
   else
-    seed_kernel<3><<<grid, 128, 0, st>>>(m, store_view(p, 0), off, seed, first_id, 0u);
-  e = cudaGetLastError();
+    seed_kernel<3><<<grid, 128, 0, st>>>(m, store_view(p, 0), p->cell_off, seed, first_id, 0u);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     pic_destroy_particles(p);
     return cuda_fail(e, "pic_seed_particles: seed kernel");
   }
-  p->cur = 0;
   *out = p;
   return PIC_OK;
 }

@@ -390,6 +390,10 @@ namespace pic {
 // Rebuild the sorted store from the cells found by the last locate
 // (cell_new, counts already filled).  Defined in rebin.cu.
 pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s);
+// Counting, cell offsets and store allocation shared by the generators
+// (particles.cu); the store's buffer 0 is then filled by the caller.
+pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,
+                        cudaStream_t st, const char* who, pic_particles_s** out, size_t* n_out);
 // Exclusive scan of n u32 values into out[0..n] (out[n] = total); total also
 // written to *total_dev when non-null.  Defined in rebin.cu.
 pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,

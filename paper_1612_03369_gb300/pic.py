@@ -34,6 +34,10 @@ SIGNATURES = {
     "pic_destroy_particles": (_I, [_P]),
     "pic_set_properties": (_I, [_P, _I, _P, _P]),
     "pic_advect": (_I, [_P, _P, _F64, _I, _I, _I, _P]),
+    "pic_cell_weights": (_I, [_P, _P, _P, _P]),
+    "pic_draw_cell_counts": (_I, [_U32, _P, _U64, _U64, _P, _P]),
+    "pic_seed_particles_mh": (_I, [_P, _P, _P, _U32, _U64, _U64, _I, _SZ, _P, _P]),
+    "pic_import_particles": (_I, [_P, _SZ, _P, _U64, _I, _SZ, _P, _P, _P]),
     "pic_advect_properties": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
     "pic_locate": (_I, [_P, _P, _P]),
     "pic_advect_record": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
@@ -145,6 +149,33 @@ def pic_set_properties(h: int, prop: int, values, stream=None):
 def pic_advect(parts: int, mesh: int, dt: float, integrator: int, precision: int, n_steps: int, stream=None):
     _check(_lib.pic_advect(parts, mesh, float(dt), int(integrator), int(precision), int(n_steps), _stream(stream)),
            "pic_advect")
+
+
+def pic_cell_weights(mesh: int, rho, w, stream=None):
+    _check(_lib.pic_cell_weights(mesh, _ptr(rho), _ptr(w), _stream(stream)), "pic_cell_weights")
+
+
+def pic_draw_cell_counts(n_cells: int, w, n_particles: int, seed: int, counts, stream=None):
+    _check(_lib.pic_draw_cell_counts(int(n_cells), _ptr(w), int(n_particles), int(seed) & (2**64 - 1), _ptr(counts),
+                                     _stream(stream)), "pic_draw_cell_counts")
+
+
+def pic_seed_particles_mh(mesh: int, per_cell, rho, thinning: int, seed: int, first_id: int = 0, n_props: int = 0,
+                          capacity: int = 0, stream=None) -> int:
+    out = C.c_void_p()
+    _check(_lib.pic_seed_particles_mh(mesh, _ptr(per_cell), _ptr(rho), int(thinning), int(seed) & (2**64 - 1),
+                                      int(first_id), int(n_props), int(capacity), _stream(stream), C.byref(out)),
+           "pic_seed_particles_mh")
+    return out.value
+
+
+def pic_import_particles(mesh: int, n: int, x, first_id: int = 0, n_props: int = 0, capacity: int = 0,
+                         stream=None) -> tuple[int, int]:
+    out = C.c_void_p()
+    outside = C.c_size_t(0)
+    _check(_lib.pic_import_particles(mesh, int(n), _ptr(x), int(first_id), int(n_props), int(capacity),
+                                     _stream(stream), C.byref(out), C.byref(outside)), "pic_import_particles")
+    return out.value, int(outside.value)
 
 
 class PropertyOdes(C.Structure):
@@ -328,6 +359,28 @@ class Mesh:
             pass
 
 
+def cell_weights(mesh: "Mesh", rho):
+    """Sec. 2.2: w_K = int_K rho_h dx for vertex values rho -> device tensor [n_cells]."""
+    import torch
+
+    r = torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64), device="cuda") \
+        if not isinstance(rho, torch.Tensor) else rho
+    w = torch.empty(mesh.ncells, dtype=torch.float64, device="cuda")
+    pic_cell_weights(mesh.h, r, w)
+    return w
+
+
+def draw_cell_counts(w, n_particles: int, seed: int):
+    """Sec. 2.2: particles per cell for n_particles weighted draws -> device int32 tensor (u32 bits)."""
+    import torch
+
+    wt = torch.as_tensor(np.ascontiguousarray(w, dtype=np.float64), device="cuda") \
+        if not isinstance(w, torch.Tensor) else w
+    counts = torch.empty(wt.shape[0], dtype=torch.int32, device="cuda")
+    pic_draw_cell_counts(wt.shape[0], wt, n_particles, seed, counts)
+    return counts
+
+
 class Particles:
     """Owning wrapper of a pic_particles handle."""
 
@@ -342,6 +395,37 @@ class Particles:
         if per_cell is not None:
             pc = torch.as_tensor(np.ascontiguousarray(per_cell, dtype=np.uint32).view(np.int32), device="cuda")
         self.h = pic_seed_particles(mesh.h, pc, uniform_count, seed, first_id, n_props, capacity, stream)
+
+    @classmethod
+    def _wrap(cls, mesh: Mesh, h: int, n_props: int) -> "Particles":
+        obj = cls.__new__(cls)
+        obj.mesh, obj.dim, obj.n_props, obj.h = mesh, mesh.dim, n_props, h
+        return obj
+
+    @classmethod
+    def metropolis_hastings(cls, mesh: Mesh, per_cell, rho, thinning: int = 8, seed: int = 0, first_id: int = 0,
+                            n_props: int = 0, capacity: int = 0, stream=None) -> "Particles":
+        """Sec. 2.2 in-cell Metropolis-Hastings generation for a vertex density rho."""
+        import torch
+
+        pc = torch.as_tensor(np.ascontiguousarray(per_cell, dtype=np.uint32).view(np.int32), device="cuda") \
+            if not isinstance(per_cell, torch.Tensor) else per_cell
+        r = torch.as_tensor(np.ascontiguousarray(rho, dtype=np.float64), device="cuda") \
+            if not isinstance(rho, torch.Tensor) else rho
+        h = pic_seed_particles_mh(mesh.h, pc, r, thinning, seed, first_id, n_props, capacity, stream)
+        return cls._wrap(mesh, h, n_props)
+
+    @classmethod
+    def import_points(cls, mesh: Mesh, x, first_id: int = 0, n_props: int = 0, capacity: int = 0,
+                      stream=None) -> tuple["Particles", int]:
+        """Sec. 2.2 prescribed locations: x [dim][n] -> (store, number of points outside)."""
+        import torch
+
+        xt = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda") \
+            if not isinstance(x, torch.Tensor) else x.contiguous()
+        n = int(xt.shape[1]) if xt.dim() == 2 else 0
+        h, outside = pic_import_particles(mesh.h, n, xt, first_id, n_props, capacity, stream)
+        return cls._wrap(mesh, h, n_props), outside
 
     def advect_properties(self, dt, integrator=PIC_RK4, n_steps=1, damage=-1, alpha=0.0, beta=0.0, deformation=-1,
                           stream=None):
