@@ -15,7 +15,9 @@ so no L2 flush is needed between steps.
 c3 is the precision form (FP32 basis) at 128^3; c4 times the adjoint
 (recorded forward + reverse sweep) at 32^3 x 32 per cell over 20 steps; c5
 times the 64-problem ensemble (10 steps per persistent graph launch); c2p
-times c2 with the damage and deformation-gradient ODEs.  The default is c2.
+times c2 with the damage and deformation-gradient ODEs; next times the rows
+after the hot path (time interpolation, property ODEs, transfers,
+generation) on the c2 workload.  The default is c2.
 
 Under torchrun (N > 1) every rank advances its own replica of c1-c3
 (independent problems, no data-path collective: weak scaling), and the 64
@@ -450,6 +452,165 @@ def run_props(args):
     }
 
 
+# FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
+# counted by ncu on the 64^3 x 20 workload; profiles/next_rows_c2_64cubed.md).
+FP64_FLOPS = {
+    "advect_props_kernel<3,RK4>": 3937.0,  # per particle-step
+    "vertex_partial_kernel<3>": 42.00,     # per particle
+    "lsq_linear_kernel<3>": 40.75,         # per particle
+    "mh_seed_kernel<3>": 238.96,           # per chain step
+    "cell_weights_kernel<3>": 1815.0,      # per cell
+}
+# FP64 peak: the GB300's nominal FP64 rate, 1.25 TFLOP/s (FMA = 2 flops).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def _fp64_roof(kernel, units, ms):
+    f = FP64_FLOPS.get(kernel)
+    if f is None or ms <= 0:
+        return {"kernel": kernel, "bound": "fp64", "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "peak_kind": "derived (nominal FP64 rate)"}
+    ach = f * units / (ms / 1e3) / 1e12
+    return {"kernel": kernel, "bound": "fp64", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "fp64_flops_per_unit": f, "peak_kind": "derived (nominal FP64 rate)"}
+
+
+def run_next(args):
+    """The rows after the hot path, each on the 64^3 x 20 workload (c2):
+    f1 time interpolation, f2 property ODEs, f3 particle -> field transfers,
+    f4 generation; each with its bound and the oracle timed on a sample."""
+    import torch
+    import oracle as O
+    from paper_1612_03369_gb300 import pic as P
+
+    wl = W.c2()
+    dt = wl.dt
+    mesh = P.Mesh(wl.n, wl.X, wl.U)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(reps):
+            fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def cpu(fn, units, what):
+        t0 = time.perf_counter()
+        fn()
+        el = time.perf_counter() - t0
+        return {"value": units / el, "seconds": el, "cores": 1, "kind": "oracle", "sample": what}
+
+    om = O.Mesh(wl.n, wl.X, wl.U)
+    rows = {}
+    # f1: time interpolation between two fields (RK4 half-step stages average them)
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=3)
+    N = parts.state()[0]
+    steady = timed(lambda: parts.advect(dt, 4, 1), args.steps)
+    mesh.set_velocity(wl.U, U_next=0.5 * wl.U)
+    two = timed(lambda: parts.advect(dt, 4, 1), args.steps)
+    mesh.set_velocity(wl.U)
+    om2 = O.Mesh(wl.n, wl.X, wl.U)
+    om2.set_velocity_next(0.5 * wl.U)
+    sub = O.seed_particles(om2, uniform_count=wl.ppc, seed=wl.pseed, n_props=0)
+    sub = sub.subset(np.arange(sub.n) % 2000 == 0)
+    rows["f1_time_interpolation"] = {
+        "value": N / (two / 1e3), "unit": "particle-steps/s", "ms_per_step": two, "steady_ms_per_step": steady,
+        "bound": "alu (FP32 issue; two Q2 contractions at the c = 1/2 stages)",
+        "cpu_baseline": cpu(lambda: O.advect(om2, sub, dt, 4, 1), sub.n, "%d particles, one RK4 step" % sub.n)}
+    parts.close()
+    # f2: property ODEs (damage + F)
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=10)
+    eye = np.eye(3).reshape(-1)
+    for q in range(9):
+        parts.set_property(1 + q, torch.full((N,), float(eye[q]), dtype=torch.float64, device="cuda"))
+    odes = dict(damage=0, alpha=1.0, beta=0.5, deformation=1)
+    ms = timed(lambda: parts.advect_properties(dt, 4, 1, **odes), args.steps)
+    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=10)
+    op = op.subset(np.arange(op.n) % 5000 == 0)
+    op.props[:, 1:10] = eye
+    rows["f2_property_odes"] = {
+        "value": N / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms,
+        "roofline": _fp64_roof("advect_props_kernel<3,RK4>", N, ms),
+        "cpu_baseline": cpu(lambda: O.advect_properties(om, op, dt, 4, 1, damage=0, alpha=1.0, beta=0.5, defgrad=1),
+                            op.n, "%d particles, one RK4 step with both ODEs" % op.n)}
+    parts.close()
+    # f3: transfers of one property (the store as seeded, property = x0)
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=1)
+    st = parts.export()
+    parts.set_property(0, st["x"][0].contiguous())
+    del st
+    ms_v = timed(lambda: parts.vertex_average(0), args.steps)
+    ms_l = timed(lambda: parts.project_linear(0), args.steps)
+    ms_a = timed(lambda: parts.average(0), args.steps)
+    full = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=0)
+    v0 = full.x[:, 0].copy()
+    rows["f3_transfers"] = {
+        "particles": N, "cell_average_ms": ms_a, "vertex_average_ms": ms_v, "project_linear_ms": ms_l,
+        "vertex_average": {"value": N / (ms_v / 1e3), "unit": "particles/s",
+                           "roofline": _fp64_roof("vertex_partial_kernel<3>", N, ms_v)},
+        "project_linear": {"value": N / (ms_l / 1e3), "unit": "particles/s",
+                           "roofline": _fp64_roof("lsq_linear_kernel<3>", N, ms_l)},
+        "cpu_baseline": {
+            "vertex_average": cpu(lambda: O.vertex_average(om, full.cell, full.xhat, v0), N, "all %d particles" % N),
+            "project_linear": cpu(lambda: O.cell_lsq_linear(om, full.cell, full.xhat, v0), N, "all %d particles" % N)}}
+    parts.close()
+    # f4: generation with a density, and prescribed positions
+    Xv = wl.X
+    rho = 1.0 + 4.0 * Xv[0] * Xv[1]
+    rho_d = torch.as_tensor(rho, device="cuda")
+    wts = P.cell_weights(mesh, rho_d)
+    ms_w = timed(lambda: P.cell_weights(mesh, rho_d), args.steps)
+    ms_d = timed(lambda: P.draw_cell_counts(wts, N, 7), max(2, args.steps // 5))
+    counts = P.draw_cell_counts(wts, N, 7)
+    J = 8
+    holder = []
+
+    def mh():
+        if holder:
+            holder.pop().close()
+        holder.append(P.Particles.metropolis_hastings(mesh, counts, rho_d, thinning=J, seed=3))
+
+    ms_m = timed(mh, 3)
+    holder.pop().close()
+    g = np.random.default_rng(1)
+    pts = torch.as_tensor(g.uniform(-0.05, 1.05, size=(3, N)), device="cuda")
+
+    def imp():
+        if holder:
+            holder.pop().close()
+        holder.append(P.Particles.import_points(mesh, pts)[0])
+
+    ms_i = timed(imp, 3)
+    holder.pop().close()
+    w_o = O.cell_weights(om, rho)
+    per_o = O.draw_cell_counts(w_o, 20000, 7).astype(np.uint32)
+    pts_o = pts[:, :20000].cpu().numpy().T.copy()
+    rows["f4_generation"] = {
+        "particles": N, "cells": wl.ncells, "cell_weights_ms": ms_w, "draw_counts_ms": ms_d,
+        "cell_weights": {"value": wl.ncells / (ms_w / 1e3), "unit": "cells/s",
+                         "roofline": _fp64_roof("cell_weights_kernel<3>", wl.ncells, ms_w)},
+        "metropolis_hastings_ms": ms_m, "mh_thinning": J, "import_ms": ms_i,
+        "mh": {"value": N * J / (ms_m / 1e3), "unit": "chain steps/s",
+               "roofline": _fp64_roof("mh_seed_kernel<3>", N * J, ms_m)},
+        "import": {"value": N / (ms_i / 1e3), "unit": "points/s"},
+        "cpu_baseline": {
+            "cell_weights": cpu(lambda: O.cell_weights(om, rho), wl.ncells, "all %d cells" % wl.ncells),
+            "draw_counts": cpu(lambda: O.draw_cell_counts(w_o, N, 7), N, "all %d draws" % N),
+            "metropolis_hastings": cpu(lambda: O.seed_particles_mh(om, per_o, rho, J, 3), int(per_o.sum()) * J,
+                                       "20000 particles (chain steps as unit)"),
+            "import": cpu(lambda: O.import_points(om, pts_o), 20000, "20000 points")}}
+    mesh.close()
+    return {"metric": "rows after the hot path on 64^3 x 20 (c2 workload): time interpolation, property ODEs, "
+                      "particle -> field transfers, generation",
+            "n_gpus": 1, "steps": args.steps, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "c2_3d_curl_64^3", "particles": N}, "rows": rows}
+
+
 def roofline_object(args, adv_avg_ms, particles, adv_bytes, hbm_achieved, hbm, peak_kind, rebin_ms):
     """The advect kernel's roofline.  It is bound by FP32 issue (double-float
     arithmetic), so its roofline is the FP32 ALU peak; its HBM fraction is
@@ -533,7 +694,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2p"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2p", "next"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -545,10 +706,11 @@ def main():
         if res is not None:
             print(json.dumps(res), flush=True)
         return
-    if args.config in ("c4", "c2p"):
+    if args.config in ("c4", "c2p", "next"):
         # one problem: rank 0 alone runs it
         if rank == 0:
-            print(json.dumps(run_adjoint(args) if args.config == "c4" else run_props(args)), flush=True)
+            fn = {"c4": run_adjoint, "c2p": run_props, "next": run_next}[args.config]
+            print(json.dumps(fn(args)), flush=True)
         return
     if world > 1:
         import torch

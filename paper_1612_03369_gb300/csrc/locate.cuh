@@ -140,6 +140,14 @@ __device__ uint32_t locate(const MeshView& m, const double y[D], uint32_t hintK,
     flags |= kFlagBounds;
     return global_search<D>(m, y, t, iters, flags);
   }
+  // A point outside the padded bounding box of the whole mesh (padding 1e-9
+  // of its extent) is in no cell: a cell accepts only points within about
+  // 1e-10 of its own size of it.  Testing the box first spares such points
+  // the walk over every neighbour of the hint (the paper's remark on testing
+  // the subdomain's bounding box before its cells, Sec. 2.2).
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    if (!(y[a] >= m.dlo[a] && y[a] <= m.dhi[a])) return PIC_LOST;
   bool conv = false;
   if (try_cell<D>(m, hintK, y, t, iters, flags, &conv)) return lowest_owner<D>(m, y, hintK, t, iters, flags);
 
