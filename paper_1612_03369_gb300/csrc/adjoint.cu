@@ -11,7 +11,8 @@
 //   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
 //   lambda_y_s = dt G_s^T lambda_k_s,       lambda = lambda' + sum_s lambda_y_s
 //   dL/dU_i   += dt phi-hat_i(x-hat_s) lambda_k_s
-// The stages are recomputed in FP64 from the checkpoint.  Each stage leaves a
+// The stages are recomputed from the checkpoint (double-float, as the forward
+// ran them; G in double-float, lambda in FP64).  Each stage leaves a
 // record (stage cell, x-hat_s, dt lambda_k_s) keyed by (slot, stage); the
 // records are sorted by (cell, key), summed per cell in that order, and the
 // cells' sums are added into the nodes in increasing cell order.  No floating-
@@ -20,7 +21,7 @@
 
 #include "advect.cuh"
 #include "fastpath.cuh"
-#include "grad.cuh"
+#include "grad_df.cuh"
 #include "locate.cuh"
 #include "pic_internal.cuh"
 
@@ -84,9 +85,16 @@ struct TapeStep {
 // One reverse step for every particle alive after it (thread per new slot j).
 // The stages are recomputed exactly as the forward computed them (double-
 // float locate and Q2 contraction, so the stage cells are the forward's);
-// G = du/dx at each stage is evaluated in FP64 (it carries lambda).
+// G = du/dx at each stage is evaluated in double-float and handed back in
+// FP64, where the sweep of lambda runs.
+// Resident blocks per SM requested from the register allocator (swept at
+// build time with -DPIC_REVERSE_MIN_BLOCKS=n).
+#ifndef PIC_REVERSE_MIN_BLOCKS
+#define PIC_REVERSE_MIN_BLOCKS 3
+#endif
+
 template <int D, int RK>
-__global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep tp, size_t cap, double dt,
+__global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_step_kernel(MeshView m, TapeStep tp, size_t cap, double dt,
                                                            const double* __restrict__ lam_in,
                                                            double* __restrict__ lam_out,
                                                            uint32_t* __restrict__ rec_cell,
@@ -140,26 +148,9 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
       }
       df u[D];
       q2_eval_df<D>(m, m.U2, Ks[s], ts[s], u);
-      double t64[D], ud[D], Gu[D][D], J[D][D], Ji[D][D], phi[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        k[a] = df_mul(dtd, u[a]);
-        t64[a] = df_to_double(ts[s][a]);
-      }
-      q2_value_grad<D>(m, Ks[s], t64, ud, Gu);
-      CellGeom<D> g;
-      load_cell<D>(m, Ks[s], g);
-      map_and_jacobian<D>(g, t64, phi, J);
-      invert<D>(J, Ji);
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          double acc = 0.0;
-#pragma unroll
-          for (int jj = 0; jj < D; ++jj) acc += Gu[c][jj] * Ji[jj][q];
-          G[s][c][q] = acc;
-        }
+      for (int a = 0; a < D; ++a) k[a] = df_mul(dtd, u[a]);
+      velocity_gradient_df<D>(m, Ks[s], ts[s], G[s]);
     }
     if (!ok) {
       // cannot happen for a particle that survived the step; keep it harmless
@@ -208,7 +199,11 @@ __global__ void __launch_bounds__(128) reverse_step_kernel(MeshView m, TapeStep 
 // Warp per cell: the records of the cell, in (cell, key) order, summed into
 // the cell's 3^D x D block of nodal gradient entries (lane e owns entries e,
 // e+32, ...), in double-float on the FP32 pipe; every cell is written (FP64),
-// empty ones with zeros.
+// empty ones with zeros.  The entry (node (a, b, c), comp) of a record is
+// (w_comp l_a(t0)) (l_b(t1) l_c(t2)): records are taken 32 at a time, lane i
+// forms record i's D x 3 left factors and 3^(D-1) right factors once and
+// leaves them in shared memory, then every lane adds its entries' products
+// over those records in record order.
 template <int D>
 __global__ void __launch_bounds__(256) cell_partial_kernel(uint32_t C, const uint32_t* __restrict__ rec_off,
                                                            const uint32_t* __restrict__ rec_perm,
@@ -218,42 +213,62 @@ __global__ void __launch_bounds__(256) cell_partial_kernel(uint32_t C, const uin
   constexpr int NN = (D == 3 ? 27 : 9);
   constexpr int NE = NN * D;
   constexpr int PER = (NE + 31) / 32;
-  const int lane = threadIdx.x & 31;
+  constexpr int NA = 3 * D;             // w_comp l_a(t0), index comp * 3 + a
+  constexpr int NB = (D == 3 ? 9 : 3);  // l_b(t1) l_c(t2), index c * 3 + b (2D: l_b(t1))
+  __shared__ float2 fac[256 / 32][32][NA + NB];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  // the (a, b, c, comp) of this lane's entries
-  int ea[PER], eb[PER], ec[PER], ecomp[PER];
+  int ia[PER], ib[PER];
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int ent = lane + 32 * q;
-    const int node = ent / D;
-    ecomp[q] = ent % D;
-    ea[q] = node % 3;
-    eb[q] = (node / 3) % 3;
-    ec[q] = node / 9;
+    const int node = ent / D, comp = ent % D;
+    ia[q] = comp * 3 + node % 3;
+    ib[q] = NA + (D == 3 ? (node / 9) * 3 + (node / 3) % 3 : (node / 3) % 3);
   }
   for (uint32_t K = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; K < C; K += warps) {
     df_acc acc[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) acc[q] = acc_zero();
     const uint32_t beg = rec_off[K], end = rec_off[K + 1];
-    for (uint32_t e = beg; e < end; ++e) {
-      const uint32_t r = rec_perm[e];
-      df l[D][3], w[D];
+    for (uint32_t e0 = beg; e0 < end; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      if (e < end) {
+        const uint32_t r = rec_perm[e];
+        df l[D][3], w[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const float2 tv = rec_t[a * rcap + r], wv = rec_w[a * rcap + r];
-        lagrange2_df(df_make(tv.x, tv.y), l[a]);
-        w[a] = df_make(wv.x, wv.y);
+        for (int a = 0; a < D; ++a) {
+          const float2 tv = rec_t[a * rcap + r], wv = rec_w[a * rcap + r];
+          lagrange2_df(df_make(tv.x, tv.y), l[a]);
+          w[a] = df_make(wv.x, wv.y);
+        }
+#pragma unroll
+        for (int comp = 0; comp < D; ++comp)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const df v = df_mul(w[comp], l[0][a]);
+            fac[wib][lane][comp * 3 + a] = make_float2(v.hi, v.lo);
+          }
+#pragma unroll
+        for (int c = 0; c < (D == 3 ? 3 : 1); ++c)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const df v = (D == 3) ? df_mul(l[1][b], l[2 % D][c]) : l[1][b];
+            fac[wib][lane][NA + c * 3 + b] = make_float2(v.hi, v.lo);
+          }
       }
+      __syncwarp();
+      const int cnt = (end - e0) < 32u ? (int)(end - e0) : 32;
+      for (int j = 0; j < cnt; ++j) {
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int ent = lane + 32 * q;
-        if (ent < NE) {
-          df phi = df_mul(l[0][ea[q]], l[1][eb[q]]);
-          if constexpr (D == 3) phi = df_mul(phi, l[2][ec[q]]);
-          acc_mad(acc[q], w[ecomp[q]], phi);
+        for (int q = 0; q < PER; ++q) {
+          if (lane + 32 * q < NE) {
+            const float2 A = fac[wib][j][ia[q]], B = fac[wib][j][ib[q]];
+            acc_mad(acc[q], df_make(A.x, A.y), df_make(B.x, B.y));
+          }
         }
       }
+      __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {

@@ -1,0 +1,186 @@
+// grad_df.cuh -- the velocity gradient G = du_h/dx = (du_h/dx-hat) J^{-1} at a
+// located point, in double-float arithmetic on the FP32 pipe (the FP64 pipe
+// of GB300 issues ~1/75 of the FP32 rate).  Used by the property ODEs of
+// Sec. 2.6 and by the adjoint sweep; G is handed back in FP64.
+//
+//   du/dx-hat   sum-factorised contraction of the Q2 nodal values with the
+//               1D Lagrange values l_a and derivatives l'_a:
+//                 l'_0 = 4t - 3,  l'_1 = 4 - 8t,  l'_2 = 4t - 1
+//   J           from the cell's monomial block (the map about vertex 0,
+//               Phi = X_0 + sum_k a_k m_k(t)): J_ij = sum_k a_k,i dm_k/dt_j
+//   J^{-1}      cofactors over the determinant, one double-float reciprocal
+// Every product is a double-float product (two_prod), every sum a
+// double-float accumulation, so G carries ~2^-46 relative error times the
+// conditioning of J.
+#pragma once
+
+#include "df.cuh"
+#include "fastpath.cuh"
+
+namespace pic {
+
+// a + c for a float constant c.
+__device__ __forceinline__ df df_add_f(df a, float c) {
+  const df s = two_sum(a.hi, c);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// 1 / a: FP32 reciprocal refined by one Newton step in double-float.
+__device__ __forceinline__ df df_recip(df a) {
+  const float r = __frcp_rn(a.hi);
+  const df p = two_prod(a.hi, r);                  // a.hi r exactly
+  const float e = __fsub_rn(__fsub_rn(1.0f, p.hi), __fmaf_rn(a.lo, r, p.lo));  // 1 - a r
+  return fast_two_sum(r, __fmul_rn(r, e));
+}
+
+// l'_a(t) for the quadratic Lagrange basis on {0, 1/2, 1}.
+__device__ __forceinline__ void lagrange2_deriv_df(df t, df dl[3]) {
+  const df t4 = df_scale2(t, 4.0f);
+  dl[0] = df_add_f(t4, -3.0f);
+  dl[1] = df_add_f(df_make(-2.0f * t4.hi, -2.0f * t4.lo), 4.0f);
+  dl[2] = df_add_f(t4, -1.0f);
+}
+
+// Gu[c][j] = d u_c / d t_j in cell K at double-float reference coordinates t.
+template <int D>
+__device__ __forceinline__ void q2_grad_df(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
+                                           df Gu[D][D]) {
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  const int64_t base = __ldg(m.qbase + K);
+  df l[D][3], dl[D][3];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lagrange2_df(t[a], l[a]);
+    lagrange2_deriv_df(t[a], dl[a]);
+  }
+#pragma unroll 1
+  for (int comp = 0; comp < D; ++comp) {
+    df_acc g[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) g[j] = acc_zero();
+#pragma unroll
+    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
+      df_acc sv = acc_zero(), s0 = acc_zero(), s1 = acc_zero();
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D + comp;
+        df_acc rv = acc_zero(), rd = acc_zero();
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float2 u = __ldg(row + a * D);
+          const df ud = df_make(u.x, u.y);
+          acc_mad(rv, ud, l[0][a]);
+          acc_mad(rd, ud, dl[0][a]);
+        }
+        acc_mad(sv, acc_pair(rv), l[1][b]);
+        acc_mad(s0, acc_pair(rd), l[1][b]);
+        acc_mad(s1, acc_pair(rv), dl[1][b]);
+      }
+      if constexpr (D == 3) {
+        acc_mad(g[0], acc_pair(s0), l[2][cz]);
+        acc_mad(g[1], acc_pair(s1), l[2][cz]);
+        acc_mad(g[2], acc_pair(sv), dl[2][cz]);
+      } else {
+        g[0] = s0;
+        g[1] = s1;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < D; ++j) Gu[comp][j] = acc_result(g[j]);
+  }
+}
+
+// J_ij = dPhi_i/dt_j from the monomial block: in 3D the monomials are
+// (t0, t1, t2, t0 t1, t0 t2, t1 t2, t0 t1 t2), in 2D (t0, t1, t0 t1).
+template <int D>
+__device__ __forceinline__ void map_jacobian_df(const CellBlock<D>& cb, const df t[D], df J[D][D]) {
+  if constexpr (D == 3) {
+    const df t01 = df_mul(t[0], t[1]), t02 = df_mul(t[0], t[2]), t12 = df_mul(t[1], t[2]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      df_acc j0 = acc_init(cb.a[0][i]), j1 = acc_init(cb.a[1][i]), j2 = acc_init(cb.a[2][i]);
+      acc_mad(j0, cb.a[3][i], t[1]);
+      acc_mad(j0, cb.a[4][i], t[2]);
+      acc_mad(j0, cb.a[6][i], t12);
+      acc_mad(j1, cb.a[3][i], t[0]);
+      acc_mad(j1, cb.a[5][i], t[2]);
+      acc_mad(j1, cb.a[6][i], t02);
+      acc_mad(j2, cb.a[4][i], t[0]);
+      acc_mad(j2, cb.a[5][i], t[1]);
+      acc_mad(j2, cb.a[6][i], t01);
+      J[i][0] = acc_result(j0);
+      J[i][1] = acc_result(j1);
+      J[i][2] = acc_result(j2);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      df_acc j0 = acc_init(cb.a[0][i]), j1 = acc_init(cb.a[1][i]);
+      acc_mad(j0, cb.a[2][i], t[1]);
+      acc_mad(j1, cb.a[2][i], t[0]);
+      J[i][0] = acc_result(j0);
+      J[i][1] = acc_result(j1);
+    }
+  }
+}
+
+// a b - c d
+__device__ __forceinline__ df df_det2(df a, df b, df c, df d) {
+  df_acc s = acc_zero();
+  acc_mad(s, a, b);
+  acc_mad(s, c, df_make(-d.hi, -d.lo));
+  return acc_result(s);
+}
+
+template <int D>
+__device__ __forceinline__ void invert_df(const df J[D][D], df Ji[D][D]) {
+  if constexpr (D == 2) {
+    const df inv = df_recip(df_det2(J[0][0], J[1][1], J[0][1], J[1][0]));
+    Ji[0][0] = df_mul(J[1][1], inv);
+    Ji[0][1] = df_mul(df_make(-J[0][1].hi, -J[0][1].lo), inv);
+    Ji[1][0] = df_mul(df_make(-J[1][0].hi, -J[1][0].lo), inv);
+    Ji[1][1] = df_mul(J[0][0], inv);
+  } else {
+    df c[3][3];
+    c[0][0] = df_det2(J[1][1], J[2][2], J[1][2], J[2][1]);
+    c[0][1] = df_det2(J[1][2], J[2][0], J[1][0], J[2][2]);
+    c[0][2] = df_det2(J[1][0], J[2][1], J[1][1], J[2][0]);
+    c[1][0] = df_det2(J[0][2], J[2][1], J[0][1], J[2][2]);
+    c[1][1] = df_det2(J[0][0], J[2][2], J[0][2], J[2][0]);
+    c[1][2] = df_det2(J[0][1], J[2][0], J[0][0], J[2][1]);
+    c[2][0] = df_det2(J[0][1], J[1][2], J[0][2], J[1][1]);
+    c[2][1] = df_det2(J[0][2], J[1][0], J[0][0], J[1][2]);
+    c[2][2] = df_det2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    df_acc det = acc_zero();
+    acc_mad(det, J[0][0], c[0][0]);
+    acc_mad(det, J[0][1], c[0][1]);
+    acc_mad(det, J[0][2], c[0][2]);
+    const df inv = df_recip(acc_result(det));
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) Ji[r][q] = df_mul(c[q][r], inv);
+  }
+}
+
+// G = du_h/dx at double-float reference coordinates t of cell K, in FP64.
+template <int D>
+__device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], double G[D][D]) {
+  df Gu[D][D], J[D][D], Ji[D][D];
+  q2_grad_df<D>(m, m.U2, K, t, Gu);
+  CellBlock<D> cb;
+  load_block<D>(m, K, cb);
+  map_jacobian_df<D>(cb, t, J);
+  invert_df<D>(J, Ji);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      df_acc s = acc_zero();
+#pragma unroll
+      for (int j = 0; j < D; ++j) acc_mad(s, Gu[c][j], Ji[j][q]);
+      G[c][q] = df_to_double(acc_result(s));
+    }
+}
+
+}  // namespace pic

@@ -6,12 +6,13 @@
 // system z = (x, d, F) stepped by the same RK tableau over the same located
 // stage points: the position part runs through advect_particle unchanged
 // (double-float stages, the same locate), so positions and cells are those
-// of pic_advect bit for bit, and at every stage an OdeHook evaluates G in
-// FP64 at the stage's (cell, x-hat) and advances its own stage values.
+// of pic_advect bit for bit, and at every stage an OdeHook evaluates G (in
+// double-float on the FP32 pipe, handed back in FP64) at the stage's
+// (cell, x-hat) and advances its own stage values in FP64.
 #include <cmath>
 
 #include "advect.cuh"
-#include "grad.cuh"
+#include "grad_df.cuh"
 
 namespace pic {
 
@@ -48,10 +49,8 @@ struct OdeHook {
     double zs[NZ];
 #pragma unroll
     for (int q = 0; q < NZ; ++q) zs[q] = p == 0 ? z[q] : z[q] + c * k[q];
-    double t64[D], G[D][D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) t64[a] = df_to_double(t[a]);
-    velocity_gradient<D>(m, K, t64, G);
+    double G[D][D];
+    velocity_gradient_df<D>(m, K, t, G);
     double f[NZ];
     f[0] = 0.0;
     if (o.damage >= 0) {
@@ -98,8 +97,14 @@ struct OdeHook {
   }
 };
 
+// Resident blocks per SM requested from the register allocator (swept at
+// build time with -DPIC_PROPS_MIN_BLOCKS=n).
+#ifndef PIC_PROPS_MIN_BLOCKS
+#define PIC_PROPS_MIN_BLOCKS 6
+#endif
+
 template <int D, int RK>
-__global__ void __launch_bounds__(128) advect_props_kernel(MeshView m, StoreView s, df dt, double dt64, OdeArgs o,
+__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) advect_props_kernel(MeshView m, StoreView s, df dt, double dt64, OdeArgs o,
                                                            uint32_t* __restrict__ cell_new,
                                                            uint32_t* __restrict__ counts,
                                                            DevCounters* __restrict__ ctr) {
