@@ -452,10 +452,14 @@ def run_props(args):
     }
 
 
+# FP32 flops (FADD + FMUL + 2 FFMA) per particle-step of the property-ODE
+# kernel (G and the stage arithmetic in double-float), counted by ncu on the
+# 64^3 x 20 workload (profiles/next_rows_c2_64cubed.md).
+PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 28040.0
+
 # FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
 # counted by ncu on the 64^3 x 20 workload; profiles/next_rows_c2_64cubed.md).
 FP64_FLOPS = {
-    "advect_props_kernel<3,RK4>": 3937.0,  # per particle-step
     "vertex_partial_kernel<3>": 42.00,     # per particle
     "lsq_linear_kernel<3>": 40.75,         # per particle
     "mh_seed_kernel<3>": 238.96,           # per chain step
@@ -533,9 +537,15 @@ def run_next(args):
     op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=10)
     op = op.subset(np.arange(op.n) % 5000 == 0)
     op.props[:, 1:10] = eye
+    ode_ms = ms - steady  # the ODE kernel: the step's time beyond the plain advect + rebin
+    ach = PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP * N / (ode_ms / 1e3) / 1e12
     rows["f2_property_odes"] = {
         "value": N / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms,
-        "roofline": _fp64_roof("advect_props_kernel<3,RK4>", N, ms),
+        "roofline": {"kernel": "props_ode_kernel<3,RK4>", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                     "fp32_flops_per_particle_step": PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP,
+                     "kernel_ms": ode_ms, "kernel_ms_how": "step with ODEs minus the plain step",
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"},
         "cpu_baseline": cpu(lambda: O.advect_properties(om, op, dt, 4, 1, damage=0, alpha=1.0, beta=0.5, defgrad=1),
                             op.n, "%d particles, one RK4 step with both ODEs" % op.n)}
     parts.close()

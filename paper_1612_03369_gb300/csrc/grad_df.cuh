@@ -163,9 +163,9 @@ __device__ __forceinline__ void invert_df(const df J[D][D], df Ji[D][D]) {
   }
 }
 
-// G = du_h/dx at double-float reference coordinates t of cell K, in FP64.
+// G = du_h/dx at double-float reference coordinates t of cell K.
 template <int D>
-__device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], double G[D][D]) {
+__device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], df G[D][D]) {
   df Gu[D][D], J[D][D], Ji[D][D];
   q2_grad_df<D>(m, m.U2, K, t, Gu);
   CellBlock<D> cb;
@@ -179,8 +179,28 @@ __device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t
       df_acc s = acc_zero();
 #pragma unroll
       for (int j = 0; j < D; ++j) acc_mad(s, Gu[c][j], Ji[j][q]);
-      G[c][q] = df_to_double(acc_result(s));
+      G[c][q] = acc_result(s);
     }
+}
+
+// The same, handed back in FP64.
+template <int D>
+__device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], double G[D][D]) {
+  df g[D][D];
+  velocity_gradient_df<D>(m, K, t, g);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+#pragma unroll
+    for (int q = 0; q < D; ++q) G[c][q] = df_to_double(g[c][q]);
+}
+
+// sqrt(a), a >= 0: FP32 root refined by one Newton step in double-float.
+__device__ __forceinline__ df df_sqrt(df a) {
+  if (!(a.hi > 0.f)) return df_make(0.f, 0.f);
+  const float r = __fsqrt_rn(a.hi);
+  const df r2 = two_prod(r, r);
+  const float e = __fdiv_rn(__fadd_rn(__fsub_rn(a.hi, r2.hi), __fsub_rn(a.lo, r2.lo)), __fmul_rn(2.0f, r));
+  return fast_two_sum(r, e);
 }
 
 }  // namespace pic

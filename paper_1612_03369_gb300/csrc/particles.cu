@@ -46,6 +46,7 @@ extern "C" pic_status pic_destroy_particles(pic_particles p) {
   cudaFree(p->perm);
   cudaFree(p->ctr);
   cudaFree(p->xfer);
+  cudaFree(p->stage_rec);
   for (int k = 0; k < 3 * p->ev_cap; ++k) cudaEventDestroy(p->ev[k]);
   free(p->ev);
   free(p);

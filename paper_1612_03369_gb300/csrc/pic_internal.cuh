@@ -97,6 +97,7 @@ struct pic_particles_s {
   uint32_t* perm;         // [capacity]
   pic::DevCounters* ctr;  // device counters and status word
   double* xfer;           // [2 * 2^dim][C] per-cell partial sums of the vertex averages, allocated on first use
+  void* stage_rec;        // property ODEs: per stage cell [4][cap] u32 then x-hat [4][dim][cap] float2, on first use
   cudaStream_t stream;
   // optional event timing of pic_advect (instrumentation)
   int timing;

@@ -4,11 +4,16 @@
 //   deformation gradient F' = G F,                         G = grad u_h
 // with |.| the Frobenius norm.  The properties and the position form one
 // system z = (x, d, F) stepped by the same RK tableau over the same located
-// stage points: the position part runs through advect_particle unchanged
-// (double-float stages, the same locate), so positions and cells are those
-// of pic_advect bit for bit, and at every stage an OdeHook evaluates G (in
-// double-float on the FP32 pipe, handed back in FP64) at the stage's
-// (cell, x-hat) and advances its own stage values in FP64.
+// stage points.  Each time step runs in two kernels:
+//   1. the particle step of pic_advect (the same advect_particle, so
+//      positions, cells and order are those of pic_advect bit for bit),
+//      recording every stage's (cell, x-hat);
+//   2. the ODEs over the recorded stages, G and the stage arithmetic in
+//      double-float on the FP32 pipe, without the locate code, so this
+//      kernel keeps few registers live and many warps resident;
+// then the rebin carries the properties with the particles.  The stage
+// records take 4 (4 + 8 dim) bytes per particle of scratch, allocated with
+// the store on first use.
 #include <cmath>
 
 #include "advect.cuh"
@@ -19,95 +24,37 @@ namespace pic {
 struct OdeArgs {
   int damage;   // property slot of d, or -1
   int defgrad;  // first of D*D slots of F (row-major), or -1
-  double alpha, beta;
+  df alpha, beta;
 };
 
-template <int D, int RK>
-struct OdeHook {
-  static constexpr int NZ = 1 + D * D;  // z = (d, F_00, F_01, ...)
-  const MeshView& m;
-  const double dt;
-  const OdeArgs& o;
-  double z[NZ], k[NZ], acc[NZ];
+// Stage records: for every evaluation point p < S of particle i, the located
+// cell and the double-float reference coordinates, [S][i] and [S][D][i].
+struct StageRec {
+  uint32_t* cell;
+  float2* t;
+  size_t cap;
+};
 
-  __device__ __forceinline__ OdeHook(const MeshView& m_, const StoreView& s, uint32_t i, double dt_,
-                                     const OdeArgs& o_)
-      : m(m_), dt(dt_), o(o_) {
-    z[0] = o.damage >= 0 ? s.props[(size_t)o.damage * s.cap + i] : 0.0;
-#pragma unroll
-    for (int q = 0; q < D * D; ++q) z[1 + q] = o.defgrad >= 0 ? s.props[(size_t)(o.defgrad + q) * s.cap + i] : 0.0;
-#pragma unroll
-    for (int q = 0; q < NZ; ++q) k[q] = acc[q] = 0.0;
-  }
-
-  // Evaluation point p: stage value z_p = z + c_p k_{p-1}, increment
-  // k_p = dt f(z_p) with f from G at the located stage point.
-  template <int DD>
+struct RecordHook {
+  StageRec r;
+  uint32_t i;
+  template <int D>
   __device__ __forceinline__ void stage(int p, uint32_t K, const df* t) {
-    using TB = Tableau<RK>;
-    const double c = p == 0 ? 0.0 : (double)TB::c(p);
-    double zs[NZ];
+    r.cell[(size_t)p * r.cap + i] = K;
 #pragma unroll
-    for (int q = 0; q < NZ; ++q) zs[q] = p == 0 ? z[q] : z[q] + c * k[q];
-    double G[D][D];
-    velocity_gradient_df<D>(m, K, t, G);
-    double f[NZ];
-    f[0] = 0.0;
-    if (o.damage >= 0) {
-      double s = 0.0;
-#pragma unroll
-      for (int r = 0; r < D; ++r)
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          const double e = 0.5 * (G[r][q] + G[q][r]);
-          s += e * e;
-        }
-      f[0] = o.alpha * sqrt(s) - o.beta * zs[0];
-    }
-#pragma unroll
-    for (int r = 0; r < D; ++r)
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        double a = 0.0;
-        if (o.defgrad >= 0) {
-#pragma unroll
-          for (int j = 0; j < D; ++j) a += G[r][j] * zs[1 + j * D + q];
-        }
-        f[1 + r * D + q] = a;
-      }
-    const double w = (double)TB::w(p);
-#pragma unroll
-    for (int q = 0; q < NZ; ++q) {
-      k[q] = dt * f[q];
-      if (w != 0.0) acc[q] += w * k[q];
-    }
-  }
-
-  // z_{n+1} = z + sum_s b_s k_s, written to the enabled slots.
-  __device__ __forceinline__ void finish(const StoreView& s, uint32_t i) const {
-    using TB = Tableau<RK>;
-    double zn[NZ];
-#pragma unroll
-    for (int q = 0; q < NZ; ++q) zn[q] = TB::divide6() ? z[q] + acc[q] / 6.0 : z[q] + acc[q];
-    if (o.damage >= 0) s.props[(size_t)o.damage * s.cap + i] = zn[0];
-    if (o.defgrad >= 0) {
-#pragma unroll
-      for (int q = 0; q < D * D; ++q) s.props[(size_t)(o.defgrad + q) * s.cap + i] = zn[1 + q];
-    }
+    for (int a = 0; a < D; ++a) r.t[((size_t)p * D + a) * r.cap + i] = make_float2(t[a].hi, t[a].lo);
   }
 };
 
-// Resident blocks per SM requested from the register allocator (swept at
-// build time with -DPIC_PROPS_MIN_BLOCKS=n).
-#ifndef PIC_PROPS_MIN_BLOCKS
-#define PIC_PROPS_MIN_BLOCKS 6
-#endif
-
+// Phase 1: the particle step of pic_advect (the same advect_particle, so
+// positions, cells and order are bit for bit those of pic_advect), leaving
+// each stage's (cell, x-hat) behind.
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) advect_props_kernel(MeshView m, StoreView s, df dt, double dt64, OdeArgs o,
-                                                           uint32_t* __restrict__ cell_new,
-                                                           uint32_t* __restrict__ counts,
-                                                           DevCounters* __restrict__ ctr) {
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kernel(MeshView m, StoreView s, df dt,
+                                                                                  StageRec rec,
+                                                                                  uint32_t* __restrict__ cell_new,
+                                                                                  uint32_t* __restrict__ counts,
+                                                                                  DevCounters* __restrict__ ctr) {
   const uint32_t n = ctr->n_alive;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -116,17 +63,104 @@ __global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) advect_props_kernel
     unsigned flags = 0, lost = 0, steps = 0;
     if (i < n) {
       steps = 1;
-      OdeHook<D, RK> hook(m, s, i, dt64, o);
+      RecordHook hook{rec, i};
       const uint32_t Kn = advect_particle<D, RK, false, false>(m, s, i, s.cell[i], dt, iters, flags, hook);
       cell_new[i] = Kn;
-      if (Kn != PIC_LOST) {
-        hook.finish(s, i);
+      if (Kn != PIC_LOST)
         atomicAdd(counts + Kn, 1u);
-      } else {
+      else
         lost = 1;
-      }
     }
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
+  }
+}
+
+// Phase 2, thread per surviving particle: the property ODEs over the recorded
+// stages, in double-float.  For stage p: z_p = z + c_p k_{p-1},
+// k_p = dt f(G_p, z_p), and z' = z + sum_p w_p k_p (/ 6 for RK4), with
+//   f_d = alpha |(G + G^T)/2|_F - beta d,   f_F = G F.
+// Resident blocks per SM requested from the register allocator (swept at
+// build time with -DPIC_PROPS_MIN_BLOCKS=n).
+#ifndef PIC_PROPS_MIN_BLOCKS
+#define PIC_PROPS_MIN_BLOCKS 5
+#endif
+
+template <int D, int RK>
+__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(MeshView m, StoreView s, df dt, OdeArgs o, StageRec rec,
+                                                        const uint32_t* __restrict__ cell_new,
+                                                        const DevCounters* __restrict__ ctr) {
+  using TB = Tableau<RK>;
+  constexpr int NZ = 1 + D * D;  // z = (d, F_00, F_01, ...)
+  const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);
+  const uint32_t n = ctr->n_alive;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (cell_new[i] == PIC_LOST) continue;
+    df z[NZ], k[NZ], acc[NZ];
+    z[0] = o.damage >= 0 ? df_from_double(s.props[(size_t)o.damage * s.cap + i]) : df_make(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < D * D; ++q)
+      z[1 + q] = o.defgrad >= 0 ? df_from_double(s.props[(size_t)(o.defgrad + q) * s.cap + i]) : df_make(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NZ; ++q) k[q] = acc[q] = df_make(0.f, 0.f);
+#pragma unroll 1
+    for (int p = 0; p < TB::S; ++p) {
+      const uint32_t K = rec.cell[(size_t)p * rec.cap + i];
+      if (K >= m.C) break;  // cannot happen for a survivor
+      df t[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float2 v = rec.t[((size_t)p * D + a) * rec.cap + i];
+        t[a] = df_make(v.x, v.y);
+      }
+      df G[D][D];
+      velocity_gradient_df<D>(m, K, t, G);
+      const float c = p == 0 ? 0.f : TB::c(p);
+      df zs[NZ];
+#pragma unroll
+      for (int q = 0; q < NZ; ++q) zs[q] = p == 0 ? z[q] : df_add(z[q], df_scale2(k[q], c));
+      df f[NZ];
+      f[0] = df_make(0.f, 0.f);
+      if (o.damage >= 0) {
+        df_acc e2 = acc_zero();
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            const df e = df_scale2(df_add(G[r][q], G[q][r]), 0.5f);
+            acc_mad(e2, e, e);
+          }
+        df_acc fd = acc_zero();
+        acc_mad(fd, o.alpha, df_sqrt(acc_result(e2)));
+        acc_mad(fd, df_make(-o.beta.hi, -o.beta.lo), zs[0]);
+        f[0] = acc_result(fd);
+      }
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          df_acc a = acc_zero();
+          if (o.defgrad >= 0) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) acc_mad(a, G[r][j], zs[1 + j * D + q]);
+          }
+          f[1 + r * D + q] = acc_result(a);
+        }
+      const float w = TB::w(p);
+#pragma unroll
+      for (int q = 0; q < NZ; ++q) {
+        k[q] = df_mul(dt, f[q]);
+        if (w != 0.f) acc[q] = df_add(acc[q], df_scale2(k[q], w));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NZ; ++q) {
+      const df zn = df_add(z[q], TB::divide6() ? df_mul(acc[q], sixth) : acc[q]);
+      if (q == 0) {
+        if (o.damage >= 0) s.props[(size_t)o.damage * s.cap + i] = df_to_double(zn);
+      } else if (o.defgrad >= 0) {
+        s.props[(size_t)(o.defgrad + q - 1) * s.cap + i] = df_to_double(zn);
+      }
+    }
   }
 }
 
@@ -137,20 +171,27 @@ static int props_grid(size_t n) {
   return (int)(g > 0 ? g : 1);
 }
 
+template <int D, int RK>
+static void launch_props_rk(pic_particles_s* p, const MeshView& m, df dt, const OdeArgs& o, StageRec rec,
+                            cudaStream_t st) {
+  const StoreView s = store_view(p, p->cur);
+  const int g = props_grid(p->capacity);
+  advect_record_kernel<D, RK><<<g, 128, 0, st>>>(m, s, dt, rec, p->cell_new, p->counts, p->ctr);
+  props_ode_kernel<D, RK><<<g, 128, 0, st>>>(m, s, dt, o, rec, p->cell_new, p->ctr);
+  count_launches(2);
+}
+
 template <int D>
-static void launch_props(pic_particles_s* p, const MeshView& m, double dt, int rk, const OdeArgs& o,
+static void launch_props(pic_particles_s* p, const MeshView& m, double dt, int rk, const OdeArgs& o, StageRec rec,
                          cudaStream_t st) {
   const float hi = (float)dt;
   const df dtd = {hi, (float)(dt - (double)hi)};
-  const StoreView s = store_view(p, p->cur);
-  const int g = props_grid(p->capacity);
   if (rk == 1)
-    advect_props_kernel<D, 1><<<g, 128, 0, st>>>(m, s, dtd, dt, o, p->cell_new, p->counts, p->ctr);
+    launch_props_rk<D, 1>(p, m, dtd, o, rec, st);
   else if (rk == 2)
-    advect_props_kernel<D, 2><<<g, 128, 0, st>>>(m, s, dtd, dt, o, p->cell_new, p->counts, p->ctr);
+    launch_props_rk<D, 2>(p, m, dtd, o, rec, st);
   else
-    advect_props_kernel<D, 4><<<g, 128, 0, st>>>(m, s, dtd, dt, o, p->cell_new, p->counts, p->ctr);
-  count_launches(1);
+    launch_props_rk<D, 4>(p, m, dtd, o, rec, st);
 }
 
 }  // namespace pic
@@ -183,15 +224,30 @@ extern "C" pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, 
     return (set_error("pic_advect_properties: damage slot overlaps the deformation slots"), PIC_ERR_ARG);
   if (odes->damage >= 0 && !(std::isfinite(odes->alpha) && std::isfinite(odes->beta)))
     return (set_error("pic_advect_properties: alpha, beta not finite"), PIC_ERR_ARG);
-  const OdeArgs o = {odes->damage, odes->deformation, odes->alpha, odes->beta};
+  auto split = [](double v) {
+    const float hi = (float)v;
+    return df{hi, (float)(v - (double)hi)};
+  };
+  const OdeArgs o = {odes->damage, odes->deformation, split(odes->alpha), split(odes->beta)};
   cudaStream_t st = (cudaStream_t)stream;
   const MeshView m = mesh_view(mesh);
+  if (!parts->stage_rec) {
+    const size_t bytes = (size_t)4 * parts->capacity * (sizeof(uint32_t) + sizeof(float2) * d);
+    if (cudaMalloc(&parts->stage_rec, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      parts->stage_rec = nullptr;
+      return (set_error("pic_advect_properties: cannot allocate %zu bytes of stage records", bytes), PIC_ERR_OOM);
+    }
+  }
+  const StageRec rec = {(uint32_t*)parts->stage_rec,
+                        (float2*)((char*)parts->stage_rec + (size_t)4 * parts->capacity * sizeof(uint32_t)),
+                        parts->capacity};
   for (int step = 0; step < n_steps; ++step) {
     PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
     if (d == 2)
-      launch_props<2>(parts, m, dt, (int)integrator, o, st);
+      launch_props<2>(parts, m, dt, (int)integrator, o, rec, st);
     else
-      launch_props<3>(parts, m, dt, (int)integrator, o, st);
+      launch_props<3>(parts, m, dt, (int)integrator, o, rec, st);
     PIC_CUDA(cudaGetLastError());
     pic_status r = rebin_from_counts(parts, st);
     if (r != PIC_OK) return r;
