@@ -82,24 +82,23 @@ struct TapeStep {
   const uint32_t* n_next;  // particles after the step
 };
 
-// One reverse step for every particle alive after it (thread per new slot j).
-// The stages are recomputed exactly as the forward computed them (double-
-// float locate and Q2 contraction, so the stage cells are the forward's);
-// G = du/dx at each stage is evaluated in double-float and handed back in
-// FP64, where the sweep of lambda runs.
-// Resident blocks per SM requested from the register allocator (swept at
-// build time with -DPIC_REVERSE_MIN_BLOCKS=n).
+// Resident blocks per SM requested from the register allocator for the
+// lambda sweep (swept at build time with -DPIC_REVERSE_MIN_BLOCKS=n).
 #ifndef PIC_REVERSE_MIN_BLOCKS
-#define PIC_REVERSE_MIN_BLOCKS 3
+#define PIC_REVERSE_MIN_BLOCKS 4
 #endif
 
+// One reverse step, in two kernels over the particles alive after the step
+// (thread per new slot j, old slot i = perm[j]).
+//
+// reverse_stages_kernel recomputes the step's stages from the checkpoint
+// exactly as the forward computed them (double-float stage points, the same
+// locate and Q2 contraction, so the stage cells are the forward's) and
+// leaves stage s's cell and double-float x-hat in record 4 j + s.
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_step_kernel(MeshView m, TapeStep tp, size_t cap, double dt,
-                                                           const double* __restrict__ lam_in,
-                                                           double* __restrict__ lam_out,
-                                                           uint32_t* __restrict__ rec_cell,
-                                                           uint64_t* __restrict__ rec_key, float2* __restrict__ rec_t,
-                                                           float2* __restrict__ rec_w, DevCounters* __restrict__ ctr) {
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) reverse_stages_kernel(
+    MeshView m, TapeStep tp, size_t cap, double dt, uint32_t* __restrict__ rec_cell, float2* __restrict__ rec_t,
+    DevCounters* __restrict__ ctr) {
   using TB = AdjTableau<RK>;
   constexpr int S = TB::S;
   const uint32_t n = *tp.n_next;
@@ -112,71 +111,101 @@ __global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_step_kern
       latch_status(ctr, PIC_STATUS_BOUNDS);
       continue;
     }
-    double x[D], lam[D];
-    df xd[D], ts[S][D];
-    double G[S][D][D];
-    uint32_t Ks[S];
+    df xd[D], ts[D], k[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      x[a] = tp.x[a * cap + i];
       const float2 v = tp.xhat[a * cap + i];
-      ts[0][a] = df_make(v.x, v.y);
-      lam[a] = lam_in[a * cap + j];
-      xd[a] = df_from_double(x[a]);
+      ts[a] = df_make(v.x, v.y);
+      xd[a] = df_from_double(tp.x[a * cap + i]);
     }
-    Ks[0] = tp.cell[i];
-    bool ok = Ks[0] < m.C;
-    df k[D];
+    uint32_t K = tp.cell[i];
+    if (K >= m.C) {
+      latch_status(ctr, PIC_STATUS_BOUNDS);
+      continue;
+    }
     int iters = 0;
     unsigned flags = 0;
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < S; ++s) {
-      if (!ok) break;
       if (s > 0) {
         df y[D];
         float hint[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           y[a] = df_add(xd[a], df_scale2(k[a], (float)TB::a(s)));
-          hint[a] = ts[s - 1][a].hi;
+          hint[a] = ts[a].hi;
         }
-        Ks[s] = locate_df<D>(m, y, Ks[s - 1], hint, ts[s], iters, flags);
-        if (Ks[s] == PIC_LOST) {
-          ok = false;
+        K = locate_df<D>(m, y, K, hint, ts, iters, flags);
+        if (K == PIC_LOST) {
+          // cannot happen for a particle that survived the step; keep it harmless
+          latch_status(ctr, PIC_STATUS_BOUNDS);
           break;
         }
       }
-      df u[D];
-      q2_eval_df<D>(m, m.U2, Ks[s], ts[s], u);
+      const size_t r = (size_t)kRecPerParticle * j + s;
+      rec_cell[r] = K;
 #pragma unroll
-      for (int a = 0; a < D; ++a) k[a] = df_mul(dtd, u[a]);
-      velocity_gradient_df<D>(m, Ks[s], ts[s], G[s]);
+      for (int a = 0; a < D; ++a) rec_t[a * rcap + r] = make_float2(ts[a].hi, ts[a].lo);
+      if (s + 1 < S) {
+        df u[D];
+        q2_eval_df<D>(m, m.U2, K, ts, u);
+#pragma unroll
+        for (int a = 0; a < D; ++a) k[a] = df_mul(dtd, u[a]);
+      }
     }
+  }
+}
+
+// reverse_lambda_kernel sweeps the stages backwards with G_s = du/dx at the
+// recorded stage points (double-float, handed back in FP64; lambda in FP64):
+//   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
+//   lambda_y_s = dt G_s^T lambda_k_s,   lambda = lambda' + sum_s lambda_y_s
+// and completes record 4 j + s with its key and weight dt lambda_k_s.  A
+// particle whose stages were not all recorded has its records cleared.
+template <int D, int RK>
+__global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_kernel(
+    MeshView m, TapeStep tp, size_t cap, double dt, const double* __restrict__ lam_in, double* __restrict__ lam_out,
+    uint32_t* __restrict__ rec_cell, uint64_t* __restrict__ rec_key, const float2* __restrict__ rec_t,
+    float2* __restrict__ rec_w) {
+  using TB = AdjTableau<RK>;
+  constexpr int S = TB::S;
+  const uint32_t n = *tp.n_next;
+  const size_t rcap = kRecPerParticle * cap;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = tp.perm[j];
+    if (i >= cap) continue;
+    bool ok = true;
+#pragma unroll
+    for (int s = 0; s < S; ++s) ok = ok && rec_cell[(size_t)kRecPerParticle * j + s] < m.C;
     if (!ok) {
-      // cannot happen for a particle that survived the step; keep it harmless
-      latch_status(ctr, PIC_STATUS_BOUNDS);
 #pragma unroll
       for (int s = 0; s < kRecPerParticle; ++s) rec_cell[(size_t)kRecPerParticle * j + s] = PIC_LOST;
       continue;
     }
-    // reverse sweep over the stages
-    double lam_x[D], lam_ynext[D];
+    double lam[D], lam_x[D], lam_ynext[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
+      lam[a] = lam_in[a * cap + j];
       lam_x[a] = lam[a];
       lam_ynext[a] = 0.0;
     }
-#pragma unroll
+#pragma unroll 1
     for (int s = S - 1; s >= 0; --s) {
+      const size_t r = (size_t)kRecPerParticle * j + s;
+      df t[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const float2 v = rec_t[a * rcap + r];
+        t[a] = df_make(v.x, v.y);
+      }
+      double G[D][D];
+      velocity_gradient_df<D>(m, rec_cell[r], t, G);
       double lk[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) lk[a] = TB::b(s) * lam[a] + (s + 1 < S ? TB::a(s + 1) * lam_ynext[a] : 0.0);
-      const size_t r = (size_t)kRecPerParticle * j + s;
-      rec_cell[r] = Ks[s];
       rec_key[r] = r;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        rec_t[a * rcap + r] = make_float2(ts[s][a].hi, ts[s][a].lo);
         const df w = df_from_double(dt * lk[a]);
         rec_w[a * rcap + r] = make_float2(w.hi, w.lo);
       }
@@ -184,7 +213,7 @@ __global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_step_kern
       for (int q = 0; q < D; ++q) {
         double acc = 0.0;
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc += G[s][c][q] * lk[c];
+        for (int c = 0; c < D; ++c) acc += G[c][q] * lk[c];
         lam_ynext[q] = dt * acc;
         lam_x[q] += lam_ynext[q];
       }
@@ -341,8 +370,10 @@ static int grid_of(size_t n, int block) {
 template <int D, int RK>
 static void launch_reverse(pic_tape_s* tp, const MeshView& m, const TapeStep& ts, const double* lin, double* lout,
                            cudaStream_t st) {
-  reverse_step_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, lin, lout, tp->rec_cell,
-                                                                     tp->rec_key, tp->rec_t, tp->rec_w, tp->parts->ctr);
+  reverse_stages_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, tp->rec_cell, tp->rec_t,
+                                                                       tp->parts->ctr);
+  reverse_lambda_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, lin, lout, tp->rec_cell,
+                                                                       tp->rec_key, tp->rec_t, tp->rec_w);
 }
 
 }  // namespace pic
@@ -492,7 +523,7 @@ extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, do
       else if (tp->integrator == 2) launch_reverse<3, 2>(tp, m, ts, lin, lout, st);
       else launch_reverse<3, 4>(tp, m, ts, lin, lout, st);
     }
-    count_launches(1);
+    count_launches(2);
     PIC_CUDA(cudaGetLastError());
     pic_status r = sort_by_cell_run(rcap, tp->rec_cell, tp->rec_key, tp->C, tp->rec_perm, tp->rec_off, sc, st);
     if (r != PIC_OK) return r;
