@@ -102,6 +102,21 @@ pic_status pic_destroy_mesh(pic_mesh mesh);
  * Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_set_velocity_dofs(pic_mesh mesh, const double *U, const double *U_next, void *stream);
 
+/* Staged upload of the next field, so that its copy overlaps the current
+ * step (a flow solver hands over u_h^{n+1} while the particles take step n).
+ * pic_stage_velocity_dofs copies U ([dim][nnodes] FP64, host (pinned for an
+ * asynchronous copy) or device) into a staging buffer on copy_stream; the
+ * caller keeps U unchanged until the copy has run (copy_stream order).
+ * pic_commit_velocity_dofs makes the staged field the field of the mesh on
+ * `stream`: `stream` waits for the copy, then the FP32 and double-float
+ * copies are rebuilt there.  A staging buffer is allocated on first use; a
+ * later stage waits (on the device) until the previous commit's conversions
+ * have released it.  U_next, if set, is unchanged.
+ * Errors: PIC_ERR_ARG; PIC_ERR_STATE (no first field set, a stage while one
+ * is pending, a commit with nothing staged); PIC_ERR_OOM; PIC_ERR_CUDA. */
+pic_status pic_stage_velocity_dofs(pic_mesh mesh, const double *U, void *copy_stream);
+pic_status pic_commit_velocity_dofs(pic_mesh mesh, void *stream);
+
 /* Generation from local coordinates (Sec. 2.2, Remark "local generation"):
  * cells are visited in index order and n_K particles created in cell K with
  * reference coordinates x-hat uniform in [0,1)^dim, position x = Phi_K(x-hat),

@@ -189,6 +189,9 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
 
 extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   if (!m) return PIC_OK;
+  cudaFree(m->Ustage);
+  if (m->ev_staged) cudaEventDestroy(m->ev_staged);
+  if (m->ev_free) cudaEventDestroy(m->ev_free);
   cudaFree(m->X);
   cudaFree(m->U);
   cudaFree(m->U32);
@@ -233,5 +236,53 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
   m->has_next = U_next ? 1 : 0;
+  return PIC_OK;
+}
+
+// Staged upload (overlap of the next field's copy with the current step).
+// The copy goes to a staging buffer on `copy_stream`; it first waits for the
+// buffer to be free (the conversions of the commit that last released it).
+extern "C" pic_status pic_stage_velocity_dofs(pic_mesh m, const double* U, void* copy_stream) {
+  if (!m || !U) return (set_error("pic_stage_velocity_dofs: null argument"), PIC_ERR_ARG);
+  if (!m->has_velocity) return (set_error("pic_stage_velocity_dofs: set a first field with pic_set_velocity_dofs"), PIC_ERR_STATE);
+  if (m->staged) return (set_error("pic_stage_velocity_dofs: a staged field is not committed yet"), PIC_ERR_STATE);
+  cudaStream_t cs = (cudaStream_t)copy_stream;
+  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
+  if (!m->Ustage) {
+    if (cudaMalloc(&m->Ustage, sizeof(double) * n) != cudaSuccess) {
+      cudaGetLastError();
+      m->Ustage = nullptr;
+      return (set_error("pic_stage_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
+    }
+  }
+  if (!m->ev_staged) PIC_CUDA(cudaEventCreateWithFlags(&m->ev_staged, cudaEventDisableTiming));
+  if (!m->ev_free) PIC_CUDA(cudaEventCreateWithFlags(&m->ev_free, cudaEventDisableTiming));
+  if (m->free_recorded) PIC_CUDA(cudaStreamWaitEvent(cs, m->ev_free, 0));
+  PIC_CUDA(cudaMemcpyAsync(m->Ustage, U, sizeof(double) * n, cudaMemcpyDefault, cs));
+  PIC_CUDA(cudaEventRecord(m->ev_staged, cs));
+  m->staged = 1;
+  return PIC_OK;
+}
+
+// Make the staged field the field u_h^n on `stream`: wait for the copy, swap
+// the FP64 buffers, rebuild the FP32 and double-float copies, and mark the
+// released buffer free once those conversions have run.
+extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
+  if (!m) return (set_error("pic_commit_velocity_dofs: null mesh"), PIC_ERR_ARG);
+  if (!m->staged) return (set_error("pic_commit_velocity_dofs: nothing staged"), PIC_ERR_STATE);
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
+  PIC_CUDA(cudaStreamWaitEvent(st, m->ev_staged, 0));
+  double* t = m->U;
+  m->U = m->Ustage;
+  m->Ustage = t;
+  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
+  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  count_launches(2);
+  PIC_CUDA(cudaGetLastError());
+  PIC_CUDA(cudaEventRecord(m->ev_free, st));
+  m->free_recorded = 1;
+  m->staged = 0;
   return PIC_OK;
 }

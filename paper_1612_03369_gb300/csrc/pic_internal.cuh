@@ -70,6 +70,11 @@ struct pic_mesh_s {
   int has_next;
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
+  // staged upload of the next field (pic_stage_velocity_dofs): FP64 buffer,
+  // "copy done" and "buffer free" events, created on first use
+  double* Ustage;
+  cudaEvent_t ev_staged, ev_free;
+  int staged, free_recorded;
 };
 
 struct pic_particles_s {

@@ -34,6 +34,8 @@ SIGNATURES = {
     "pic_destroy_particles": (_I, [_P]),
     "pic_set_properties": (_I, [_P, _I, _P, _P]),
     "pic_advect": (_I, [_P, _P, _F64, _I, _I, _I, _P]),
+    "pic_stage_velocity_dofs": (_I, [_P, _P, _P]),
+    "pic_commit_velocity_dofs": (_I, [_P, _P]),
     "pic_cell_weights": (_I, [_P, _P, _P, _P]),
     "pic_draw_cell_counts": (_I, [_U32, _P, _U64, _U64, _P, _P]),
     "pic_seed_particles_mh": (_I, [_P, _P, _P, _U32, _U64, _U64, _I, _SZ, _P, _P]),
@@ -149,6 +151,15 @@ def pic_set_properties(h: int, prop: int, values, stream=None):
 def pic_advect(parts: int, mesh: int, dt: float, integrator: int, precision: int, n_steps: int, stream=None):
     _check(_lib.pic_advect(parts, mesh, float(dt), int(integrator), int(precision), int(n_steps), _stream(stream)),
            "pic_advect")
+
+
+def pic_stage_velocity_dofs(mesh: int, U, copy_stream=None):
+    """U: pinned host tensor (asynchronous copy) or device tensor [dim][nnodes] float64."""
+    _check(_lib.pic_stage_velocity_dofs(mesh, _ptr(U), _stream(copy_stream)), "pic_stage_velocity_dofs")
+
+
+def pic_commit_velocity_dofs(mesh: int, stream=None):
+    _check(_lib.pic_commit_velocity_dofs(mesh, _stream(stream)), "pic_commit_velocity_dofs")
 
 
 def pic_cell_weights(mesh: int, rho, w, stream=None):
