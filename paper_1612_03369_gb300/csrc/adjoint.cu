@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) reverse_stages_ker
       for (int a = 0; a < D; ++a) rec_t[a * rcap + r] = make_float2(ts[a].hi, ts[a].lo);
       if (s + 1 < S) {
         df u[D];
-        q2_eval_df<D>(m, m.U2, K, ts, u);
+        q2_eval_df<D>(m, m.Qc, K, ts, u);
 #pragma unroll
         for (int a = 0; a < D; ++a) k[a] = df_mul(dtd, u[a]);
       }

@@ -42,27 +42,27 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
 // t^n + theta dt, theta = 0, 1/2, 1 for tcode = 0, 1, 2: the steady field,
 // or with a second field set, (1 - theta) u_h^n + theta u_h^{n+1} (reading
 // of the time interpolation of Sec. 2.3; theta = 1/2 is the exact average).
-// The Q2 contraction is in double-float, or FP32 for the precision form; it
-// sits in a rolled loop over the (one or two) fields so the kernel holds one
-// copy of it.
+// The Q2 evaluation (per-cell monomial form, Horner) is in double-float, or
+// FP32 for the precision form; it sits in a rolled loop over the (one or two)
+// fields so the kernel holds one copy of it.
 template <int D, bool F32B, bool TWO>
 __device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const df t[D], int tcode, df u[D]) {
   if constexpr (!TWO) {
     if constexpr (F32B)
-      q2_eval_f32<D>(m, m.U2, K, t, u);
+      q2_eval_f32<D>(m, m.Qc, K, t, u);
     else
-      q2_eval_df<D>(m, m.U2, K, t, u);
+      q2_eval_df<D>(m, m.Qc, K, t, u);
     return;
   }
   const bool two = m.has_next && tcode == 1;
-  const float2* first = (m.has_next && tcode == 2) ? m.U2n : m.U2;
+  const float4* first = (m.has_next && tcode == 2) ? m.Qcn : m.Qc;
 #pragma unroll 1
   for (int f = 0; f < (two ? 2 : 1); ++f) {
     df v[D];
     if constexpr (F32B)
-      q2_eval_f32<D>(m, f == 0 ? first : m.U2n, K, t, v);
+      q2_eval_f32<D>(m, f == 0 ? first : m.Qcn, K, t, v);
     else
-      q2_eval_df<D>(m, f == 0 ? first : m.U2n, K, t, v);
+      q2_eval_df<D>(m, f == 0 ? first : m.Qcn, K, t, v);
 #pragma unroll
     for (int a = 0; a < D; ++a) u[a] = (f == 0) ? v[a] : df_scale2(df_add(u[a], v[a]), 0.5f);
   }

@@ -393,8 +393,8 @@ __device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], 
 // ---------------------------------------------------------- Q2 velocity --
 // u_h = sum_{a,b,c} U[node(K; a,b,c)] l_a(t0) l_b(t1) l_c(t2) with the 1D
 // quadratic Lagrange basis on {0, 1/2, 1}:
-//   l0 = (1-t)(1-2t) = -w v,  l1 = 4 t w,  l2 = t v,  w = 1-t, v = 2t-1,
-// all in double-float, contracted one axis at a time.
+//   l0 = (1-t)(1-2t) = -w v,  l1 = 4 t w,  l2 = t v,  w = 1-t, v = 2t-1.
+// lagrange2_df gives the basis in double-float (used by the gradient).
 
 __device__ __forceinline__ void lagrange2_df(df t, df l[3]) {
   const df ws = two_sum(1.0f, -t.hi);
@@ -407,100 +407,96 @@ __device__ __forceinline__ void lagrange2_df(df t, df l[3]) {
   l[2] = df_mul(t, v);
 }
 
-template <int D>
-__device__ __forceinline__ void q2_eval_df(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
-                                           df u[D]) {
-  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
-  df L0[3], L1[3], L2[3];
-  lagrange2_df(t[0], L0);
-  lagrange2_df(t[1], L1);
-  if constexpr (D == 3) lagrange2_df(t[2], L2);
-  df_acc outer[D];
-#pragma unroll
-  for (int comp = 0; comp < D; ++comp) outer[comp] = acc_zero();
-  // rows (b, cz) in order; the basis values of the current b and cz sit in
-  // L1[0] and L2[0] and are rotated after each row (no indexed register
-  // arrays, rolled loops keep the instruction footprint small)
-#pragma unroll 1
-  for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
-    df_acc mid[D];
-#pragma unroll
-    for (int comp = 0; comp < D; ++comp) mid[comp] = acc_zero();
-#pragma unroll 1
-    for (int b = 0; b < 3; ++b) {
-      const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
-      float2 nd[3 * D];
-#pragma unroll
-      for (int q = 0; q < 3 * D; ++q) nd[q] = __ldg(row + q);
-#pragma unroll
-      for (int comp = 0; comp < D; ++comp) {
-        df_acc r;
-        {
-          const df p = two_prod(nd[comp].x, L0[0].hi);
-          float lo = __fmaf_rn(nd[comp].x, L0[0].lo, p.lo);
-          r.s = p.hi;
-          r.e = __fmaf_rn(nd[comp].y, L0[0].hi, lo);
-        }
-        acc_mad(r, df_make(nd[D + comp].x, nd[D + comp].y), L0[1]);
-        acc_mad(r, df_make(nd[2 * D + comp].x, nd[2 * D + comp].y), L0[2]);
-        acc_mad(mid[comp], acc_pair(r), L1[0]);
-      }
-      const df l = L1[0];
-      L1[0] = L1[1];
-      L1[1] = L1[2];
-      L1[2] = l;
-    }
-#pragma unroll
-    for (int comp = 0; comp < D; ++comp) {
-      if constexpr (D == 3)
-        acc_mad(outer[comp], acc_pair(mid[comp]), L2[0]);
-      else
-        outer[comp] = mid[comp];
-    }
-    if constexpr (D == 3) {
-      const df l = L2[0];
-      L2[0] = L2[1];
-      L2[1] = L2[2];
-      L2[2] = l;
-    }
-  }
-#pragma unroll
-  for (int comp = 0; comp < D; ++comp) u[comp] = acc_result(outer[comp]);
+// The evaluation itself uses the per-cell monomial form about the cell
+// centre (built from the nodal values when the field is set):
+//   u_c(s) = sum_{p,q,r} C_pqr s0^p s1^q s2^r,   s = t - 1/2,
+// evaluated by nested Horner steps, 26 per component in 3D (8 in 2D),
+// each a double-float multiply-add.  For smooth fields |C_pqr| falls
+// with p + q + r (C_000 is the centre node's value), so the evaluation is
+// well conditioned.
+
+// c + a s in double-float, the result left unnormalised (its low part may
+// exceed half an ulp of the high part slightly; the next step multiplies it
+// exactly through two_prod and an FMA).
+__device__ __forceinline__ df df_horner(df a, df s, df c) {
+  const df p = two_prod(a.hi, s.hi);
+  float e = __fmaf_rn(a.hi, s.lo, p.lo);
+  e = __fmaf_rn(a.lo, s.hi, e);
+  const df q = two_sum(p.hi, c.hi);
+  return df_make(q.hi, __fadd_rn(q.lo, __fadd_rn(e, c.lo)));
 }
 
-// FP32 basis and contraction (precision form): only the high parts.
+// s = t - 1/2 in double-float.
+__device__ __forceinline__ df centred(df t) {
+  const df d = two_sum(t.hi, -0.5f);
+  return fast_two_sum(d.hi, __fadd_rn(d.lo, t.lo));
+}
+
 template <int D>
-__device__ __forceinline__ void q2_eval_f32(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
-                                            df u[D]) {
-  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = __ldg(m.qbase + K);  // node (2i, 2j, 2k) of the cell
-  float L[D][3];
+__device__ __forceinline__ void q2_eval_df(const MeshView& m, const float4* __restrict__ Qc, uint32_t K, const df t[D],
+                                           df u[D]) {
+  constexpr int NS = (D == 3 ? 3 : 1);
+  df s[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) lagrange2<float>(t[a].hi, L[a]);
-  float out[D];
+  for (int a = 0; a < D; ++a) s[a] = centred(t[a]);
+  const float4* cell = Qc + (size_t)K * D * (5 * NS);
+#pragma unroll 1
+  for (int comp = 0; comp < D; ++comp) {
+    const float4* cq = cell + comp * (5 * NS);
+    df g[NS];
 #pragma unroll
-  for (int comp = 0; comp < D; ++comp) out[comp] = 0.f;
+    for (int r = 0; r < NS; ++r) {
+      float4 v[5];
 #pragma unroll
-  for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
-    float mid[D];
+      for (int k = 0; k < 5; ++k) v[k] = __ldg(cq + 5 * r + k);
+      df c[10];
 #pragma unroll
-    for (int comp = 0; comp < D; ++comp) mid[comp] = 0.f;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D;
-#pragma unroll
-      for (int comp = 0; comp < D; ++comp) {
-        const float s = fmaf(L[0][2], __ldg(row + 2 * D + comp).x,
-                             fmaf(L[0][1], __ldg(row + D + comp).x, L[0][0] * __ldg(row + comp).x));
-        mid[comp] = fmaf(L[1][b], s, mid[comp]);
+      for (int k = 0; k < 5; ++k) {
+        c[2 * k] = df_make(v[k].x, v[k].y);
+        c[2 * k + 1] = df_make(v[k].z, v[k].w);
       }
+      df h[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) h[q] = df_horner(df_horner(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
+      g[r] = df_horner(df_horner(h[2], s[1], h[1]), s[1], h[0]);
     }
-#pragma unroll
-    for (int comp = 0; comp < D; ++comp) out[comp] = (D == 3) ? fmaf(L[D - 1][cz], mid[comp], out[comp]) : mid[comp];
+    if constexpr (D == 3)
+      u[comp] = df_norm(df_horner(df_horner(g[2], s[2], g[1]), s[2], g[0]));
+    else
+      u[comp] = df_norm(g[0]);
   }
+}
+
+// FP32 basis and contraction (precision form): the same monomial form on
+// the high parts, FP32 Horner steps.
+template <int D>
+__device__ __forceinline__ void q2_eval_f32(const MeshView& m, const float4* __restrict__ Qc, uint32_t K, const df t[D],
+                                            df u[D]) {
+  constexpr int NS = (D == 3 ? 3 : 1);
+  float s[D];
 #pragma unroll
-  for (int comp = 0; comp < D; ++comp) u[comp] = df_make(out[comp], 0.f);
+  for (int a = 0; a < D; ++a) s[a] = t[a].hi - 0.5f;
+  const float4* cell = Qc + (size_t)K * D * (5 * NS);
+#pragma unroll
+  for (int comp = 0; comp < D; ++comp) {
+    const float4* cq = cell + comp * (5 * NS);
+    float g[NS];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      float c[10];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const float4 v = __ldg(cq + 5 * r + k);
+        c[2 * k] = v.x;
+        c[2 * k + 1] = v.z;
+      }
+      float h[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) h[q] = fmaf(fmaf(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
+      g[r] = fmaf(fmaf(h[2], s[1], h[1]), s[1], h[0]);
+    }
+    u[comp] = df_make((D == 3) ? fmaf(fmaf(g[2], s[2], g[1]), s[2], g[0]) : g[0], 0.f);
+  }
 }
 
 }  // namespace pic

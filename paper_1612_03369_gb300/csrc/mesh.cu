@@ -92,6 +92,78 @@ __global__ void to_df_nodes_kernel(const double* __restrict__ U, float2* __restr
   }
 }
 
+// Per-cell monomial coefficients of the Q2 field about the cell centre:
+// with s = t - 1/2 the 1D Lagrange basis on {0, 1/2, 1} is
+//   l_0 = -s + 2 s^2,   l_1 = 1 - 4 s^2,   l_2 = s + 2 s^2,
+// i.e. l_a(s) = sum_p T[p][a] s^p with T = [[0, 1, 0], [-1, 0, 1], [2, -4, 2]],
+// so u_c(s) = sum_{p,q,r} C_pqr s0^p s1^q s2^r with C = (T x T x T) U_cell.
+// Computed in FP64 one axis at a time (products by 0, +-1, 2, -4 are exact;
+// each output rounds once or twice), stored as double-float pairs:
+// per cell and component, slice r (3 in 3D, 1 in 2D) holds C[r][q][p] at
+// pair q*3 + p of 5 float4 (the tenth pair is zero).
+__device__ __forceinline__ void t_axis(double v0, double v1, double v2, double& c0, double& c1, double& c2) {
+  c0 = v1;
+  c1 = v2 - v0;
+  c2 = 2.0 * (v0 + v2) - 4.0 * v1;
+}
+
+template <int D>
+__global__ void q2_coeff_kernel(MeshView m, const double* __restrict__ U, float4* __restrict__ Qc) {
+  constexpr int NS = (D == 3 ? 3 : 1);
+  const size_t total = (size_t)m.C * D;
+  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t K = (uint32_t)(idx / D);
+    const int comp = (int)(idx % D);
+    int c[3];
+    cell_ijk<D>(m, K, c);
+    const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+    const double* Uc = U + (int64_t)comp * m.nnodes + base;
+    double V[3][3][3];  // [r (z)][q (y)][p (x)]
+#pragma unroll
+    for (int r = 0; r < NS; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double* row = Uc + q * sy + (D == 3 ? r * sz : 0);
+        t_axis(row[0], row[1], row[2], V[r][q][0], V[r][q][1], V[r][q][2]);
+      }
+#pragma unroll
+    for (int r = 0; r < NS; ++r)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) t_axis(V[r][0][p], V[r][1][p], V[r][2][p], V[r][0][p], V[r][1][p], V[r][2][p]);
+    if constexpr (D == 3) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) t_axis(V[0][q][p], V[1][q][p], V[2][q][p], V[0][q][p], V[1][q][p], V[2][q][p]);
+    }
+    float4* out = Qc + ((size_t)K * D + comp) * (5 * NS);
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      float2 pr[10];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) pr[e] = split_df(V[r][e / 3][e % 3]);
+      pr[9] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) out[5 * r + k] = make_float4(pr[2 * k].x, pr[2 * k].y, pr[2 * k + 1].x, pr[2 * k + 1].y);
+    }
+  }
+}
+
+// Coefficients of one field (U FP64 on the device) into Qc.
+static void build_coefficients(const pic_mesh_s* m, const double* U, float4* Qc, cudaStream_t st) {
+  MeshView v = mesh_view(m);
+  const size_t total = (size_t)m->C * m->dim;
+  const int g = (int)((total + 127) / 128 < 4096 ? (total + 127) / 128 : 4096);
+  if (m->dim == 2)
+    q2_coeff_kernel<2><<<g, 128, 0, st>>>(v, U, Qc);
+  else
+    q2_coeff_kernel<3><<<g, 128, 0, st>>>(v, U, Qc);
+  count_launches(1);
+}
+
+static size_t coeff_float4s(const pic_mesh_s* m) { return (size_t)m->C * m->dim * (m->dim == 3 ? 15 : 5); }
+
 __global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -202,6 +274,8 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->Un);
   cudaFree(m->U32n);
   cudaFree(m->U2n);
+  cudaFree(m->Qc);
+  cudaFree(m->Qcn);
   free(m);
   return PIC_OK;
 }
@@ -212,14 +286,16 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   const size_t n = (size_t)m->dim * (size_t)m->nnodes;
   if (!m->U) {
     if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&m->U2, sizeof(float2) * n) != cudaSuccess) {
+        cudaMalloc(&m->U2, sizeof(float2) * n) != cudaSuccess ||
+        cudaMalloc(&m->Qc, sizeof(float4) * coeff_float4s(m)) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
   if (U_next && !m->Un) {
     if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32n, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&m->U2n, sizeof(float2) * n) != cudaSuccess) {
+        cudaMalloc(&m->U2n, sizeof(float2) * n) != cudaSuccess ||
+        cudaMalloc(&m->Qcn, sizeof(float4) * coeff_float4s(m)) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
@@ -228,10 +304,12 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
   to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
   to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  build_coefficients(m, m->U, m->Qc, st);
   if (U_next) {
     PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
     to_f32_kernel<<<g, 256, 0, st>>>(m->Un, m->U32n, n);
     to_df_nodes_kernel<<<g, 256, 0, st>>>(m->Un, m->U2n, m->dim, (size_t)m->nnodes);
+    build_coefficients(m, m->Un, m->Qcn, st);
   }
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
@@ -279,6 +357,7 @@ extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
   const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
   to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  build_coefficients(m, m->U, m->Qc, st);
   count_launches(2);
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaEventRecord(m->ev_free, st));

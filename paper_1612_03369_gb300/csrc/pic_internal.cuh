@@ -67,6 +67,8 @@ struct pic_mesh_s {
   double* Un;    // the same three copies of the field at the end of the step
   float* U32n;   // (time interpolation), allocated when a second field is set
   float2* U2n;
+  float4* Qc;    // [C][dim][slices][5] per-cell monomial coefficients (double-float pairs, see fastpath.cuh)
+  float4* Qcn;   // the same for the field at the end of the step
   int has_next;
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
@@ -136,6 +138,8 @@ struct MeshView {
   const uint32_t* qbase;
   const float2* U2;
   const float2* U2n;  // field at the end of the step, when has_next
+  const float4* Qc;   // per-cell monomial coefficients of the field (and of the second field)
+  const float4* Qcn;
   int has_next;
   double dlo[3], dhi[3];
 };
@@ -160,6 +164,8 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.qbase = m->qbase;
   v.U2 = m->U2;
   v.U2n = m->U2n;
+  v.Qc = m->Qc;
+  v.Qcn = m->Qcn;
   v.has_next = m->has_next;
   return v;
 }
@@ -341,52 +347,6 @@ __device__ __forceinline__ bool in_ref_cell(const double t[D]) {
 #pragma unroll
   for (int a = 0; a < D; ++a) in = in && (t[a] >= -kInsideEps) && (t[a] <= 1.0 + kInsideEps);
   return in;
-}
-
-// --------------------------------------------------------- Q2 velocity --
-// u_h(x) = sum_{a,b,c} U[node(K; a,b,c)] l_a(t0) l_b(t1) l_c(t2), with the 1D
-// quadratic Lagrange basis on {0, 1/2, 1}:
-//   l0 = (1-t)(1-2t), l1 = 4t(1-t), l2 = t(2t-1)
-// contracted one axis at a time (sum factorisation).
-
-template <typename T>
-__device__ __forceinline__ void lagrange2(T t, T l[3]) {
-  const T one = (T)1, two = (T)2, four = (T)4;
-  l[0] = (one - t) * (one - two * t);
-  l[1] = four * t * (one - t);
-  l[2] = t * (two * t - one);
-}
-
-template <int D, typename T>
-__device__ __forceinline__ void q2_eval(const MeshView& m, const T* __restrict__ U, uint32_t K, const double tin[D],
-                                        double u[D]) {
-  int c[3];
-  cell_ijk<D>(m, K, c);
-  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
-  T l[D][3];
-#pragma unroll
-  for (int a = 0; a < D; ++a) lagrange2<T>((T)tin[a], l[a]);
-#pragma unroll
-  for (int comp = 0; comp < D; ++comp) {
-    const T* Uc = U + comp * m.nnodes + base;
-    T s = (T)0;
-#pragma unroll
-    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
-      T sc = (T)0;
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const T* row = Uc + b * sy + (D == 3 ? cz * sz : 0);
-        T sb = l[0][0] * __ldg(row) + l[0][1] * __ldg(row + 1) + l[0][2] * __ldg(row + 2);
-        sc += l[1][b] * sb;
-      }
-      if (D == 3)
-        s += l[2][cz] * sc;
-      else
-        s = sc;
-    }
-    u[comp] = (double)s;
-  }
 }
 
 }  // namespace pic
