@@ -119,7 +119,7 @@ struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x +
 // Resident blocks per SM requested from the register allocator (tuning knob,
 // swept at build time with -DPIC_ADVECT_MIN_BLOCKS=n).
 #ifndef PIC_ADVECT_MIN_BLOCKS
-#define PIC_ADVECT_MIN_BLOCKS 5
+#define PIC_ADVECT_MIN_BLOCKS 6
 #endif
 
 // Per-stage work riding on the position integration: hook.stage(p, K, t) is

@@ -113,8 +113,10 @@ __global__ void q2_coeff_kernel(MeshView m, const double* __restrict__ U, float4
   const size_t total = (size_t)m.C * D;
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t K = (uint32_t)(idx / D);
-    const int comp = (int)(idx % D);
+    // neighbouring threads take neighbouring cells of one component, so a
+    // warp's node reads fall on a few rows of the nodal array
+    const uint32_t K = (uint32_t)(idx % m.C);
+    const int comp = (int)(idx / m.C);
     int c[3];
     cell_ijk<D>(m, K, c);
     const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
@@ -164,10 +166,6 @@ static void build_coefficients(const pic_mesh_s* m, const double* U, float4* Qc,
 
 static size_t coeff_float4s(const pic_mesh_s* m) { return (size_t)m->C * m->dim * (m->dim == 3 ? 15 : 5); }
 
-__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
-}
 
 }  // namespace pic
 
@@ -266,14 +264,11 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   if (m->ev_free) cudaEventDestroy(m->ev_free);
   cudaFree(m->X);
   cudaFree(m->U);
-  cudaFree(m->U32);
   cudaFree(m->bbox);
   cudaFree(m->blk);
   cudaFree(m->qbase);
   cudaFree(m->U2);
   cudaFree(m->Un);
-  cudaFree(m->U32n);
-  cudaFree(m->U2n);
   cudaFree(m->Qc);
   cudaFree(m->Qcn);
   free(m);
@@ -285,30 +280,24 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = (size_t)m->dim * (size_t)m->nnodes;
   if (!m->U) {
-    if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&m->U2, sizeof(float2) * n) != cudaSuccess ||
+    if (cudaMalloc(&m->U, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U2, sizeof(float2) * n) != cudaSuccess ||
         cudaMalloc(&m->Qc, sizeof(float4) * coeff_float4s(m)) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
   if (U_next && !m->Un) {
-    if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U32n, sizeof(float) * n) != cudaSuccess ||
-        cudaMalloc(&m->U2n, sizeof(float2) * n) != cudaSuccess ||
+    if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess ||
         cudaMalloc(&m->Qcn, sizeof(float4) * coeff_float4s(m)) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
-  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
-  to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
-  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  m->u2_valid = 0;
   build_coefficients(m, m->U, m->Qc, st);
   if (U_next) {
     PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
-    to_f32_kernel<<<g, 256, 0, st>>>(m->Un, m->U32n, n);
-    to_df_nodes_kernel<<<g, 256, 0, st>>>(m->Un, m->U2n, m->dim, (size_t)m->nnodes);
     build_coefficients(m, m->Un, m->Qcn, st);
   }
   PIC_CUDA(cudaGetLastError());
@@ -354,14 +343,26 @@ extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
   double* t = m->U;
   m->U = m->Ustage;
   m->Ustage = t;
-  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  to_f32_kernel<<<g, 256, 0, st>>>(m->U, m->U32, n);
-  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  m->u2_valid = 0;
   build_coefficients(m, m->U, m->Qc, st);
-  count_launches(2);
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaEventRecord(m->ev_free, st));
   m->free_recorded = 1;
   m->staged = 0;
   return PIC_OK;
 }
+
+namespace pic {
+
+pic_status ensure_nodal_df(pic_mesh_s* m, cudaStream_t st) {
+  if (m->u2_valid) return PIC_OK;
+  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
+  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
+  count_launches(1);
+  PIC_CUDA(cudaGetLastError());
+  m->u2_valid = 1;
+  return PIC_OK;
+}
+
+}  // namespace pic

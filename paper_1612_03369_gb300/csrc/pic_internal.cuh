@@ -59,14 +59,12 @@ struct pic_mesh_s {
   int64_t nverts, nnodes;
   double* X;     // [dim][nverts]
   double* U;     // [dim][nnodes]
-  float* U32;    // [dim][nnodes] FP32 copy for the FP32-basis form
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
   uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
-  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo)
-  double* Un;    // the same three copies of the field at the end of the step
-  float* U32n;   // (time interpolation), allocated when a second field is set
-  float2* U2n;
+  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo), for the gradient; built on demand
+  int u2_valid;  // U2 holds the current field
+  double* Un;    // the field at the end of the step (time interpolation), when set
   float4* Qc;    // [C][dim][slices][5] per-cell monomial coefficients (double-float pairs, see fastpath.cuh)
   float4* Qcn;   // the same for the field at the end of the step
   int has_next;
@@ -132,12 +130,10 @@ struct MeshView {
   int64_t nverts, nnodes;
   const double* X;
   const double* U;
-  const float* U32;
   const double* bbox;
   const float4* blk;
   const uint32_t* qbase;
   const float2* U2;
-  const float2* U2n;  // field at the end of the step, when has_next
   const float4* Qc;   // per-cell monomial coefficients of the field (and of the second field)
   const float4* Qcn;
   int has_next;
@@ -158,12 +154,10 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.nnodes = m->nnodes;
   v.X = m->X;
   v.U = m->U;
-  v.U32 = m->U32;
   v.bbox = m->bbox;
   v.blk = m->blk;
   v.qbase = m->qbase;
   v.U2 = m->U2;
-  v.U2n = m->U2n;
   v.Qc = m->Qc;
   v.Qcn = m->Qcn;
   v.has_next = m->has_next;
@@ -356,6 +350,9 @@ namespace pic {
 // Rebuild the sorted store from the cells found by the last locate
 // (cell_new, counts already filled).  Defined in rebin.cu.
 pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s);
+// Build the nodal double-float copy U2 of the current field if it is stale
+// (mesh.cu); the callers that evaluate velocity gradients call it first.
+pic_status ensure_nodal_df(pic_mesh_s* m, cudaStream_t st);
 // Counting, cell offsets and store allocation shared by the generators
 // (particles.cu); the store's buffer 0 is then filled by the caller.
 pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,

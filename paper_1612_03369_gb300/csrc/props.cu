@@ -239,6 +239,10 @@ extern "C" pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, 
       return (set_error("pic_advect_properties: cannot allocate %zu bytes of stage records", bytes), PIC_ERR_OOM);
     }
   }
+  {
+    pic_status r = ensure_nodal_df(mesh, st);
+    if (r != PIC_OK) return r;
+  }
   const StageRec rec = {(uint32_t*)parts->stage_rec,
                         (float2*)((char*)parts->stage_rec + (size_t)4 * parts->capacity * sizeof(uint32_t)),
                         parts->capacity};
