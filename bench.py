@@ -78,12 +78,15 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def workload(name: str):
+def workload(name: str, n: int | None = None):
+    """The named workload; n overrides the cells per axis (for profiling a
+    kernel at a size ncu can capture), and the result is then no bench line
+    of the named configuration."""
     if name == "c1":
-        return W.c1()
+        return W.c1() if n is None else W.c1(n=n)
     if name == "c3":
-        return W.c3()
-    return W.c2()
+        return W.c3() if n is None else W.c3(n=n)
+    return W.c2() if n is None else W.c2(n=n)
 
 
 class ClockSampler:
@@ -141,7 +144,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    wl = workload(args.config)
+    wl = workload(args.config, args.mesh)
     precision = P.PIC_FP32_BASIS if args.config == "c3" else P.PIC_FP64
     mesh = P.Mesh(wl.n, wl.X, wl.U)
     parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
@@ -749,6 +752,8 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2p", "next"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", type=int, default=None,
+                    help="cells per axis instead of the configuration's (profiling only: not that configuration)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

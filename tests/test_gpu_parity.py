@@ -220,10 +220,15 @@ def test_geometric_harmonic_averages(P, oracle_mod, kind):
     parts.set_property(0, pos)
     parts.set_property(1, (st["x"][2] - 0.5).contiguous())  # changes sign
     parts.advect(wl.dt, 4, 2)
-    g = H.gpu_state(parts)
+    # the oracle's own run on the same seeded inputs
+    om, op = H.oracle_seed(oracle_mod, wl)
+    op.props[:, 0] = 1.0 + op.x[:, 0] + op.x[:, 1]
+    op.props[:, 1] = op.x[:, 2] - 0.5
+    op = oracle_mod.advect(om, op, wl.dt, 4, 2)
+    np.testing.assert_array_equal(H.gpu_state(parts)["cell"], op.cell)
     for prop in (0, 1):
         ga, gc = parts.average(prop, empty_fill=-9.0, kind=kind)
-        oa, oc = oracle_mod.cell_average(wl.ncells, g["cell"], g["props"][:, prop], empty_fill=-9.0, kind=kind)
+        oa, oc = oracle_mod.cell_average(wl.ncells, op.cell, op.props[:, prop], empty_fill=-9.0, kind=kind)
         ga = ga.cpu().numpy()
         np.testing.assert_array_equal(gc.cpu().numpy().astype(np.int64), oc)
         np.testing.assert_array_equal(np.isnan(ga), np.isnan(oa))
