@@ -63,8 +63,8 @@ def advect_bytes(dim: int, ppc: float, xhat_bytes: int = 8) -> float:
 # (current advect kernel, 64^3 workload, RK4, FP64 form, steady field): FP32
 # flops executed per particle-step (FFMA counted as 2) and DRAM bytes per
 # particle per launch.  They describe that kernel on that workload only.
-ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 8832.2
-ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 922.04e6 / 5242880
+ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 9074.8
+ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 968.99e6 / 5242880
 # FP32 peak derived from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

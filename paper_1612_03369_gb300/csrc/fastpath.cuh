@@ -65,21 +65,22 @@ __device__ __forceinline__ void load_block(const MeshView& m, uint32_t K, CellBl
 template <int D>
 __device__ __forceinline__ void map32(const CellBlock<D>& cb, const float t[D], float phi[D], float J[D][D]) {
   if constexpr (D == 2) {
-    const float t01 = t[0] * t[1];
+    const float t01 = __fmul_rn(t[0], t[1]);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi;
-      phi[c] = fmaf(a3, t01, fmaf(a2, t[1], a1 * t[0]));
+      phi[c] = fmaf(a3, t01, fmaf(a2, t[1], __fmul_rn(a1, t[0])));
       J[c][0] = fmaf(a3, t[1], a1);
       J[c][1] = fmaf(a3, t[0], a2);
     }
   } else {
-    const float t01 = t[0] * t[1], t02 = t[0] * t[2], t12 = t[1] * t[2], t012 = t01 * t[2];
+    const float t01 = __fmul_rn(t[0], t[1]), t02 = __fmul_rn(t[0], t[2]), t12 = __fmul_rn(t[1], t[2]);
+    const float t012 = __fmul_rn(t01, t[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi, a4 = cb.a[3][c].hi;
       const float a5 = cb.a[4][c].hi, a6 = cb.a[5][c].hi, a7 = cb.a[6][c].hi;
-      phi[c] = fmaf(a7, t012, fmaf(a6, t12, fmaf(a5, t02, fmaf(a4, t01, fmaf(a3, t[2], fmaf(a2, t[1], a1 * t[0]))))));
+      phi[c] = fmaf(a7, t012, fmaf(a6, t12, fmaf(a5, t02, fmaf(a4, t01, fmaf(a3, t[2], fmaf(a2, t[1], __fmul_rn(a1, t[0])))))));
       J[c][0] = fmaf(a7, t12, fmaf(a5, t[2], fmaf(a4, t[1], a1)));
       J[c][1] = fmaf(a7, t02, fmaf(a6, t[2], fmaf(a4, t[0], a2)));
       J[c][2] = fmaf(a7, t01, fmaf(a6, t[1], fmaf(a5, t[0], a3)));
@@ -89,29 +90,34 @@ __device__ __forceinline__ void map32(const CellBlock<D>& cb, const float t[D], 
 
 template <int D>
 __device__ __forceinline__ bool solve32(const float J[D][D], const float r[D], float d[D]) {
+  // Every operation is an explicit rounded intrinsic, in a fixed order, so
+  // that every kernel inlining this (the advect kernel's template instances,
+  // the stage-recording kernel, the adjoint's stage kernel) computes the same
+  // iterates bit for bit, whatever the compiler would contract on its own.
+  auto det2 = [](float a, float b, float c, float e) { return __fmaf_rn(a, b, -__fmul_rn(c, e)); };  // a b - c e
   if constexpr (D == 2) {
-    const float det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const float det = det2(J[0][0], J[1][1], J[0][1], J[1][0]);
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float inv = 1.0f / det;
-    d[0] = (J[1][1] * r[0] - J[0][1] * r[1]) * inv;
-    d[1] = (J[0][0] * r[1] - J[1][0] * r[0]) * inv;
+    const float inv = __fdiv_rn(1.0f, det);
+    d[0] = __fmul_rn(det2(J[1][1], r[0], J[0][1], r[1]), inv);
+    d[1] = __fmul_rn(det2(J[0][0], r[1], J[1][0], r[0]), inv);
     return true;
   } else {
-    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-    const float c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-    const float c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-    const float det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const float c00 = det2(J[1][1], J[2][2], J[1][2], J[2][1]);
+    const float c01 = det2(J[1][2], J[2][0], J[1][0], J[2][2]);
+    const float c02 = det2(J[1][0], J[2][1], J[1][1], J[2][0]);
+    const float det = __fmaf_rn(J[0][2], c02, __fmaf_rn(J[0][1], c01, __fmul_rn(J[0][0], c00)));
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float inv = 1.0f / det;
-    const float c10 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-    const float c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-    const float c12 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-    const float c20 = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-    const float c21 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-    const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-    d[0] = (c00 * r[0] + c10 * r[1] + c20 * r[2]) * inv;
-    d[1] = (c01 * r[0] + c11 * r[1] + c21 * r[2]) * inv;
-    d[2] = (c02 * r[0] + c12 * r[1] + c22 * r[2]) * inv;
+    const float inv = __fdiv_rn(1.0f, det);
+    const float c10 = det2(J[0][2], J[2][1], J[0][1], J[2][2]);
+    const float c11 = det2(J[0][0], J[2][2], J[0][2], J[2][0]);
+    const float c12 = det2(J[0][1], J[2][0], J[0][0], J[2][1]);
+    const float c20 = det2(J[0][1], J[1][2], J[0][2], J[1][1]);
+    const float c21 = det2(J[0][2], J[1][0], J[0][0], J[1][2]);
+    const float c22 = det2(J[0][0], J[1][1], J[0][1], J[1][0]);
+    d[0] = __fmul_rn(__fmaf_rn(c20, r[2], __fmaf_rn(c10, r[1], __fmul_rn(c00, r[0]))), inv);
+    d[1] = __fmul_rn(__fmaf_rn(c21, r[2], __fmaf_rn(c11, r[1], __fmul_rn(c01, r[0]))), inv);
+    d[2] = __fmul_rn(__fmaf_rn(c22, r[2], __fmaf_rn(c12, r[1], __fmul_rn(c02, r[0]))), inv);
     return true;
   }
 }
