@@ -5,6 +5,7 @@
 #include <cstring>
 #include <vector>
 
+#include "df.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -97,71 +98,93 @@ __global__ void to_df_nodes_kernel(const double* __restrict__ U, float2* __restr
 //   l_0 = -s + 2 s^2,   l_1 = 1 - 4 s^2,   l_2 = s + 2 s^2,
 // i.e. l_a(s) = sum_p T[p][a] s^p with T = [[0, 1, 0], [-1, 0, 1], [2, -4, 2]],
 // so u_c(s) = sum_{p,q,r} C_pqr s0^p s1^q s2^r with C = (T x T x T) U_cell.
-// Computed in FP64 one axis at a time (products by 0, +-1, 2, -4 are exact;
-// each output rounds once or twice), stored as double-float pairs:
+// Computed in double-float on the FP32 pipe from the nodal double-float copy
+// U2 (each node converted once), one axis at a time (scalings by 2 and 4 are
+// exact; sums and differences carry ~2^-47 of their operands, the order of
+// the storage rounding itself), stored as double-float pairs:
 // per cell and component, slice r (3 in 3D, 1 in 2D) holds C[r][q][p] at
 // pair q*3 + p of 5 float4 (the tenth pair is zero).
-__device__ __forceinline__ void t_axis(double v0, double v1, double v2, double& c0, double& c1, double& c2) {
+__device__ __forceinline__ void t_axis(df v0, df v1, df v2, df& c0, df& c1, df& c2) {
   c0 = v1;
-  c1 = v2 - v0;
-  c2 = 2.0 * (v0 + v2) - 4.0 * v1;
+  c1 = df_sub(v2, v0);
+  c2 = df_sub(df_scale2(df_add(v0, v2), 2.0f), df_scale2(v1, 4.0f));
 }
 
 template <int D>
-__global__ void q2_coeff_kernel(MeshView m, const double* __restrict__ U, float4* __restrict__ Qc) {
+__global__ void __launch_bounds__(32 * D) q2_coeff_kernel(MeshView m, const float2* __restrict__ U2,
+                                                          float4* __restrict__ Qc) {
+  // A block builds the coefficients of a group of 32 consecutive cells:
+  // thread (comp, lane) does cell K0 + lane, component comp (neighbouring
+  // lanes read neighbouring nodes of one component), leaves its 5 NS float4
+  // in shared memory, and the block then writes the group's output region,
+  // which is contiguous ([K][comp][5 NS]), with coalesced float4 stores.
   constexpr int NS = (D == 3 ? 3 : 1);
-  const size_t total = (size_t)m.C * D;
+  constexpr int PER = 5 * NS;  // float4 per (cell, component)
+  __shared__ float4 sh[32 * D * PER];
+  const int lane = threadIdx.x & 31, comp = threadIdx.x >> 5;
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    // neighbouring threads take neighbouring cells of one component, so a
-    // warp's node reads fall on a few rows of the nodal array
-    const uint32_t K = (uint32_t)(idx % m.C);
-    const int comp = (int)(idx / m.C);
-    int c[3];
-    cell_ijk<D>(m, K, c);
-    const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
-    const double* Uc = U + (int64_t)comp * m.nnodes + base;
-    double V[3][3][3];  // [r (z)][q (y)][p (x)]
+  for (uint32_t K0 = blockIdx.x * 32u; K0 < m.C; K0 += gridDim.x * 32u) {
+    const uint32_t K = K0 + lane;
+    if (K < m.C) {
+      int c[3];
+      cell_ijk<D>(m, K, c);
+      const int64_t base = 2 * (int64_t)c[0] + sy * 2 * c[1] + (D == 3 ? sz * 2 * c[2] : 0);
+      const float2* Uc = U2 + base * D + comp;  // node-major [node][comp]
+      df V[3][3][3];  // [r (z)][q (y)][p (x)]
 #pragma unroll
-    for (int r = 0; r < NS; ++r)
+      for (int r = 0; r < NS; ++r)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const double* row = Uc + q * sy + (D == 3 ? r * sz : 0);
-        t_axis(row[0], row[1], row[2], V[r][q][0], V[r][q][1], V[r][q][2]);
+        for (int q = 0; q < 3; ++q) {
+          const float2* row = Uc + (q * sy + (D == 3 ? r * sz : 0)) * D;
+          const float2 a = row[0], b = row[D], e = row[2 * D];
+          t_axis(df_make(a.x, a.y), df_make(b.x, b.y), df_make(e.x, e.y), V[r][q][0], V[r][q][1], V[r][q][2]);
+        }
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) t_axis(V[r][0][p], V[r][1][p], V[r][2][p], V[r][0][p], V[r][1][p], V[r][2][p]);
+      if constexpr (D == 3) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int p = 0; p < 3; ++p) t_axis(V[0][q][p], V[1][q][p], V[2][q][p], V[0][q][p], V[1][q][p], V[2][q][p]);
       }
+      float4* out = sh + (lane * D + comp) * PER;
 #pragma unroll
-    for (int r = 0; r < NS; ++r)
+      for (int r = 0; r < NS; ++r) {
+        df pr[10];
 #pragma unroll
-      for (int p = 0; p < 3; ++p) t_axis(V[r][0][p], V[r][1][p], V[r][2][p], V[r][0][p], V[r][1][p], V[r][2][p]);
-    if constexpr (D == 3) {
+        for (int e = 0; e < 9; ++e) pr[e] = V[r][e / 3][e % 3];
+        pr[9] = df_make(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int p = 0; p < 3; ++p) t_axis(V[0][q][p], V[1][q][p], V[2][q][p], V[0][q][p], V[1][q][p], V[2][q][p]);
+        for (int k = 0; k < 5; ++k)
+          out[5 * r + k] = make_float4(pr[2 * k].hi, pr[2 * k].lo, pr[2 * k + 1].hi, pr[2 * k + 1].lo);
+      }
     }
-    float4* out = Qc + ((size_t)K * D + comp) * (5 * NS);
-#pragma unroll
-    for (int r = 0; r < NS; ++r) {
-      float2 pr[10];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) pr[e] = split_df(V[r][e / 3][e % 3]);
-      pr[9] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) out[5 * r + k] = make_float4(pr[2 * k].x, pr[2 * k].y, pr[2 * k + 1].x, pr[2 * k + 1].y);
-    }
+    __syncthreads();
+    const uint32_t ncell = (m.C - K0) < 32u ? (m.C - K0) : 32u;
+    const uint32_t nf4 = ncell * D * PER;
+    float4* dst = Qc + (size_t)K0 * D * PER;
+    for (uint32_t q = threadIdx.x; q < nf4; q += blockDim.x) dst[q] = sh[q];
+    __syncthreads();
   }
 }
 
-// Coefficients of one field (U FP64 on the device) into Qc.
-static void build_coefficients(const pic_mesh_s* m, const double* U, float4* Qc, cudaStream_t st) {
+// Coefficients of one field into Qc: the FP64 values U are first split into
+// the node-major double-float copy U2 (one conversion per nodal value).
+static void build_coefficients(const pic_mesh_s* m, const double* U, float2* U2, float4* Qc, cudaStream_t st) {
+  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
+  const int gn = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  to_df_nodes_kernel<<<gn, 256, 0, st>>>(U, U2, m->dim, (size_t)m->nnodes);
   MeshView v = mesh_view(m);
-  const size_t total = (size_t)m->C * m->dim;
-  const int g = (int)((total + 127) / 128 < 4096 ? (total + 127) / 128 : 4096);
+  const size_t groups = ((size_t)m->C + 31) / 32;
+  const size_t cap = (size_t)num_sms() * 16;
+  const int g = (int)(groups < cap ? groups : cap);
   if (m->dim == 2)
-    q2_coeff_kernel<2><<<g, 128, 0, st>>>(v, U, Qc);
+    q2_coeff_kernel<2><<<g, 64, 0, st>>>(v, U2, Qc);
   else
-    q2_coeff_kernel<3><<<g, 128, 0, st>>>(v, U, Qc);
-  count_launches(1);
+    q2_coeff_kernel<3><<<g, 96, 0, st>>>(v, U2, Qc);
+  count_launches(2);
 }
 
 static size_t coeff_float4s(const pic_mesh_s* m) { return (size_t)m->C * m->dim * (m->dim == 3 ? 15 : 5); }
@@ -269,6 +292,7 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->qbase);
   cudaFree(m->U2);
   cudaFree(m->Un);
+  cudaFree(m->U2n);
   cudaFree(m->Qc);
   cudaFree(m->Qcn);
   free(m);
@@ -287,18 +311,18 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
     }
   }
   if (U_next && !m->Un) {
-    if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess ||
+    if (cudaMalloc(&m->Un, sizeof(double) * n) != cudaSuccess || cudaMalloc(&m->U2n, sizeof(float2) * n) != cudaSuccess ||
         cudaMalloc(&m->Qcn, sizeof(float4) * coeff_float4s(m)) != cudaSuccess) {
       cudaGetLastError();
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
-  m->u2_valid = 0;
-  build_coefficients(m, m->U, m->Qc, st);
+  build_coefficients(m, m->U, m->U2, m->Qc, st);
+  m->u2_valid = 1;
   if (U_next) {
     PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
-    build_coefficients(m, m->Un, m->Qcn, st);
+    build_coefficients(m, m->Un, m->U2n, m->Qcn, st);
   }
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
@@ -343,8 +367,8 @@ extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
   double* t = m->U;
   m->U = m->Ustage;
   m->Ustage = t;
-  m->u2_valid = 0;
-  build_coefficients(m, m->U, m->Qc, st);
+  build_coefficients(m, m->U, m->U2, m->Qc, st);
+  m->u2_valid = 1;
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaEventRecord(m->ev_free, st));
   m->free_recorded = 1;

@@ -62,9 +62,10 @@ struct pic_mesh_s {
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
   uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
-  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo), for the gradient; built on demand
+  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo): the coefficients' source, and the gradient's
   int u2_valid;  // U2 holds the current field
   double* Un;    // the field at the end of the step (time interpolation), when set
+  float2* U2n;   // its double-float nodal copy (the source of Qcn)
   float4* Qc;    // [C][dim][slices][5] per-cell monomial coefficients (double-float pairs, see fastpath.cuh)
   float4* Qcn;   // the same for the field at the end of the step
   int has_next;
