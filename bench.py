@@ -54,17 +54,19 @@ def step_bytes(dim: int, n_props: int, ppc: float, xhat_bytes: int = 8) -> float
     return 2 * state + 8 + cell_data
 
 
-def advect_bytes(dim: int, ppc: float, xhat_bytes: int = 8) -> float:
-    # reads x, x-hat, cell; writes x, x-hat, new cell; cell data amortised
-    return 2 * (dim * 8 + dim * xhat_bytes + 4) + ((2 ** dim) * dim * 8 + dim * 8) / ppc
+def advect_bytes(dim: int, ppc: float, n_props: int, xhat_bytes: int = 8) -> float:
+    # reads x, x-hat, cell; writes x, x-hat, new cell; cell data amortised;
+    # the step also carries the id and properties into the new order (the
+    # previous step's rebin order is applied on the way)
+    return 2 * (dim * 8 + dim * xhat_bytes + 4 + 8 + n_props * 8) + ((2 ** dim) * dim * 8 + dim * 8) / ppc
 
 
 # From the ncu capture summarised in profiles/advect_kernel_c2_64cubed.md
 # (current advect kernel, 64^3 workload, RK4, FP64 form, steady field): FP32
 # flops executed per particle-step (FFMA counted as 2) and DRAM bytes per
 # particle per launch.  They describe that kernel on that workload only.
-ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 9074.8
-ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 968.99e6 / 5242880
+ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 9074.6
+ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 1590.70e6 / 5242880
 # FP32 peak derived from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -270,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     hbm, peak_kind = load_peaks()
     ppc = float(wl.ppc)
     value = psteps_all / (tmax / 1e3)
-    adv_bytes = advect_bytes(wl.dim, ppc)
+    adv_bytes = advect_bytes(wl.dim, ppc, wl.n_props)
     adv_avg_ms = adv_ms / max(nsteps, 1)
     per_launch_particles = psteps / max(nsteps, 1)
     achieved = adv_bytes * per_launch_particles / (adv_avg_ms / 1e3) / 1e9

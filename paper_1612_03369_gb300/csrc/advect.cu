@@ -12,20 +12,40 @@
 namespace pic {
 
 template <int D, int RK, bool F32B, bool TWO>
-__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(MeshView m, StoreView s, df dt,
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(MeshView m, StoreView s, StoreView d,
+                                                                          const uint32_t* __restrict__ perm, df dt,
                                                                           uint32_t* __restrict__ cell_new,
                                                                           uint32_t* __restrict__ counts,
                                                                           DevCounters* __restrict__ ctr) {
+  // perm == nullptr: particle j of s advances in place (d is s).  Otherwise
+  // the previous step's reordering is applied on the way: slot j of d takes
+  // particle perm[j] of s (its cell is already in d.cell[j], written by the
+  // previous rebin), with its id and properties.
   const uint32_t n = ctr->n_alive;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t i = base + threadIdx.x;
+    const uint32_t j = base + threadIdx.x;
     int iters = 0;
     unsigned flags = 0, lost = 0, steps = 0;
-    if (i < n) {
+    if (j < n) {
       steps = 1;
-      const uint32_t Kn = advect_particle<D, RK, F32B, TWO>(m, s, i, s.cell[i], dt, iters, flags);
-      cell_new[i] = Kn;
+      uint32_t i = j, K;
+      if (perm) {
+        i = perm[j];
+        K = d.cell[j];
+        if (i >= s.cap) {
+          flags |= kFlagBounds;
+          K = PIC_LOST;
+          i = 0;
+        } else {
+          d.id[j] = s.id[i];
+          for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
+        }
+      } else {
+        K = s.cell[j];
+      }
+      const uint32_t Kn = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, iters, flags);
+      cell_new[j] = Kn;
       if (Kn != PIC_LOST)
         atomicAdd(counts + Kn, 1u);
       else
@@ -109,17 +129,23 @@ static int grid_for(size_t n, int block) {
   return (int)(g > 0 ? g : 1);
 }
 
+// One advect launch.  With `fused` the previous step's reordering (perm,
+// sorted cells in the other buffer) is applied on the way: the step reads
+// buffer cur and writes buffer 1 - cur, which becomes cur.
 template <int D, int RK, bool F32B>
-static void launch_advect(pic_particles_s* p, const MeshView& m, double dt, cudaStream_t st) {
+static void launch_advect(pic_particles_s* p, const MeshView& m, double dt, bool fused, cudaStream_t st) {
   const float hi = (float)dt;
   const df dtd = {hi, (float)(dt - (double)hi)};
+  const StoreView s = store_view(p, p->cur), d = fused ? store_view(p, 1 - p->cur) : s;
+  const uint32_t* perm = fused ? p->perm : nullptr;
   if (m.has_next)
-    advect_kernel<D, RK, F32B, true><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd,
-                                                                                 p->cell_new, p->counts, p->ctr);
+    advect_kernel<D, RK, F32B, true><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
+                                                                                 p->counts, p->ctr);
   else
-    advect_kernel<D, RK, F32B, false><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, store_view(p, p->cur), dtd,
-                                                                                  p->cell_new, p->counts, p->ctr);
+    advect_kernel<D, RK, F32B, false><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
+                                                                                  p->counts, p->ctr);
   count_launches(1);
+  if (fused) p->cur = 1 - p->cur;
 }
 
 // Three events per timed step (before advect, after advect, after rebin),
@@ -138,13 +164,13 @@ static cudaEvent_t* timing_slot(pic_particles_s* p) {
 }
 
 template <int D, bool F32B>
-static void launch_advect_rk(pic_particles_s* p, const MeshView& m, double dt, int rk, cudaStream_t st) {
+static void launch_advect_rk(pic_particles_s* p, const MeshView& m, double dt, int rk, bool fused, cudaStream_t st) {
   if (rk == 1)
-    launch_advect<D, 1, F32B>(p, m, dt, st);
+    launch_advect<D, 1, F32B>(p, m, dt, fused, st);
   else if (rk == 2)
-    launch_advect<D, 2, F32B>(p, m, dt, st);
+    launch_advect<D, 2, F32B>(p, m, dt, fused, st);
   else
-    launch_advect<D, 4, F32B>(p, m, dt, st);
+    launch_advect<D, 4, F32B>(p, m, dt, fused, st);
 }
 
 }  // namespace pic
@@ -164,6 +190,11 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
   if (!mesh->has_velocity) return (set_error("pic_advect: velocity not set"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
   const MeshView m = mesh_view(mesh);
+  // Each step's rebin computes the new order (perm, sorted cells); the
+  // particles themselves move with the next step's advect, which reads them
+  // through perm, and after the last step with one gather.  Every step thus
+  // reads and writes the particle state once instead of twice.
+  bool pending = false;
   for (int step = 0; step < n_steps; ++step) {
     PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
     cudaEvent_t* ev = parts->timing ? timing_slot(parts) : nullptr;
@@ -171,19 +202,25 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
     const bool f32 = precision == PIC_FP32_BASIS;
     if (mesh->dim == 2) {
       if (f32)
-        launch_advect_rk<2, true>(parts, m, dt, (int)integrator, st);
+        launch_advect_rk<2, true>(parts, m, dt, (int)integrator, pending, st);
       else
-        launch_advect_rk<2, false>(parts, m, dt, (int)integrator, st);
+        launch_advect_rk<2, false>(parts, m, dt, (int)integrator, pending, st);
     } else {
       if (f32)
-        launch_advect_rk<3, true>(parts, m, dt, (int)integrator, st);
+        launch_advect_rk<3, true>(parts, m, dt, (int)integrator, pending, st);
       else
-        launch_advect_rk<3, false>(parts, m, dt, (int)integrator, st);
+        launch_advect_rk<3, false>(parts, m, dt, (int)integrator, pending, st);
     }
     PIC_CUDA(cudaGetLastError());
     if (ev) PIC_CUDA(cudaEventRecord(ev[1], st));
-    pic_status r = rebin_from_counts(parts, st);
+    pic_status r = rebin_order_from_counts(parts, st);
     if (r != PIC_OK) return r;
+    pending = true;
+    if (step + 1 == n_steps) {
+      r = rebin_apply_order(parts, st);
+      if (r != PIC_OK) return r;
+      pending = false;
+    }
     if (ev) PIC_CUDA(cudaEventRecord(ev[2], st));
   }
   return PIC_OK;

@@ -135,9 +135,14 @@ struct NoHook {
 // TWO: the mesh carries a second field (time interpolation).
 // Writes the new x and x-hat in place when the particle survives and returns
 // its new cell, or PIC_LOST.
+// advect_particle_to reads particle i of store s and writes its new x and
+// x-hat to slot j of store d (the same slot of the same store for the
+// in-place step; another buffer when the step also applies the previous
+// step's reordering).
 template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>
-__device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const StoreView& s, uint32_t i, uint32_t K,
-                                                    df dt, int& iters, unsigned& flags, Hook&& hook = Hook()) {
+__device__ __forceinline__ uint32_t advect_particle_to(const MeshView& m, const StoreView& s, uint32_t i,
+                                                       const StoreView& d, uint32_t j, uint32_t K, df dt, int& iters,
+                                                       unsigned& flags, Hook&& hook = Hook()) {
   using TB = Tableau<RK>;
   const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);  // 1/6 = hi + lo
   if (K >= m.C) {
@@ -185,10 +190,16 @@ __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const Sto
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    s.x[a * s.cap + i] = (x[a] + (double)acc[a].hi) + (double)acc[a].lo;
-    s.xhat[a * s.cap + i] = make_float2(ts[a].hi, ts[a].lo);
+    d.x[a * d.cap + j] = (x[a] + (double)acc[a].hi) + (double)acc[a].lo;
+    d.xhat[a * d.cap + j] = make_float2(ts[a].hi, ts[a].lo);
   }
   return Ks;
+}
+
+template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>
+__device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const StoreView& s, uint32_t i, uint32_t K,
+                                                    df dt, int& iters, unsigned& flags, Hook&& hook = Hook()) {
+  return advect_particle_to<D, RK, F32B, TWO>(m, s, i, s, i, K, dt, iters, flags, static_cast<Hook&&>(hook));
 }
 
 }  // namespace pic

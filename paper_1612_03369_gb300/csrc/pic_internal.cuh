@@ -351,6 +351,10 @@ namespace pic {
 // Rebuild the sorted store from the cells found by the last locate
 // (cell_new, counts already filled).  Defined in rebin.cu.
 pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s);
+// The two halves of rebin_from_counts: the new order (perm, offsets, sorted
+// cells in the other buffer), then the gather that applies it.
+pic_status rebin_order_from_counts(pic_particles_s* p, cudaStream_t s);
+pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s);
 // Build the nodal double-float copy U2 of the current field if it is stale
 // (mesh.cu); the callers that evaluate velocity gradients call it first.
 pic_status ensure_nodal_df(pic_mesh_s* m, cudaStream_t st);

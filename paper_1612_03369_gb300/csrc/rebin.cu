@@ -98,7 +98,10 @@ static int grid_cap(size_t n, int block, int per_sm) {
   return (int)(g ? g : 1);
 }
 
-pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
+// The new order of the store after a step: cell offsets, perm (new slot ->
+// old slot) and the sorted cells written into the other buffer; n_alive
+// becomes the survivors' count.  The particles have not moved yet.
+pic_status rebin_order_from_counts(pic_particles_s* p, cudaStream_t s) {
   pic_status r = scan_u32(p->counts, p->cell_off, p->C, p->block_sums, &p->ctr->n_next, p->cursor, s);
   if (r != PIC_OK) return r;
   const StoreView a = store_view(p, p->cur), b = store_view(p, 1 - p->cur);
@@ -107,11 +110,25 @@ pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
   rank_by_id_kernel<<<grid_cap((size_t)p->C * 32, 256, 16), 256, 0, s>>>(p->cell_off, p->key_id, p->key_src, p->perm,
                                                                         b.cell, p->C, p->capacity, &p->ctr->status,
                                                                         &p->ctr->n_alive, &p->ctr->n_next);
+  count_launches(2);
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
+
+// Move the particles into the order rebin_order_from_counts computed.
+pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s) {
+  const StoreView a = store_view(p, p->cur), b = store_view(p, 1 - p->cur);
   gather_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(a, b, p->perm, p->dim, p->ctr);
-  count_launches(3);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   p->cur = 1 - p->cur;
   return PIC_OK;
+}
+
+pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
+  pic_status r = rebin_order_from_counts(p, s);
+  if (r != PIC_OK) return r;
+  return rebin_apply_order(p, s);
 }
 
 // cell_new = cell, counts = histogram of cell (the identity relocation).
