@@ -452,15 +452,18 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, const float4* __re
     df g[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
-      float4 v[5];
-#pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] = __ldg(cq + 5 * r + k);
-      df c[10];
+      float f[20];  // ten high parts, then ten low parts
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        c[2 * k] = df_make(v[k].x, v[k].y);
-        c[2 * k + 1] = df_make(v[k].z, v[k].w);
+        const float4 v = __ldg(cq + 5 * r + k);
+        f[4 * k] = v.x;
+        f[4 * k + 1] = v.y;
+        f[4 * k + 2] = v.z;
+        f[4 * k + 3] = v.w;
       }
+      df c[10];
+#pragma unroll
+      for (int e = 0; e < 10; ++e) c[e] = df_make(f[e], f[10 + e]);
       df h[3];
 #pragma unroll
       for (int q = 0; q < 3; ++q) h[q] = df_horner(df_horner(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
@@ -489,12 +492,14 @@ __device__ __forceinline__ void q2_eval_f32(const MeshView& m, const float4* __r
     float g[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
-      float c[10];
+      float c[12];  // the high parts lead the slice: three float4
 #pragma unroll
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < 3; ++k) {
         const float4 v = __ldg(cq + 5 * r + k);
-        c[2 * k] = v.x;
-        c[2 * k + 1] = v.z;
+        c[4 * k] = v.x;
+        c[4 * k + 1] = v.y;
+        c[4 * k + 2] = v.z;
+        c[4 * k + 3] = v.w;
       }
       float h[3];
 #pragma unroll

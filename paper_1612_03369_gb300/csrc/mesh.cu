@@ -98,6 +98,9 @@ __global__ void to_df_nodes_kernel(const double* __restrict__ U, float2* __restr
 //   l_0 = -s + 2 s^2,   l_1 = 1 - 4 s^2,   l_2 = s + 2 s^2,
 // i.e. l_a(s) = sum_p T[p][a] s^p with T = [[0, 1, 0], [-1, 0, 1], [2, -4, 2]],
 // so u_c(s) = sum_{p,q,r} C_pqr s0^p s1^q s2^r with C = (T x T x T) U_cell.
+// Each slice of 5 float4 holds the high parts of C[r][q][p] at q*3 + p
+// (the tenth is zero) and then the ten low parts, so that the FP32 form
+// reads only the first three float4.
 // Computed in double-float on the FP32 pipe from the nodal double-float copy
 // U2 (each node converted once), one axis at a time (scalings by 2 and 4 are
 // exact; sums and differences carry ~2^-47 of their operands, the order of
@@ -156,9 +159,14 @@ __global__ void __launch_bounds__(32 * D) q2_coeff_kernel(MeshView m, const floa
 #pragma unroll
         for (int e = 0; e < 9; ++e) pr[e] = V[r][e / 3][e % 3];
         pr[9] = df_make(0.f, 0.f);
+        float f[20];  // the ten high parts, then the ten low parts
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
-          out[5 * r + k] = make_float4(pr[2 * k].hi, pr[2 * k].lo, pr[2 * k + 1].hi, pr[2 * k + 1].lo);
+        for (int e = 0; e < 10; ++e) {
+          f[e] = pr[e].hi;
+          f[10 + e] = pr[e].lo;
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) out[5 * r + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
       }
     }
     __syncthreads();
