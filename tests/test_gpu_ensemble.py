@@ -94,3 +94,20 @@ def test_autotuner_restores_state(P):
             np.testing.assert_array_equal(a[k], c[k])
     ens.run(4, 3, mode=1)
     _check_same(P, ens, wls, 5)
+
+
+def test_c5_full_size(P):
+    """The 64-member ensemble the benchmark runs (57M particles), 10 steps in
+    one persistent launch: every member's count is conserved, and three
+    members chosen across the size range equal their solo runs bit for bit."""
+    wls = W.c5()
+    ens, meshes = _ens(P, wls)
+    ens.run(4, wls[0].n_steps, mode=1)
+    sizes = [w.n[0] for w in wls]
+    for q in sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), len(wls) // 2}):
+        got = {k: v.cpu().numpy() for k, v in ens.export(q).items() if k != "props"}
+        solo = _solo(P, wls[q], wls[q].n_steps)
+        for k in ("id", "cell", "x", "xhat"):
+            np.testing.assert_array_equal(got[k], solo[k])
+    alive, lost = ens.state()[:2]
+    assert alive + lost == sum(w.n_particles for w in wls)
