@@ -116,21 +116,40 @@ __device__ __forceinline__ void load_ensemble(EnsShared& sh, const MeshView* vie
 }
 
 // One particle of the ensemble: its problem from the global cell, then the
-// single-mesh step, then back to a global cell.
+// single-mesh step, then back to a global cell.  With perm == nullptr slot j
+// of s advances in place (d is s); otherwise slot j of d takes particle
+// perm[j] of s, whose global cell the previous rebin left in d.cell[j], with
+// its id and properties (the previous step's order applied on the way).
 template <int D, int RK>
-__device__ __forceinline__ void ensemble_particle(const EnsShared& sh, int P, const StoreView& s, uint32_t i,
+__device__ __forceinline__ void ensemble_particle(const EnsShared& sh, int P, const StoreView& s, const StoreView& d,
+                                                  const uint32_t* __restrict__ perm, uint32_t j,
                                                   uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts,
                                                   int& iters, unsigned& flags, unsigned& lost) {
-  const uint32_t g = s.cell[i];
+  uint32_t i = j, g;
+  if (perm) {
+    i = perm[j];
+    g = d.cell[j];
+    if (i >= s.cap) {
+      flags |= kFlagBounds;
+      g = PIC_LOST;
+      i = 0;
+    } else {
+      d.id[j] = s.id[i];
+      for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
+    }
+  } else {
+    g = s.cell[j];
+  }
   uint32_t out = PIC_LOST;
   if (g < sh.base[P]) {
     const int p = problem_of(sh.base, P, g);
-    const uint32_t Kn = advect_particle<D, RK, false>(sh.views[p], s, i, g - sh.base[p], sh.dt[p], iters, flags);
+    const uint32_t Kn =
+        advect_particle_to<D, RK, false>(sh.views[p], s, i, d, j, g - sh.base[p], sh.dt[p], iters, flags);
     if (Kn != PIC_LOST) out = sh.base[p] + Kn;
   } else {
     flags |= kFlagBounds;
   }
-  cell_new[i] = out;
+  cell_new[j] = out;
   if (out != PIC_LOST)
     atomicAdd(counts + out, 1u);
   else
@@ -140,7 +159,8 @@ __device__ __forceinline__ void ensemble_particle(const EnsShared& sh, int P, co
 template <int D, int RK>
 __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_advect_kernel(
     const MeshView* __restrict__ views, const uint32_t* __restrict__ base, const df* __restrict__ dts, int P,
-    StoreView s, uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
+    StoreView s, StoreView d, const uint32_t* __restrict__ perm, uint32_t* __restrict__ cell_new,
+    uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
   __shared__ EnsShared sh;
   load_ensemble(sh, views, base, dts, P);
   const uint32_t n = ctr->n_alive;
@@ -150,7 +170,7 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_adv
     unsigned flags = 0, lost = 0, steps = 0;
     if (i < n) {
       steps = 1;
-      ensemble_particle<D, RK>(sh, P, s, i, cell_new, counts, iters, flags, lost);
+      ensemble_particle<D, RK>(sh, P, s, d, perm, i, cell_new, counts, iters, flags, lost);
     }
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
   }
@@ -183,12 +203,20 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_per
   const uint32_t gtid = bid * blockDim.x + threadIdx.x, gthreads = nb * blockDim.x;
   volatile uint32_t* n_alive = &A.ctr->n_alive;
   volatile uint32_t* n_next = &A.ctr->n_next;
+  // The particles of buffer curb stand in the order of the previous rebin
+  // (pending) or in the store's order; each step's advect applies the
+  // pending order on the way (reading curb, writing the other buffer), and
+  // one gather after the last step applies the last order.
+  int curb = A.start;
+  bool pending = false;
+  uint32_t nn = 0;
   for (int step = 0; step < A.n_steps; ++step) {
-    const StoreView& cur = A.sv[(A.start + step) & 1];
-    const StoreView& nxt = A.sv[(A.start + step + 1) & 1];
     for (uint32_t c = gtid; c < A.C; c += gthreads) A.counts[c] = 0u;
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
     const uint32_t n = *n_alive;
+    const StoreView& src = A.sv[curb];
+    const StoreView& dst = A.sv[pending ? 1 - curb : curb];
+    const uint32_t* perm = pending ? A.perm : nullptr;
     // advect: tiles of A.tile particles claimed dynamically
     for (;;) {
       if (threadIdx.x == 0) s_tile = atomicAdd(A.tile_ctr + step, 1u);
@@ -203,12 +231,15 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_per
         unsigned flags = 0, lost = 0, steps = 0;
         if (i < t1) {
           steps = 1;
-          ensemble_particle<D, RK>(sh, A.P, cur, i, A.cell_new, A.counts, iters, flags, lost);
+          ensemble_particle<D, RK>(sh, A.P, src, dst, perm, i, A.cell_new, A.counts, iters, flags, lost);
         }
         flush_counters(A.ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u,
                        flags);
       }
     }
+    if (pending) curb = 1 - curb;
+    const StoreView& cur = A.sv[curb];
+    const StoreView& nxt = A.sv[1 - curb];
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
     scan_phase_reduce(A.counts, A.C, A.tile_sums, bid, nb);
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
@@ -220,12 +251,15 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_per
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
     rank_phase(A.cell_off, A.key_id, A.key_src, A.perm, nxt.cell, A.C, A.cap, &A.ctr->status, gtid >> 5,
                gthreads >> 5);
-    if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    const uint32_t nn = *n_next;
-    gather_phase(cur, nxt, A.perm, A.dim, nn, &A.ctr->status, gtid, gthreads);
+    nn = *n_next;
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
     if (gtid == 0) *n_alive = nn;
     __threadfence();
+    pending = true;
+  }
+  if (pending) {
+    gather_phase(A.sv[curb], A.sv[1 - curb], A.perm, A.dim, nn, &A.ctr->status, gtid, gthreads);
+    if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
   }
 }
 
@@ -466,20 +500,29 @@ static pic_status enqueue_run(pic_ensemble_s* e, int integrator, int n_steps, in
       const int grid = (int)((s->capacity + kEnsBlock - 1) / kEnsBlock < (size_t)num_sms() * 16
                                  ? (s->capacity + kEnsBlock - 1) / kEnsBlock
                                  : (size_t)num_sms() * 16);
-      const StoreView sv = store_view(s, s->cur);
+      // as in pic_advect: each step applies the previous step's order on the
+      // way, and the last step's order is applied by one gather
+      const bool fused = step > 0;
+      const StoreView sv = store_view(s, s->cur), dv = fused ? store_view(s, 1 - s->cur) : sv;
+      const uint32_t* pm = fused ? s->perm : nullptr;
       if (e->dim == 2) {
-        if (rk == 1) ensemble_advect_kernel<2, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
-        else if (rk == 2) ensemble_advect_kernel<2, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
-        else ensemble_advect_kernel<2, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
+        if (rk == 1) ensemble_advect_kernel<2, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        else if (rk == 2) ensemble_advect_kernel<2, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        else ensemble_advect_kernel<2, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
       } else {
-        if (rk == 1) ensemble_advect_kernel<3, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
-        else if (rk == 2) ensemble_advect_kernel<3, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
-        else ensemble_advect_kernel<3, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, s->cell_new, s->counts, s->ctr);
+        if (rk == 1) ensemble_advect_kernel<3, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        else if (rk == 2) ensemble_advect_kernel<3, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        else ensemble_advect_kernel<3, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
       }
       count_launches(1);
       PIC_CUDA(cudaGetLastError());
-      pic_status r = rebin_from_counts(s, st);
+      if (fused) s->cur = 1 - s->cur;
+      pic_status r = rebin_order_from_counts(s, st);
       if (r != PIC_OK) return r;
+      if (step + 1 == n_steps) {
+        r = rebin_apply_order(s, st);
+        if (r != PIC_OK) return r;
+      }
     }
     return PIC_OK;
   }
