@@ -35,40 +35,68 @@ struct CellBlock {
   df a[(1 << D) - 1][D];
 };
 
+// The high parts alone (what the FP32 Newton iterations read).
+template <int D>
+struct CellBlock32 {
+  float x0[D];
+  float a[(1 << D) - 1][D];
+};
+
 template <int D>
 __host__ __device__ constexpr int block_float4s() {
   return (2 * D + 2 * D * ((1 << D) - 1)) / 4;  // 12 (3D) or 4 (2D)
 }
 
+// Block layout per cell: NF = D + (2^D - 1) D high parts (X_0, then a_k,c in
+// (k, c) order), then the NF low parts in the same order.
 template <int D>
-__device__ __forceinline__ void load_block(const MeshView& m, uint32_t K, CellBlock<D>& cb) {
-  constexpr int NF4 = block_float4s<D>();
-  const float4* p = m.blk + (size_t)K * NF4;
-  float f[4 * NF4];
+__device__ __forceinline__ void load_block_half(const MeshView& m, uint32_t K, int half, float f[]) {
+  constexpr int NH = block_float4s<D>() / 2;
+  const float4* p = m.blk + (size_t)K * block_float4s<D>() + half * NH;
 #pragma unroll
-  for (int q = 0; q < NF4; ++q) {
+  for (int q = 0; q < NH; ++q) {
     const float4 v = __ldg(p + q);
     f[4 * q] = v.x;
     f[4 * q + 1] = v.y;
     f[4 * q + 2] = v.z;
     f[4 * q + 3] = v.w;
   }
+}
+
+template <int D>
+__device__ __forceinline__ void load_block32(const MeshView& m, uint32_t K, CellBlock32<D>& cb) {
+  float f[2 * block_float4s<D>()];
+  load_block_half<D>(m, K, 0, f);
 #pragma unroll
-  for (int a = 0; a < D; ++a) cb.x0[a] = df_make(f[2 * a], f[2 * a + 1]);
+  for (int a = 0; a < D; ++a) cb.x0[a] = f[a];
 #pragma unroll
   for (int k = 0; k < (1 << D) - 1; ++k)
 #pragma unroll
-    for (int a = 0; a < D; ++a) cb.a[k][a] = df_make(f[2 * D + 2 * (k * D + a)], f[2 * D + 2 * (k * D + a) + 1]);
+    for (int a = 0; a < D; ++a) cb.a[k][a] = f[D + k * D + a];
+}
+
+template <int D>
+__device__ __forceinline__ void load_block(const MeshView& m, uint32_t K, CellBlock<D>& cb) {
+  constexpr int NF = 2 * block_float4s<D>();  // floats per half
+  float hi[NF], lo[NF];
+  load_block_half<D>(m, K, 0, hi);
+  load_block_half<D>(m, K, 1, lo);
+#pragma unroll
+  for (int a = 0; a < D; ++a) cb.x0[a] = df_make(hi[a], lo[a]);
+#pragma unroll
+  for (int k = 0; k < (1 << D) - 1; ++k)
+#pragma unroll
+    for (int a = 0; a < D; ++a) cb.a[k][a] = df_make(hi[D + k * D + a], lo[D + k * D + a]);
 }
 
 // FP32 map offset phi(t) = sum_k a_k m_k(t) and Jacobian, from the high parts.
 template <int D>
-__device__ __forceinline__ void map32(const CellBlock<D>& cb, const float t[D], float phi[D], float J[D][D]) {
+__device__ __forceinline__ void map32(const CellBlock32<D>& cb, const float t[D], float phi[D], float J[D][D]) {
   if constexpr (D == 2) {
     const float t01 = __fmul_rn(t[0], t[1]);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi;
+      const float a1 = cb.a[0][c], a2 = cb.a[1][c], a3 = cb.a[2][c];
       phi[c] = fmaf(a3, t01, fmaf(a2, t[1], __fmul_rn(a1, t[0])));
       J[c][0] = fmaf(a3, t[1], a1);
       J[c][1] = fmaf(a3, t[0], a2);
@@ -78,8 +106,8 @@ __device__ __forceinline__ void map32(const CellBlock<D>& cb, const float t[D], 
     const float t012 = __fmul_rn(t01, t[2]);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float a1 = cb.a[0][c].hi, a2 = cb.a[1][c].hi, a3 = cb.a[2][c].hi, a4 = cb.a[3][c].hi;
-      const float a5 = cb.a[4][c].hi, a6 = cb.a[5][c].hi, a7 = cb.a[6][c].hi;
+      const float a1 = cb.a[0][c], a2 = cb.a[1][c], a3 = cb.a[2][c], a4 = cb.a[3][c];
+      const float a5 = cb.a[4][c], a6 = cb.a[5][c], a7 = cb.a[6][c];
       phi[c] = fmaf(a7, t012, fmaf(a6, t12, fmaf(a5, t02, fmaf(a4, t01, fmaf(a3, t[2], fmaf(a2, t[1], __fmul_rn(a1, t[0])))))));
       J[c][0] = fmaf(a7, t12, fmaf(a5, t[2], fmaf(a4, t[1], a1)));
       J[c][1] = fmaf(a7, t02, fmaf(a6, t[2], fmaf(a4, t[0], a2)));
@@ -127,15 +155,17 @@ __device__ __forceinline__ df neg(df a) { return df_make(-a.hi, -a.lo); }
 // Double-float residual r = dloc - sum_k a_k m_k(t) at a single-float point t
 // (the monomials of t are formed exactly with two_prod).
 template <int D>
-__device__ __forceinline__ void residual_df(const CellBlock<D>& cb, const df dloc[D], const float t[D], float r[D]) {
+__device__ __forceinline__ void residual_df(const CellBlock32<D>& cb, const float lo[], const df dloc[D], const float t[D],
+                                            float r[D]) {
+  auto A = [&](int k, int c) { return df_make(-cb.a[k][c], -lo[D + k * D + c]); };
   const df m01 = two_prod(t[0], t[1]);
   if constexpr (D == 2) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       df_acc acc = acc_init(dloc[c]);
-      acc_mad_f(acc, neg(cb.a[0][c]), t[0]);
-      acc_mad_f(acc, neg(cb.a[1][c]), t[1]);
-      acc_mad(acc, neg(cb.a[2][c]), m01);
+      acc_mad_f(acc, A(0, c), t[0]);
+      acc_mad_f(acc, A(1, c), t[1]);
+      acc_mad(acc, A(2, c), m01);
       r[c] = __fadd_rn(acc.s, acc.e);
     }
   } else {
@@ -145,13 +175,13 @@ __device__ __forceinline__ void residual_df(const CellBlock<D>& cb, const df dlo
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       df_acc acc = acc_init(dloc[c]);
-      acc_mad_f(acc, neg(cb.a[0][c]), t[0]);
-      acc_mad_f(acc, neg(cb.a[1][c]), t[1]);
-      acc_mad_f(acc, neg(cb.a[2][c]), t[2]);
-      acc_mad(acc, neg(cb.a[3][c]), m01);
-      acc_mad(acc, neg(cb.a[4][c]), m02);
-      acc_mad(acc, neg(cb.a[5][c]), m12);
-      acc_mad(acc, neg(cb.a[6][c]), m012);
+      acc_mad_f(acc, A(0, c), t[0]);
+      acc_mad_f(acc, A(1, c), t[1]);
+      acc_mad_f(acc, A(2, c), t[2]);
+      acc_mad(acc, A(3, c), m01);
+      acc_mad(acc, A(4, c), m02);
+      acc_mad(acc, A(5, c), m12);
+      acc_mad(acc, A(6, c), m012);
       r[c] = __fadd_rn(acc.s, acc.e);
     }
   }
@@ -170,14 +200,19 @@ constexpr float kSettle32Tight = 1e-5f;
 template <int D>
 __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
                                              int& iters, bool accurate = true) {
-  CellBlock<D> cb;
-  load_block<D>(m, K, cb);
+  CellBlock32<D> cb;
+  load_block32<D>(m, K, cb);
   df dloc[D];
   float d32[D];
+  {
+    // X_0's low parts lead the block's second half
+    const float4 x0lo = __ldg(m.blk + (size_t)K * block_float4s<D>() + block_float4s<D>() / 2);
+    const float l[3] = {x0lo.x, x0lo.y, x0lo.z};
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    dloc[a] = df_sub(y[a], cb.x0[a]);
-    d32[a] = dloc[a].hi;
+    for (int a = 0; a < D; ++a) {
+      dloc[a] = df_sub(y[a], df_make(cb.x0[a], l[a]));
+      d32[a] = dloc[a].hi;
+    }
   }
   float phi[D], J[D][D], r[D], dt[D];
   bool settled = false;
@@ -224,7 +259,11 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
   // one Newton step with the double-float residual
   ++iters;
   map32<D>(cb, t32, phi, J);
-  residual_df<D>(cb, dloc, t32, r);
+  {
+    float lo[2 * block_float4s<D>()];
+    load_block_half<D>(m, K, 1, lo);
+    residual_df<D>(cb, lo, dloc, t32, r);
+  }
   if (!solve32<D>(J, r, dt)) return kCellFail;
   float mx = 0.f;
 #pragma unroll

@@ -46,15 +46,23 @@ __device__ __forceinline__ float2 split_df(double v) {
 //   a_t0 = e1, a_t1 = e2, a_t2 = e4, a_t0t1 = e3 - e1 - e2,
 //   a_t0t2 = e5 - e1 - e4, a_t1t2 = e6 - e2 - e4,
 //   a_t0t1t2 = e7 - e3 - e5 - e6 + e1 + e2 + e4.
+// Stored as the NF high parts (X_0, then a_k,c in (k, c) order) followed by
+// the NF low parts in the same order, so that the FP32 Newton iterations
+// read only the first half.
 template <int D>
-__global__ void cell_block_kernel(MeshView m, float2* __restrict__ blk) {
+__global__ void cell_block_kernel(MeshView m, float* __restrict__ blk) {
   constexpr int NK = (1 << D) - 1;
-  constexpr int NF2 = D + NK * D;
+  constexpr int NF = D + NK * D;
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
     CellGeom<D> g;
     load_cell<D>(m, K, g);
-    float2* out = blk + (size_t)K * NF2;
-    for (int a = 0; a < D; ++a) out[a] = split_df(g.x0[a]);
+    float* out = blk + (size_t)K * 2 * NF;
+    auto put = [&](int idx, double v) {
+      const float2 p = split_df(v);
+      out[idx] = p.x;
+      out[NF + idx] = p.y;
+    };
+    for (int a = 0; a < D; ++a) put(a, g.x0[a]);
     for (int a = 0; a < D; ++a) {
       double coef[NK];
       if constexpr (D == 2) {
@@ -70,7 +78,7 @@ __global__ void cell_block_kernel(MeshView m, float2* __restrict__ blk) {
         coef[5] = g.e[6][a] - g.e[2][a] - g.e[4][a];
         coef[6] = g.e[7][a] - g.e[3][a] - g.e[5][a] - g.e[6][a] + g.e[1][a] + g.e[2][a] + g.e[4][a];
       }
-      for (int k = 0; k < NK; ++k) out[D + k * D + a] = split_df(coef[k]);
+      for (int k = 0; k < NK; ++k) put(D + k * D + a, coef[k]);
     }
   }
 }
@@ -274,11 +282,11 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   const int grid = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   if (dim == 2) {
     cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox);
-    cell_block_kernel<2><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+    cell_block_kernel<2><<<grid, 256, 0, st>>>(mv, (float*)m->blk);
     cell_qbase_kernel<2><<<grid, 256, 0, st>>>(mv, m->qbase);
   } else {
     cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox);
-    cell_block_kernel<3><<<grid, 256, 0, st>>>(mv, (float2*)m->blk);
+    cell_block_kernel<3><<<grid, 256, 0, st>>>(mv, (float*)m->blk);
     cell_qbase_kernel<3><<<grid, 256, 0, st>>>(mv, m->qbase);
   }
   e = cudaGetLastError();
