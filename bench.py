@@ -461,8 +461,8 @@ def run_ensemble(args, rank=0, world=1, local_rank=0):
 
 def run_props(args):
     """c2 with the Sec. 2.6 property ODEs: every step also integrates the
-    damage variable and the 3x3 deformation gradient (FP64 velocity gradient
-    at every stage) on top of advect+locate+rebin."""
+    damage variable and the 3x3 deformation gradient (double-float velocity
+    gradient at every stage) on top of advect+locate+rebin."""
     import torch
     from paper_1612_03369_gb300 import pic as P
 
@@ -502,7 +502,7 @@ def run_props(args):
 # FP32 flops (FADD + FMUL + 2 FFMA) per particle-step of the property-ODE
 # kernel (G and the stage arithmetic in double-float), counted by ncu on the
 # 64^3 x 20 workload (profiles/next_rows_c2_64cubed.md).
-PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 28040.0
+PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 18488.0
 
 # FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
 # counted by ncu on the 64^3 x 20 workload; profiles/next_rows_c2_64cubed.md).

@@ -239,9 +239,11 @@ pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, double dt, 
 
 /* Adjoint (gradients with respect to the velocity field).
  * pic_advect_record: n_steps of pic_advect (FP64 form) that also keep, for
- * every step, the store at the start of the step (x, x-hat, cell) and the
- * rebin's permutation; the store ends where pic_advect would leave it.
- * Memory: about (dim*16 + 8) bytes per particle per step plus work arrays.
+ * every step, each particle's stage records (the located cell and the
+ * reference coordinates of every stage point, as the step used them) and the
+ * rebin's permutation; the store ends where pic_advect would leave it, bit
+ * for bit.  Memory: (20 + 32 dim) bytes per particle of capacity per step,
+ * plus work arrays.
  * The mesh and its velocity must not change until the tape is used.
  * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA. */
 pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator, int n_steps,
@@ -254,10 +256,11 @@ pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_
  *   dL_dU      [dim][nnodes] device, overwritten with dL/dU
  *   dL_dx0     [dim][N_0] device or NULL: dL/dx at the start, store order at
  *              the start (0 for particles lost during the run)
- * The stages are recomputed in FP64 from the checkpoints.  Per-stage
- * contributions are summed per cell in (cell, particle slot, stage) order and
- * the cells into the nodes in cell order: the result is reproducible bit for
- * bit.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+ * The velocity gradients at the recorded stage points and the adjoint
+ * variables are carried in double-float arithmetic (~2^-44 relative).
+ * Per-stage contributions are summed per cell in (cell, stage, particle slot)
+ * order and the cells into the nodes in cell order: the result is
+ * reproducible bit for bit.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_tape_adjoint(pic_tape tape, const double *dL_dxfinal, double *dL_dU, double *dL_dx0, void *stream);
 pic_status pic_destroy_tape(pic_tape tape);
 

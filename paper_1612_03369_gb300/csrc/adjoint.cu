@@ -4,19 +4,20 @@
 // endpoints.
 //
 // pic_advect_record advances the store like pic_advect and keeps, for every
-// step, the store at the start of the step (x, x-hat, cell) and the rebin's
-// permutation (new slot -> old slot).  pic_tape_adjoint then sweeps the steps
-// backwards.  For one step, with y_s = x + a_s k_{s-1}, k_s = dt u(y_s),
+// step, each particle's stage records (the located cell and double-float
+// x-hat of every stage point, exactly as the step used them) and the rebin's
+// permutation (new slot -> old slot).  pic_tape_adjoint then sweeps the
+// steps backwards.  For one step, with y_s = x + a_s k_{s-1}, k_s = dt u(y_s),
 // x' = x + sum_s b_s k_s and G_s = du/dx at y_s (cell held fixed):
 //   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
 //   lambda_y_s = dt G_s^T lambda_k_s,       lambda = lambda' + sum_s lambda_y_s
 //   dL/dU_i   += dt phi-hat_i(x-hat_s) lambda_k_s
-// The stages are recomputed from the checkpoint (double-float, as the forward
-// ran them; G in double-float, lambda in FP64).  Each stage leaves a
-// record (stage cell, x-hat_s, dt lambda_k_s) keyed by (slot, stage); the
-// records are sorted by (cell, key), summed per cell in that order, and the
-// cells' sums are added into the nodes in increasing cell order.  No floating-
-// point atomics, so the gradient is bit-for-bit reproducible.
+// G and lambda in double-float.  Each stage's contribution (stage cell,
+// x-hat_s, dt lambda_k_s) is a record keyed by (stage, slot); the records are
+// sorted by (cell, key), summed per cell in that order, and the cells' sums
+// are added into the nodes in increasing cell order.  No floating-point
+// atomics, so the gradient is bit-for-bit reproducible.
+#include <cmath>
 #include <cstdlib>
 
 #include "advect.cuh"
@@ -32,16 +33,14 @@ struct pic_tape_s {
   double dt;
   size_t cap;
   uint32_t C;
-  double** x;      // [n_steps] of [dim][cap]
-  float2** xhat;   // [n_steps] of [dim][cap]
-  uint32_t** cell; // [n_steps] of [cap]
-  uint32_t** perm; // [n_steps] of [cap] (new slot -> old slot)
-  uint32_t* n_dev; // [n_steps + 1] particles at the start of each step (and at the end)
+  uint32_t** rcell;  // [n_steps] of [4][cap]: stage cells (StageRec layout, slots of the start of the step)
+  float2** rt;       // [n_steps] of [dim][4][cap]: stage x-hat, double-float
+  uint32_t** perm;   // [n_steps] of [cap] (new slot -> old slot)
+  uint32_t* n_dev;   // [n_steps + 1] particles at the start of each step (and at the end)
   // reverse-sweep work
-  double* lam[2];      // [dim][cap]
-  uint32_t* rec_cell;  // [4 cap]
+  float2* lam[2];      // [dim][cap] double-float
+  uint32_t* rec_cell;  // [4 cap] stage cells of the step's survivors, PIC_LOST elsewhere (the sort's keys)
   uint64_t* rec_key;   // [4 cap]
-  float2* rec_t;       // [dim][4 cap] double-float x-hat of the stage
   float2* rec_w;       // [dim][4 cap] double-float dt lambda_k
   uint32_t* rec_perm;  // [4 cap]
   uint32_t* rec_off;   // [C + 1]
@@ -53,31 +52,35 @@ namespace pic {
 
 constexpr int kRecPerParticle = 4;
 
+// The tableaux with a_s (a power of two or zero) as float and b_s as a
+// double-float (1/6 and 1/3 to ~2^-48).
 template <int RK>
 struct AdjTableau;
 template <>
 struct AdjTableau<1> {
   static constexpr int S = 1;
-  __device__ static double a(int) { return 0.0; }
-  __device__ static double b(int) { return 1.0; }
+  __device__ static float a(int) { return 0.f; }
+  __device__ static df b(int) { return df_make(1.f, 0.f); }
 };
 template <>
 struct AdjTableau<2> {
   static constexpr int S = 2;
-  __device__ static double a(int s) { return s == 1 ? 0.5 : 0.0; }
-  __device__ static double b(int s) { return s == 1 ? 1.0 : 0.0; }
+  __device__ static float a(int s) { return s == 1 ? 0.5f : 0.f; }
+  __device__ static df b(int s) { return df_make(s == 1 ? 1.f : 0.f, 0.f); }
 };
 template <>
 struct AdjTableau<4> {
   static constexpr int S = 4;
-  __device__ static double a(int s) { return s == 3 ? 1.0 : (s == 0 ? 0.0 : 0.5); }
-  __device__ static double b(int s) { return (s == 0 || s == 3) ? 1.0 / 6.0 : 1.0 / 3.0; }
+  __device__ static float a(int s) { return s == 3 ? 1.f : (s == 0 ? 0.f : 0.5f); }
+  __device__ static df b(int s) {
+    return (s == 0 || s == 3) ? df_make(0.1666666716337204f, -4.967053879312289e-09f)
+                              : df_make(0.3333333432674408f, -9.934107758624577e-09f);
+  }
 };
 
 struct TapeStep {
-  const double* x;
-  const float2* xhat;
-  const uint32_t* cell;
+  const uint32_t* rcell;
+  const float2* rt;
   const uint32_t* perm;
   const uint32_t* n_next;  // particles after the step
 };
@@ -88,140 +91,84 @@ struct TapeStep {
 #define PIC_REVERSE_MIN_BLOCKS 4
 #endif
 
-// One reverse step, in two kernels over the particles alive after the step
-// (thread per new slot j, old slot i = perm[j]).
-//
-// reverse_stages_kernel recomputes the step's stages from the checkpoint
-// exactly as the forward computed them (double-float stage points, the same
-// locate and Q2 contraction, so the stage cells are the forward's) and
-// leaves stage s's cell and double-float x-hat in record 4 j + s.
+// One reverse step, thread per particle alive after the step (new slot j,
+// old slot i = perm[j]): the stages backwards with G_s = du/dx at the
+// recorded stage points, all in double-float on the FP32 pipe:
+//   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
+//   lambda_y_s = dt G_s^T lambda_k_s,   lambda = lambda' + sum_s lambda_y_s
+// and record r = s cap + i gets its cell, key and weight dt lambda_k_s.  The
+// records of particles that did not survive the step stay PIC_LOST.
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) reverse_stages_kernel(
-    MeshView m, TapeStep tp, size_t cap, double dt, uint32_t* __restrict__ rec_cell, float2* __restrict__ rec_t,
+__global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_kernel(
+    MeshView m, TapeStep tp, size_t cap, df dt, const float2* __restrict__ lam_in, float2* __restrict__ lam_out,
+    uint32_t* __restrict__ rec_cell, uint64_t* __restrict__ rec_key, float2* __restrict__ rec_w,
     DevCounters* __restrict__ ctr) {
   using TB = AdjTableau<RK>;
   constexpr int S = TB::S;
   const uint32_t n = *tp.n_next;
   const size_t rcap = kRecPerParticle * cap;
-  const float dthi = (float)dt;
-  const df dtd = df_make(dthi, (float)(dt - (double)dthi));
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const uint32_t i = tp.perm[j];
     if (i >= cap) {
       latch_status(ctr, PIC_STATUS_BOUNDS);
       continue;
     }
-    df xd[D], ts[D], k[D];
+    uint32_t Ks[S];
+    bool ok = true;
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const float2 v = tp.xhat[a * cap + i];
-      ts[a] = df_make(v.x, v.y);
-      xd[a] = df_from_double(tp.x[a * cap + i]);
+    for (int s = 0; s < S; ++s) {
+      Ks[s] = tp.rcell[(size_t)s * cap + i];
+      ok = ok && Ks[s] < m.C;
     }
-    uint32_t K = tp.cell[i];
-    if (K >= m.C) {
+    if (!ok) {  // cannot happen for a particle that survived the step
       latch_status(ctr, PIC_STATUS_BOUNDS);
       continue;
     }
-    int iters = 0;
-    unsigned flags = 0;
-#pragma unroll 1
-    for (int s = 0; s < S; ++s) {
-      if (s > 0) {
-        df y[D];
-        float hint[D];
-#pragma unroll
-        for (int a = 0; a < D; ++a) {
-          y[a] = df_add(xd[a], df_scale2(k[a], (float)TB::a(s)));
-          hint[a] = ts[a].hi;
-        }
-        K = locate_df<D>(m, y, K, hint, ts, iters, flags);
-        if (K == PIC_LOST) {
-          // cannot happen for a particle that survived the step; keep it harmless
-          latch_status(ctr, PIC_STATUS_BOUNDS);
-          break;
-        }
-      }
-      const size_t r = (size_t)kRecPerParticle * j + s;
-      rec_cell[r] = K;
-#pragma unroll
-      for (int a = 0; a < D; ++a) rec_t[a * rcap + r] = make_float2(ts[a].hi, ts[a].lo);
-      if (s + 1 < S) {
-        df u[D];
-        q2_eval_df<D>(m, m.Qc, K, ts, u);
-#pragma unroll
-        for (int a = 0; a < D; ++a) k[a] = df_mul(dtd, u[a]);
-      }
-    }
-  }
-}
-
-// reverse_lambda_kernel sweeps the stages backwards with G_s = du/dx at the
-// recorded stage points (double-float, handed back in FP64; lambda in FP64):
-//   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
-//   lambda_y_s = dt G_s^T lambda_k_s,   lambda = lambda' + sum_s lambda_y_s
-// and completes record 4 j + s with its key and weight dt lambda_k_s.  A
-// particle whose stages were not all recorded has its records cleared.
-template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_kernel(
-    MeshView m, TapeStep tp, size_t cap, double dt, const double* __restrict__ lam_in, double* __restrict__ lam_out,
-    uint32_t* __restrict__ rec_cell, uint64_t* __restrict__ rec_key, const float2* __restrict__ rec_t,
-    float2* __restrict__ rec_w) {
-  using TB = AdjTableau<RK>;
-  constexpr int S = TB::S;
-  const uint32_t n = *tp.n_next;
-  const size_t rcap = kRecPerParticle * cap;
-  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t i = tp.perm[j];
-    if (i >= cap) continue;
-    bool ok = true;
-#pragma unroll
-    for (int s = 0; s < S; ++s) ok = ok && rec_cell[(size_t)kRecPerParticle * j + s] < m.C;
-    if (!ok) {
-#pragma unroll
-      for (int s = 0; s < kRecPerParticle; ++s) rec_cell[(size_t)kRecPerParticle * j + s] = PIC_LOST;
-      continue;
-    }
-    double lam[D], lam_x[D], lam_ynext[D];
+    df lam[D], lam_x[D], lam_ynext[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      lam[a] = lam_in[a * cap + j];
+      const float2 v = lam_in[a * cap + j];
+      lam[a] = df_make(v.x, v.y);
       lam_x[a] = lam[a];
-      lam_ynext[a] = 0.0;
+      lam_ynext[a] = df_make(0.f, 0.f);
     }
 #pragma unroll 1
     for (int s = S - 1; s >= 0; --s) {
-      const size_t r = (size_t)kRecPerParticle * j + s;
+      const size_t r = (size_t)s * cap + i;
       df t[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const float2 v = rec_t[a * rcap + r];
+        const float2 v = tp.rt[a * rcap + r];
         t[a] = df_make(v.x, v.y);
       }
-      double G[D][D];
-      velocity_gradient_df<D>(m, rec_cell[r], t, G);
-      double lk[D];
+      uint32_t K = Ks[0];
 #pragma unroll
-      for (int a = 0; a < D; ++a) lk[a] = TB::b(s) * lam[a] + (s + 1 < S ? TB::a(s + 1) * lam_ynext[a] : 0.0);
+      for (int q = 1; q < S; ++q) K = (s == q) ? Ks[q] : K;
+      df G[D][D];
+      velocity_gradient_df<D>(m, K, t, G);
+      const df bs = TB::b(s);
+      const float an = s + 1 < S ? TB::a(s + 1) : 0.f;
+      df lk[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) lk[a] = df_add(df_mul(bs, lam[a]), df_scale2(lam_ynext[a], an));
+      rec_cell[r] = K;
       rec_key[r] = r;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const df w = df_from_double(dt * lk[a]);
+        const df w = df_mul(dt, lk[a]);
         rec_w[a * rcap + r] = make_float2(w.hi, w.lo);
       }
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        double acc = 0.0;
+        df_acc acc = acc_zero();
 #pragma unroll
-        for (int c = 0; c < D; ++c) acc += G[c][q] * lk[c];
-        lam_ynext[q] = dt * acc;
-        lam_x[q] += lam_ynext[q];
+        for (int c = 0; c < D; ++c) acc_mad(acc, G[c][q], lk[c]);
+        lam_ynext[q] = df_mul(dt, acc_result(acc));
+        lam_x[q] = df_add(lam_x[q], lam_ynext[q]);
       }
     }
 #pragma unroll
-    for (int s = S; s < kRecPerParticle; ++s) rec_cell[(size_t)kRecPerParticle * j + s] = PIC_LOST;
-#pragma unroll
-    for (int a = 0; a < D; ++a) lam_out[a * cap + i] = lam_x[a];
+    for (int a = 0; a < D; ++a) lam_out[a * cap + i] = make_float2(lam_x[a].hi, lam_x[a].lo);
   }
 }
 
@@ -346,19 +293,24 @@ __global__ void node_reduce_kernel(MeshView m, const double* __restrict__ partia
   }
 }
 
-// lam[a*cap + j] = src[a*n + j] for j < n (dense caller layout -> strided).
-__global__ void copy_in_kernel(const double* __restrict__ src, double* __restrict__ dst, const uint32_t* n_dev, int dim,
+// lam[a*cap + j] = src[a*n + j] for j < n (dense caller layout -> strided,
+// FP64 -> double-float).
+__global__ void copy_in_kernel(const double* __restrict__ src, float2* __restrict__ dst, const uint32_t* n_dev, int dim,
                                size_t cap) {
   const uint32_t n = *n_dev;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x)
-    dst[(q / n) * cap + q % n] = src[q];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x) {
+    const df v = df_from_double(src[q]);
+    dst[(q / n) * cap + q % n] = make_float2(v.hi, v.lo);
+  }
 }
 
-__global__ void copy_out_kernel(const double* __restrict__ src, double* __restrict__ dst, const uint32_t* n_dev, int dim,
+__global__ void copy_out_kernel(const float2* __restrict__ src, double* __restrict__ dst, const uint32_t* n_dev, int dim,
                                 size_t cap) {
   const uint32_t n = *n_dev;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x)
-    dst[q] = src[(q / n) * cap + q % n];
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < (size_t)n * dim; q += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = src[(q / n) * cap + q % n];
+    dst[q] = df_to_double(df_make(v.x, v.y));
+  }
 }
 
 static int grid_of(size_t n, int block) {
@@ -368,12 +320,12 @@ static int grid_of(size_t n, int block) {
 }
 
 template <int D, int RK>
-static void launch_reverse(pic_tape_s* tp, const MeshView& m, const TapeStep& ts, const double* lin, double* lout,
+static void launch_reverse(pic_tape_s* tp, const MeshView& m, const TapeStep& ts, const float2* lin, float2* lout,
                            cudaStream_t st) {
-  reverse_stages_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, tp->rec_cell, tp->rec_t,
-                                                                       tp->parts->ctr);
-  reverse_lambda_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, tp->dt, lin, lout, tp->rec_cell,
-                                                                       tp->rec_key, tp->rec_t, tp->rec_w);
+  const float hi = (float)tp->dt;
+  const df dtd = {hi, (float)(tp->dt - (double)hi)};
+  reverse_lambda_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, dtd, lin, lout, tp->rec_cell,
+                                                                       tp->rec_key, tp->rec_w, tp->parts->ctr);
 }
 
 }  // namespace pic
@@ -383,21 +335,18 @@ using namespace pic;
 extern "C" pic_status pic_destroy_tape(pic_tape tp) {
   if (!tp) return PIC_OK;
   for (int s = 0; s < tp->n_steps; ++s) {
-    if (tp->x) cudaFree(tp->x[s]);
-    if (tp->xhat) cudaFree(tp->xhat[s]);
-    if (tp->cell) cudaFree(tp->cell[s]);
+    if (tp->rcell) cudaFree(tp->rcell[s]);
+    if (tp->rt) cudaFree(tp->rt[s]);
     if (tp->perm) cudaFree(tp->perm[s]);
   }
-  free(tp->x);
-  free(tp->xhat);
-  free(tp->cell);
+  free(tp->rcell);
+  free(tp->rt);
   free(tp->perm);
   cudaFree(tp->n_dev);
   cudaFree(tp->lam[0]);
   cudaFree(tp->lam[1]);
   cudaFree(tp->rec_cell);
   cudaFree(tp->rec_key);
-  cudaFree(tp->rec_t);
   cudaFree(tp->rec_w);
   cudaFree(tp->rec_perm);
   cudaFree(tp->rec_off);
@@ -411,7 +360,9 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
                                         int n_steps, void* stream, pic_tape* out) {
   if (!out) return (set_error("pic_advect_record: out is NULL"), PIC_ERR_ARG);
   *out = nullptr;
-  if (!parts || !mesh || parts->mesh != mesh) return (set_error("pic_advect_record: bad handles"), PIC_ERR_ARG);
+  if (!parts || !mesh || parts->mesh != mesh || parts->dim != mesh->dim)
+    return (set_error("pic_advect_record: bad handles"), PIC_ERR_ARG);
+  if (!std::isfinite(dt)) return (set_error("pic_advect_record: dt not finite"), PIC_ERR_ARG);
   if (n_steps < 1) return (set_error("pic_advect_record: n_steps must be >= 1"), PIC_ERR_ARG);
   if (integrator != PIC_EULER && integrator != PIC_RK2 && integrator != PIC_RK4)
     return (set_error("pic_advect_record: unknown integrator"), PIC_ERR_ARG);
@@ -419,10 +370,6 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   if (mesh->has_next)
     return (set_error("pic_advect_record: the adjoint supports a steady field only (no U_next)"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
-  {
-    pic_status r0 = ensure_nodal_df(mesh, st);  // the reverse sweep's gradients read the nodal copy
-    if (r0 != PIC_OK) return r0;
-  }
   pic_tape_s* tp = (pic_tape_s*)calloc(1, sizeof(pic_tape_s));
   tp->parts = parts;
   tp->mesh = mesh;
@@ -434,23 +381,20 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   tp->C = mesh->C;
   const size_t cap = tp->cap, d = (size_t)tp->dim, rcap = kRecPerParticle * cap;
   const int NE = (tp->dim == 3 ? 27 : 9) * tp->dim;
-  tp->x = (double**)calloc(n_steps, sizeof(double*));
-  tp->xhat = (float2**)calloc(n_steps, sizeof(float2*));
-  tp->cell = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
+  tp->rcell = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
+  tp->rt = (float2**)calloc(n_steps, sizeof(float2*));
   tp->perm = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
-  bool ok = tp->x && tp->xhat && tp->cell && tp->perm;
+  bool ok = tp->rcell && tp->rt && tp->perm;
   for (int s = 0; s < n_steps && ok; ++s) {
-    ok = ok && cudaMalloc(&tp->x[s], sizeof(double) * d * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&tp->xhat[s], sizeof(float2) * d * cap) == cudaSuccess;
-    ok = ok && cudaMalloc(&tp->cell[s], sizeof(uint32_t) * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->rcell[s], sizeof(uint32_t) * rcap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->rt[s], sizeof(float2) * d * rcap) == cudaSuccess;
     ok = ok && cudaMalloc(&tp->perm[s], sizeof(uint32_t) * cap) == cudaSuccess;
   }
   ok = ok && cudaMalloc(&tp->n_dev, sizeof(uint32_t) * (n_steps + 1)) == cudaSuccess;
-  ok = ok && cudaMalloc(&tp->lam[0], sizeof(double) * d * cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&tp->lam[1], sizeof(double) * d * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->lam[0], sizeof(float2) * d * cap) == cudaSuccess;
+  ok = ok && cudaMalloc(&tp->lam[1], sizeof(float2) * d * cap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_cell, sizeof(uint32_t) * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_key, sizeof(uint64_t) * rcap) == cudaSuccess;
-  ok = ok && cudaMalloc(&tp->rec_t, sizeof(float2) * d * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_w, sizeof(float2) * d * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_perm, sizeof(uint32_t) * rcap) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->rec_off, sizeof(uint32_t) * ((size_t)tp->C + 1)) == cudaSuccess;
@@ -461,20 +405,21 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
     pic_destroy_tape(tp);
     return (set_error("pic_advect_record: device allocation failed"), PIC_ERR_OOM);
   }
+  const MeshView m = mesh_view(mesh);
   for (int s = 0; s < n_steps; ++s) {
-    const int c = parts->cur;
-    cudaError_t e = cudaMemcpyAsync(tp->x[s], parts->x[c], sizeof(double) * d * cap, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tp->xhat[s], parts->xhat[c], sizeof(float2) * d * cap, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tp->cell[s], parts->cell[c], sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(tp->n_dev + s, &parts->ctr->n_alive, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(tp->n_dev + s, &parts->ctr->n_alive, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st);
     if (e != cudaSuccess) {
       pic_destroy_tape(tp);
-      return cuda_fail(e, "pic_advect_record: checkpoint");
+      return cuda_fail(e, "pic_advect_record: count");
     }
-    pic_status r = pic_advect(parts, mesh, dt, integrator, PIC_FP64, 1, stream);
+    launch_advect_record(parts, m, dt, (int)integrator, StageRec{tp->rcell[s], tp->rt[s], cap}, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      pic_destroy_tape(tp);
+      return cuda_fail(e, "pic_advect_record: step");
+    }
+    pic_status r = rebin_from_counts(parts, st);
     if (r != PIC_OK) {
       pic_destroy_tape(tp);
       return r;
@@ -502,22 +447,21 @@ extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, do
   const MeshView m = mesh_view(mesh);
   const size_t cap = tp->cap, d = (size_t)tp->dim, rcap = kRecPerParticle * cap;
   PIC_CUDA(cudaMemsetAsync(dL_dU, 0, sizeof(double) * d * (size_t)mesh->nnodes, st));
-  PIC_CUDA(cudaMemsetAsync(tp->lam[0], 0, sizeof(double) * d * cap, st));
+  PIC_CUDA(cudaMemsetAsync(tp->lam[0], 0, sizeof(float2) * d * cap, st));
   copy_in_kernel<<<grid_of(d * cap, 256), 256, 0, st>>>(dL_dxfinal, tp->lam[0], tp->n_dev + tp->n_steps, tp->dim, cap);
   count_launches(1);
   int cur = 0;
   const SortScratch sc = sort_scratch_layout(tp->sort_scratch, rcap, tp->C);
   for (int s = tp->n_steps - 1; s >= 0; --s) {
     TapeStep ts;
-    ts.x = tp->x[s];
-    ts.xhat = tp->xhat[s];
-    ts.cell = tp->cell[s];
+    ts.rcell = tp->rcell[s];
+    ts.rt = tp->rt[s];
     ts.perm = tp->perm[s];
     ts.n_next = tp->n_dev + s + 1;
-    PIC_CUDA(cudaMemsetAsync(tp->lam[1 - cur], 0, sizeof(double) * d * cap, st));
+    PIC_CUDA(cudaMemsetAsync(tp->lam[1 - cur], 0, sizeof(float2) * d * cap, st));
     PIC_CUDA(cudaMemsetAsync(tp->rec_cell, 0xFF, sizeof(uint32_t) * rcap, st));
-    const double* lin = tp->lam[cur];
-    double* lout = tp->lam[1 - cur];
+    const float2* lin = tp->lam[cur];
+    float2* lout = tp->lam[1 - cur];
     if (tp->dim == 2) {
       if (tp->integrator == 1) launch_reverse<2, 1>(tp, m, ts, lin, lout, st);
       else if (tp->integrator == 2) launch_reverse<2, 2>(tp, m, ts, lin, lout, st);
@@ -527,17 +471,17 @@ extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, do
       else if (tp->integrator == 2) launch_reverse<3, 2>(tp, m, ts, lin, lout, st);
       else launch_reverse<3, 4>(tp, m, ts, lin, lout, st);
     }
-    count_launches(2);
+    count_launches(1);
     PIC_CUDA(cudaGetLastError());
     pic_status r = sort_by_cell_run(rcap, tp->rec_cell, tp->rec_key, tp->C, tp->rec_perm, tp->rec_off, sc, st);
     if (r != PIC_OK) return r;
     const int gp = grid_of((size_t)tp->C * 32, 256);
     const int gn = grid_of(d * (size_t)mesh->nnodes, 256);
     if (tp->dim == 2) {
-      cell_partial_kernel<2><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, tp->rec_t, tp->rec_w, rcap, tp->partial);
+      cell_partial_kernel<2><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, ts.rt, tp->rec_w, rcap, tp->partial);
       node_reduce_kernel<2><<<gn, 256, 0, st>>>(m, tp->partial, dL_dU);
     } else {
-      cell_partial_kernel<3><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, tp->rec_t, tp->rec_w, rcap, tp->partial);
+      cell_partial_kernel<3><<<gp, 256, 0, st>>>(tp->C, tp->rec_off, tp->rec_perm, ts.rt, tp->rec_w, rcap, tp->partial);
       node_reduce_kernel<3><<<gn, 256, 0, st>>>(m, tp->partial, dL_dU);
     }
     count_launches(2);

@@ -8,6 +8,7 @@
 //                (t0, t1, t0 t1) in 2D; X_0 and every a_k as double-floats
 //                (192 B per hex, 64 B per quad, 16-byte aligned)
 //   U2           Q2 nodal values as double-floats, node-major [node][dim]
+//                (the source of the coefficient slices below)
 //
 // Inverse map (Newton, Sec. 2.2 / Remark 2.1): FP32 iterations on the local
 // offset y - X_0 until the update falls below 1e-5, then one Newton step

@@ -3,14 +3,16 @@
 // of GB300 issues ~1/75 of the FP32 rate).  Used by the property ODEs of
 // Sec. 2.6 and by the adjoint sweep; G is handed back in FP64.
 //
-//   du/dx-hat   sum-factorised contraction of the Q2 nodal values with the
-//               1D Lagrange values l_a and derivatives l'_a:
-//                 l'_0 = 4t - 3,  l'_1 = 4 - 8t,  l'_2 = 4t - 1
+//   du/dx-hat   from the cell's monomial coefficients about its centre
+//               (u_c = sum c_pqr s0^p s1^q s2^r, s = x-hat - 1/2, so
+//               d/dx-hat = d/ds): Horner steps that carry each partial
+//               sum's value and its derivatives along the axes already
+//               passed
 //   J           from the cell's monomial block (the map about vertex 0,
 //               Phi = X_0 + sum_k a_k m_k(t)): J_ij = sum_k a_k,i dm_k/dt_j
 //   J^{-1}      cofactors over the determinant, one double-float reciprocal
 // Every product is a double-float product (two_prod), every sum a
-// double-float accumulation, so G carries ~2^-46 relative error times the
+// double-float sum, so G carries ~2^-44 relative error times the
 // conditioning of J.
 #pragma once
 
@@ -33,60 +35,56 @@ __device__ __forceinline__ df df_recip(df a) {
   return fast_two_sum(r, __fmul_rn(r, e));
 }
 
-// l'_a(t) for the quadratic Lagrange basis on {0, 1/2, 1}.
-__device__ __forceinline__ void lagrange2_deriv_df(df t, df dl[3]) {
-  const df t4 = df_scale2(t, 4.0f);
-  dl[0] = df_add_f(t4, -3.0f);
-  dl[1] = df_add_f(df_make(-2.0f * t4.hi, -2.0f * t4.lo), 4.0f);
-  dl[2] = df_add_f(t4, -1.0f);
-}
-
-// Gu[c][j] = d u_c / d t_j in cell K at double-float reference coordinates t.
+// Gu[c][j] = d u_c / d t_j in cell K at double-float reference coordinates
+// t, from the coefficient slices q2_eval_df reads (slice r holds the nine
+// c_pq r, index 3 q + p).  Along s0 each row (q, r) gives its value h and
+// derivative h' = c_1 + 2 c_2 s0; along s1 each slice gives its value g and
+// the derivatives g0 (of the h') and g1 (of the h); along s2 the slices
+// combine the same way.  47 double-float Horner steps per component.
 template <int D>
-__device__ __forceinline__ void q2_grad_df(const MeshView& m, const float2* __restrict__ U2, uint32_t K, const df t[D],
-                                           df Gu[D][D]) {
-  const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
-  const int64_t base = __ldg(m.qbase + K);
-  df l[D][3], dl[D][3];
+__device__ __forceinline__ void q2_grad_mono_df(const float4* __restrict__ Qc, uint32_t K, const df t[D],
+                                                df Gu[D][D]) {
+  constexpr int NS = (D == 3 ? 3 : 1);
+  df s[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    lagrange2_df(t[a], l[a]);
-    lagrange2_deriv_df(t[a], dl[a]);
-  }
+  for (int a = 0; a < D; ++a) s[a] = centred(t[a]);
+  const float4* cell = Qc + (size_t)K * D * (5 * NS);
 #pragma unroll 1
   for (int comp = 0; comp < D; ++comp) {
-    df_acc g[D];
+    const float4* cq = cell + comp * (5 * NS);
+    df g[NS], g0[NS], g1[NS];
 #pragma unroll
-    for (int j = 0; j < D; ++j) g[j] = acc_zero();
+    for (int r = 0; r < NS; ++r) {
+      float f[20];  // ten high parts, then ten low parts
 #pragma unroll
-    for (int cz = 0; cz < (D == 3 ? 3 : 1); ++cz) {
-      df_acc sv = acc_zero(), s0 = acc_zero(), s1 = acc_zero();
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float2* row = U2 + (base + b * sy + (D == 3 ? cz * sz : 0)) * D + comp;
-        df_acc rv = acc_zero(), rd = acc_zero();
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const float2 u = __ldg(row + a * D);
-          const df ud = df_make(u.x, u.y);
-          acc_mad(rv, ud, l[0][a]);
-          acc_mad(rd, ud, dl[0][a]);
-        }
-        acc_mad(sv, acc_pair(rv), l[1][b]);
-        acc_mad(s0, acc_pair(rd), l[1][b]);
-        acc_mad(s1, acc_pair(rv), dl[1][b]);
+      for (int k = 0; k < 5; ++k) {
+        const float4 v = __ldg(cq + 5 * r + k);
+        f[4 * k] = v.x;
+        f[4 * k + 1] = v.y;
+        f[4 * k + 2] = v.z;
+        f[4 * k + 3] = v.w;
       }
-      if constexpr (D == 3) {
-        acc_mad(g[0], acc_pair(s0), l[2][cz]);
-        acc_mad(g[1], acc_pair(s1), l[2][cz]);
-        acc_mad(g[2], acc_pair(sv), dl[2][cz]);
-      } else {
-        g[0] = s0;
-        g[1] = s1;
+      df c[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) c[e] = df_make(f[e], f[10 + e]);
+      df h[3], h0[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        h[q] = df_horner(df_horner(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
+        h0[q] = df_horner(df_scale2(c[3 * q + 2], 2.0f), s[0], c[3 * q + 1]);
       }
+      g[r] = df_horner(df_horner(h[2], s[1], h[1]), s[1], h[0]);
+      g0[r] = df_horner(df_horner(h0[2], s[1], h0[1]), s[1], h0[0]);
+      g1[r] = df_horner(df_scale2(h[2], 2.0f), s[1], h[1]);
     }
-#pragma unroll
-    for (int j = 0; j < D; ++j) Gu[comp][j] = acc_result(g[j]);
+    if constexpr (D == 3) {
+      Gu[comp][0] = df_norm(df_horner(df_horner(g0[2], s[2], g0[1]), s[2], g0[0]));
+      Gu[comp][1] = df_norm(df_horner(df_horner(g1[2], s[2], g1[1]), s[2], g1[0]));
+      Gu[comp][2] = df_norm(df_horner(df_scale2(g[2], 2.0f), s[2], g[1]));
+    } else {
+      Gu[comp][0] = df_norm(g0[0]);
+      Gu[comp][1] = df_norm(g1[0]);
+    }
   }
 }
 
@@ -167,7 +165,7 @@ __device__ __forceinline__ void invert_df(const df J[D][D], df Ji[D][D]) {
 template <int D>
 __device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], df G[D][D]) {
   df Gu[D][D], J[D][D], Ji[D][D];
-  q2_grad_df<D>(m, m.U2, K, t, Gu);
+  q2_grad_mono_df<D>(m.Qc, K, t, Gu);
   CellBlock<D> cb;
   load_block<D>(m, K, cb);
   map_jacobian_df<D>(cb, t, J);

@@ -335,7 +335,6 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
   }
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
   build_coefficients(m, m->U, m->U2, m->Qc, st);
-  m->u2_valid = 1;
   if (U_next) {
     PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
     build_coefficients(m, m->Un, m->U2n, m->Qcn, st);
@@ -384,25 +383,9 @@ extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
   m->U = m->Ustage;
   m->Ustage = t;
   build_coefficients(m, m->U, m->U2, m->Qc, st);
-  m->u2_valid = 1;
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaEventRecord(m->ev_free, st));
   m->free_recorded = 1;
   m->staged = 0;
   return PIC_OK;
 }
-
-namespace pic {
-
-pic_status ensure_nodal_df(pic_mesh_s* m, cudaStream_t st) {
-  if (m->u2_valid) return PIC_OK;
-  const size_t n = (size_t)m->dim * (size_t)m->nnodes;
-  const int g = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  to_df_nodes_kernel<<<g, 256, 0, st>>>(m->U, m->U2, m->dim, (size_t)m->nnodes);
-  count_launches(1);
-  PIC_CUDA(cudaGetLastError());
-  m->u2_valid = 1;
-  return PIC_OK;
-}
-
-}  // namespace pic

@@ -62,8 +62,7 @@ struct pic_mesh_s {
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
   uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
-  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo): the coefficients' source, and the gradient's
-  int u2_valid;  // U2 holds the current field
+  float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo): the coefficients' source
   double* Un;    // the field at the end of the step (time interpolation), when set
   float2* U2n;   // its double-float nodal copy (the source of Qcn)
   float4* Qc;    // [C][dim][slices][5] per-cell monomial coefficients (double-float pairs, see fastpath.cuh)
@@ -103,7 +102,7 @@ struct pic_particles_s {
   uint32_t* perm;         // [capacity]
   pic::DevCounters* ctr;  // device counters and status word
   double* xfer;           // [2 * 2^dim][C] per-cell partial sums of the vertex averages, allocated on first use
-  void* stage_rec;        // property ODEs: per stage cell [4][cap] u32 then x-hat [4][dim][cap] float2, on first use
+  void* stage_rec;        // property ODEs: StageRec arrays, cell [4][cap] u32 then x-hat [dim][4][cap] float2, on first use
   cudaStream_t stream;
   // optional event timing of pic_advect (instrumentation)
   int timing;
@@ -134,7 +133,6 @@ struct MeshView {
   const double* bbox;
   const float4* blk;
   const uint32_t* qbase;
-  const float2* U2;
   const float4* Qc;   // per-cell monomial coefficients of the field (and of the second field)
   const float4* Qcn;
   int has_next;
@@ -158,7 +156,6 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.bbox = m->bbox;
   v.blk = m->blk;
   v.qbase = m->qbase;
-  v.U2 = m->U2;
   v.Qc = m->Qc;
   v.Qcn = m->Qcn;
   v.has_next = m->has_next;
@@ -354,10 +351,21 @@ pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s);
 // The two halves of rebin_from_counts: the new order (perm, offsets, sorted
 // cells in the other buffer), then the gather that applies it.
 pic_status rebin_order_from_counts(pic_particles_s* p, cudaStream_t s);
+// Stage records of one step (props.cu): for evaluation point p < 4 of the
+// particle in slot i (store order at the start of the step), the located
+// cell at cell[p cap + i] and component a of its double-float x-hat at
+// t[(4 a + p) cap + i], so that record r = p cap + i has its components at
+// t[a 4 cap + r].
+struct StageRec {
+  uint32_t* cell;
+  float2* t;
+  size_t cap;
+};
+// One particle step of pic_advect (FP64 form, in place, counts and cell_new
+// for the rebin) that also writes the stage records.
+void launch_advect_record(pic_particles_s* p, const MeshView& m, double dt, int rk, const StageRec& rec,
+                          cudaStream_t st);
 pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s);
-// Build the nodal double-float copy U2 of the current field if it is stale
-// (mesh.cu); the callers that evaluate velocity gradients call it first.
-pic_status ensure_nodal_df(pic_mesh_s* m, cudaStream_t st);
 // Counting, cell offsets and store allocation shared by the generators
 // (particles.cu); the store's buffer 0 is then filled by the caller.
 pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,

@@ -27,14 +27,6 @@ struct OdeArgs {
   df alpha, beta;
 };
 
-// Stage records: for every evaluation point p < S of particle i, the located
-// cell and the double-float reference coordinates, [S][i] and [S][D][i].
-struct StageRec {
-  uint32_t* cell;
-  float2* t;
-  size_t cap;
-};
-
 struct RecordHook {
   StageRec r;
   uint32_t i;
@@ -42,7 +34,7 @@ struct RecordHook {
   __device__ __forceinline__ void stage(int p, uint32_t K, const df* t) {
     r.cell[(size_t)p * r.cap + i] = K;
 #pragma unroll
-    for (int a = 0; a < D; ++a) r.t[((size_t)p * D + a) * r.cap + i] = make_float2(t[a].hi, t[a].lo);
+    for (int a = 0; a < D; ++a) r.t[((size_t)a * 4 + p) * r.cap + i] = make_float2(t[a].hi, t[a].lo);
   }
 };
 
@@ -82,7 +74,7 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kern
 // Resident blocks per SM requested from the register allocator (swept at
 // build time with -DPIC_PROPS_MIN_BLOCKS=n).
 #ifndef PIC_PROPS_MIN_BLOCKS
-#define PIC_PROPS_MIN_BLOCKS 5
+#define PIC_PROPS_MIN_BLOCKS 4
 #endif
 
 template <int D, int RK>
@@ -109,7 +101,7 @@ __global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(Me
       df t[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        const float2 v = rec.t[((size_t)p * D + a) * rec.cap + i];
+        const float2 v = rec.t[((size_t)a * 4 + p) * rec.cap + i];
         t[a] = df_make(v.x, v.y);
       }
       df G[D][D];
@@ -194,6 +186,30 @@ static void launch_props(pic_particles_s* p, const MeshView& m, double dt, int r
     launch_props_rk<D, 4>(p, m, dtd, o, rec, st);
 }
 
+template <int D>
+static void launch_record_d(pic_particles_s* p, const MeshView& m, df dt, int rk, const StageRec& rec,
+                            cudaStream_t st) {
+  const StoreView s = store_view(p, p->cur);
+  const int g = props_grid(p->capacity);
+  if (rk == 1)
+    advect_record_kernel<D, 1><<<g, 128, 0, st>>>(m, s, dt, rec, p->cell_new, p->counts, p->ctr);
+  else if (rk == 2)
+    advect_record_kernel<D, 2><<<g, 128, 0, st>>>(m, s, dt, rec, p->cell_new, p->counts, p->ctr);
+  else
+    advect_record_kernel<D, 4><<<g, 128, 0, st>>>(m, s, dt, rec, p->cell_new, p->counts, p->ctr);
+  count_launches(1);
+}
+
+void launch_advect_record(pic_particles_s* p, const MeshView& m, double dt, int rk, const StageRec& rec,
+                          cudaStream_t st) {
+  const float hi = (float)dt;
+  const df dtd = {hi, (float)(dt - (double)hi)};
+  if (p->dim == 2)
+    launch_record_d<2>(p, m, dtd, rk, rec, st);
+  else
+    launch_record_d<3>(p, m, dtd, rk, rec, st);
+}
+
 }  // namespace pic
 
 using namespace pic;
@@ -238,10 +254,6 @@ extern "C" pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, 
       parts->stage_rec = nullptr;
       return (set_error("pic_advect_properties: cannot allocate %zu bytes of stage records", bytes), PIC_ERR_OOM);
     }
-  }
-  {
-    pic_status r = ensure_nodal_df(mesh, st);
-    if (r != PIC_OK) return r;
   }
   const StageRec rec = {(uint32_t*)parts->stage_rec,
                         (float2*)((char*)parts->stage_rec + (size_t)4 * parts->capacity * sizeof(uint32_t)),
