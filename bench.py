@@ -341,20 +341,13 @@ def run_adjoint(args):
         return P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed)
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fwd_ms, adj_ms, rec_ms = [], [], []
-    for rep in range(args.warmup + args.steps):
+
+    def gradient(kind):
+        # recorded forward, then the reverse sweep: (record ms, reverse ms)
         p = fresh()
         torch.cuda.synchronize()
         e0.record()
-        p.advect(wl.dt, 4, steps)
-        e1.record()
-        torch.cuda.synchronize()
-        f = e0.elapsed_time(e1)
-        p.close()
-        p = fresh()
-        torch.cuda.synchronize()
-        e0.record()
-        tape = P.pic_advect_record(p.h, mesh.h, wl.dt, 4, steps)
+        tape = P.pic_advect_record_tape(p.h, mesh.h, wl.dt, 4, steps, kind)
         e1.record()
         torch.cuda.synchronize()
         r = e0.elapsed_time(e1)
@@ -369,11 +362,27 @@ def run_adjoint(args):
         a = e0.elapsed_time(e1)
         P.pic_destroy_tape(tape)
         p.close()
+        return r, a
+
+    fwd_ms, adj_ms, rec_ms = [], [], []
+    for rep in range(args.warmup + args.steps):
+        p = fresh()
+        torch.cuda.synchronize()
+        e0.record()
+        p.advect(wl.dt, 4, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        f = e0.elapsed_time(e1)
+        p.close()
+        r, a = gradient(P.PIC_TAPE_STAGES)
         if rep >= args.warmup:
             fwd_ms.append(f)
             rec_ms.append(r)
             adj_ms.append(a)
     f, r, a = statistics.median(fwd_ms), statistics.median(rec_ms), statistics.median(adj_ms)
+    # the same gradient through a checkpoint tape (about half the memory)
+    ck = [gradient(P.PIC_TAPE_CHECKPOINTS) for _ in range(1 + max(1, args.steps))][1:]
+    ck_r, ck_a = statistics.median(c[0] for c in ck), statistics.median(c[1] for c in ck)
     psteps = N * steps
     return {
         "metric": "adjoint particle-steps/s (recorded forward + reverse sweep), 3D Q2 mesh",
@@ -384,6 +393,10 @@ def run_adjoint(args):
                    "one_benchmark_step": "one full gradient: %d recorded steps + reverse sweep" % steps},
         "forward_plain_ms": f, "record_ms": r, "reverse_ms": a,
         "forward_plain_particle_steps_per_s": psteps / (f / 1e3),
+        "tape": "stage records (116 B per particle-step)",
+        "checkpoint_tape": {"record_ms": ck_r, "reverse_ms": ck_a, "gradient_ms": ck_r + ck_a,
+                            "particle_steps_per_s": psteps / ((ck_r + ck_a) / 1e3),
+                            "bytes_per_particle_step": 56},
         "accuracy": "dL/dU within 1e-11 of max|dL/dU| of the oracle's reverse mode (tests/test_gpu_adjoint.py)",
     }
 

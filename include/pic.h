@@ -249,6 +249,21 @@ pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, double dt, 
 pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator, int n_steps,
                              void *stream, pic_tape *out);
 
+/* What a tape keeps per step.
+ *   PIC_TAPE_STAGES       the stage records above, read back by the sweep:
+ *                         (20 + 32 dim) bytes per particle of capacity
+ *   PIC_TAPE_CHECKPOINTS  the store at the start of the step (x, x-hat, cell)
+ *                         and the permutation: (8 + 16 dim) bytes per particle
+ *                         of capacity; the sweep replays each step from its
+ *                         checkpoint with the forward's own particle step, so
+ *                         the gradient is the same bit for bit, at the cost of
+ *                         one more advect per step.
+ * pic_advect_record is pic_advect_record_tape with PIC_TAPE_STAGES.
+ * Errors: those of pic_advect_record; an unknown kind is PIC_ERR_ARG. */
+typedef enum { PIC_TAPE_STAGES = 0, PIC_TAPE_CHECKPOINTS = 1 } pic_tape_kind;
+pic_status pic_advect_record_tape(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                                  int n_steps, pic_tape_kind kind, void *stream, pic_tape *out);
+
 /* Reverse sweep of a recorded run (adjoint of the Sec. 2.3 integrators over
  * located stages; a stage's cell is held fixed, where u_h is continuous):
  *   dL_dxfinal [dim][N_final] device: dL/dx of the particles alive at the end,

@@ -33,8 +33,15 @@ struct pic_tape_s {
   double dt;
   size_t cap;
   uint32_t C;
-  uint32_t** rcell;  // [n_steps] of [4][cap]: stage cells (StageRec layout, slots of the start of the step)
-  float2** rt;       // [n_steps] of [dim][4][cap]: stage x-hat, double-float
+  int kind;          // pic_tape_kind
+  int n_rec;         // stage-record sets: n_steps (stage tapes) or 1 (the replay's, checkpoint tapes)
+  uint32_t** rcell;  // [n_rec] of [4][cap]: stage cells (StageRec layout, slots of the start of the step)
+  float2** rt;       // [n_rec] of [dim][4][cap]: stage x-hat, double-float
+  double** x;        // checkpoint tapes: [n_steps] of [dim][cap], the store at the start of the step
+  float2** xhat;     //   [n_steps] of [dim][cap]
+  uint32_t** cell;   //   [n_steps] of [cap]
+  double* sink_x;    //   [dim][cap] the replayed step's new positions (discarded)
+  float2* sink_xhat; //   [dim][cap]
   uint32_t** perm;   // [n_steps] of [cap] (new slot -> old slot)
   uint32_t* n_dev;   // [n_steps + 1] particles at the start of each step (and at the end)
   // reverse-sweep work
@@ -169,6 +176,23 @@ __global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_ke
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) lam_out[a * cap + i] = make_float2(lam_x[a].hi, lam_x[a].lo);
+  }
+}
+
+// Checkpoint tapes: the step replayed from the store as it was at the start
+// of the step, for every particle then alive, by the forward's own
+// advect_particle (so the stage records are the forward's bit for bit); the
+// new positions go to a sink.
+template <int D, int RK>
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) replay_step_kernel(MeshView m, StoreView s, StoreView sink,
+                                                                                const uint32_t* __restrict__ n_start,
+                                                                                df dt, StageRec rec) {
+  const uint32_t n = *n_start;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int iters = 0;
+    unsigned flags = 0;
+    RecordHook hook{rec, i};
+    advect_particle_to<D, RK, false, false>(m, s, i, sink, i, s.cell[i], dt, iters, flags, hook);
   }
 }
 
@@ -320,10 +344,23 @@ static int grid_of(size_t n, int block) {
 }
 
 template <int D, int RK>
-static void launch_reverse(pic_tape_s* tp, const MeshView& m, const TapeStep& ts, const float2* lin, float2* lout,
-                           cudaStream_t st) {
+static void launch_reverse(pic_tape_s* tp, const MeshView& m, int step, const TapeStep& ts, const float2* lin,
+                           float2* lout, cudaStream_t st) {
   const float hi = (float)tp->dt;
   const df dtd = {hi, (float)(tp->dt - (double)hi)};
+  if (tp->kind == PIC_TAPE_CHECKPOINTS) {
+    StoreView s{}, sink{};
+    s.x = tp->x[step];
+    s.xhat = tp->xhat[step];
+    s.cell = tp->cell[step];
+    s.cap = tp->cap;
+    sink.x = tp->sink_x;
+    sink.xhat = tp->sink_xhat;
+    sink.cap = tp->cap;
+    replay_step_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, s, sink, tp->n_dev + step, dtd,
+                                                                     StageRec{tp->rcell[0], tp->rt[0], tp->cap});
+    count_launches(1);
+  }
   reverse_lambda_kernel<D, RK><<<grid_of(tp->cap, 128), 128, 0, st>>>(m, ts, tp->cap, dtd, lin, lout, tp->rec_cell,
                                                                        tp->rec_key, tp->rec_w, tp->parts->ctr);
 }
@@ -334,14 +371,24 @@ using namespace pic;
 
 extern "C" pic_status pic_destroy_tape(pic_tape tp) {
   if (!tp) return PIC_OK;
-  for (int s = 0; s < tp->n_steps; ++s) {
+  for (int s = 0; s < tp->n_rec; ++s) {
     if (tp->rcell) cudaFree(tp->rcell[s]);
     if (tp->rt) cudaFree(tp->rt[s]);
+  }
+  for (int s = 0; s < tp->n_steps; ++s) {
     if (tp->perm) cudaFree(tp->perm[s]);
+    if (tp->x) cudaFree(tp->x[s]);
+    if (tp->xhat) cudaFree(tp->xhat[s]);
+    if (tp->cell) cudaFree(tp->cell[s]);
   }
   free(tp->rcell);
   free(tp->rt);
   free(tp->perm);
+  free(tp->x);
+  free(tp->xhat);
+  free(tp->cell);
+  cudaFree(tp->sink_x);
+  cudaFree(tp->sink_xhat);
   cudaFree(tp->n_dev);
   cudaFree(tp->lam[0]);
   cudaFree(tp->lam[1]);
@@ -356,10 +403,12 @@ extern "C" pic_status pic_destroy_tape(pic_tape tp) {
   return PIC_OK;
 }
 
-extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
-                                        int n_steps, void* stream, pic_tape* out) {
+extern "C" pic_status pic_advect_record_tape(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                                             int n_steps, pic_tape_kind kind, void* stream, pic_tape* out) {
   if (!out) return (set_error("pic_advect_record: out is NULL"), PIC_ERR_ARG);
   *out = nullptr;
+  if (kind != PIC_TAPE_STAGES && kind != PIC_TAPE_CHECKPOINTS)
+    return (set_error("pic_advect_record: unknown tape kind %d", (int)kind), PIC_ERR_ARG);
   if (!parts || !mesh || parts->mesh != mesh || parts->dim != mesh->dim)
     return (set_error("pic_advect_record: bad handles"), PIC_ERR_ARG);
   if (!std::isfinite(dt)) return (set_error("pic_advect_record: dt not finite"), PIC_ERR_ARG);
@@ -379,16 +428,34 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   tp->dt = dt;
   tp->cap = parts->capacity;
   tp->C = mesh->C;
+  tp->kind = (int)kind;
+  const bool ckpt = kind == PIC_TAPE_CHECKPOINTS;
+  tp->n_rec = ckpt ? 1 : n_steps;
   const size_t cap = tp->cap, d = (size_t)tp->dim, rcap = kRecPerParticle * cap;
   const int NE = (tp->dim == 3 ? 27 : 9) * tp->dim;
-  tp->rcell = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
-  tp->rt = (float2**)calloc(n_steps, sizeof(float2*));
+  tp->rcell = (uint32_t**)calloc(tp->n_rec, sizeof(uint32_t*));
+  tp->rt = (float2**)calloc(tp->n_rec, sizeof(float2*));
   tp->perm = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
   bool ok = tp->rcell && tp->rt && tp->perm;
-  for (int s = 0; s < n_steps && ok; ++s) {
+  if (ckpt) {
+    tp->x = (double**)calloc(n_steps, sizeof(double*));
+    tp->xhat = (float2**)calloc(n_steps, sizeof(float2*));
+    tp->cell = (uint32_t**)calloc(n_steps, sizeof(uint32_t*));
+    ok = ok && tp->x && tp->xhat && tp->cell;
+    ok = ok && cudaMalloc(&tp->sink_x, sizeof(double) * d * cap) == cudaSuccess;
+    ok = ok && cudaMalloc(&tp->sink_xhat, sizeof(float2) * d * cap) == cudaSuccess;
+  }
+  for (int s = 0; s < tp->n_rec && ok; ++s) {
     ok = ok && cudaMalloc(&tp->rcell[s], sizeof(uint32_t) * rcap) == cudaSuccess;
     ok = ok && cudaMalloc(&tp->rt[s], sizeof(float2) * d * rcap) == cudaSuccess;
+  }
+  for (int s = 0; s < n_steps && ok; ++s) {
     ok = ok && cudaMalloc(&tp->perm[s], sizeof(uint32_t) * cap) == cudaSuccess;
+    if (ckpt) {
+      ok = ok && cudaMalloc(&tp->x[s], sizeof(double) * d * cap) == cudaSuccess;
+      ok = ok && cudaMalloc(&tp->xhat[s], sizeof(float2) * d * cap) == cudaSuccess;
+      ok = ok && cudaMalloc(&tp->cell[s], sizeof(uint32_t) * cap) == cudaSuccess;
+    }
   }
   ok = ok && cudaMalloc(&tp->n_dev, sizeof(uint32_t) * (n_steps + 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&tp->lam[0], sizeof(float2) * d * cap) == cudaSuccess;
@@ -409,11 +476,22 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   for (int s = 0; s < n_steps; ++s) {
     cudaError_t e = cudaMemcpyAsync(tp->n_dev + s, &parts->ctr->n_alive, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st);
+    if (ckpt) {
+      const int c = parts->cur;
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tp->x[s], parts->x[c], sizeof(double) * d * cap, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tp->xhat[s], parts->xhat[c], sizeof(float2) * d * cap, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tp->cell[s], parts->cell[c], sizeof(uint32_t) * cap, cudaMemcpyDeviceToDevice, st);
+    }
     if (e != cudaSuccess) {
       pic_destroy_tape(tp);
-      return cuda_fail(e, "pic_advect_record: count");
+      return cuda_fail(e, "pic_advect_record: checkpoint");
     }
-    launch_advect_record(parts, m, dt, (int)integrator, StageRec{tp->rcell[s], tp->rt[s], cap}, st);
+    // a checkpoint tape keeps one record set, which the sweep's replay rewrites
+    launch_advect_record(parts, m, dt, (int)integrator, StageRec{tp->rcell[ckpt ? 0 : s], tp->rt[ckpt ? 0 : s], cap},
+                         st);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       pic_destroy_tape(tp);
@@ -439,6 +517,11 @@ extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, doub
   return PIC_OK;
 }
 
+extern "C" pic_status pic_advect_record(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
+                                        int n_steps, void* stream, pic_tape* out) {
+  return pic_advect_record_tape(parts, mesh, dt, integrator, n_steps, PIC_TAPE_STAGES, stream, out);
+}
+
 extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, double* dL_dU, double* dL_dx0,
                                        void* stream) {
   if (!tp || !dL_dxfinal || !dL_dU) return (set_error("pic_tape_adjoint: null argument"), PIC_ERR_ARG);
@@ -454,8 +537,8 @@ extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, do
   const SortScratch sc = sort_scratch_layout(tp->sort_scratch, rcap, tp->C);
   for (int s = tp->n_steps - 1; s >= 0; --s) {
     TapeStep ts;
-    ts.rcell = tp->rcell[s];
-    ts.rt = tp->rt[s];
+    ts.rcell = tp->rcell[tp->kind == PIC_TAPE_CHECKPOINTS ? 0 : s];
+    ts.rt = tp->rt[tp->kind == PIC_TAPE_CHECKPOINTS ? 0 : s];
     ts.perm = tp->perm[s];
     ts.n_next = tp->n_dev + s + 1;
     PIC_CUDA(cudaMemsetAsync(tp->lam[1 - cur], 0, sizeof(float2) * d * cap, st));
@@ -463,13 +546,13 @@ extern "C" pic_status pic_tape_adjoint(pic_tape tp, const double* dL_dxfinal, do
     const float2* lin = tp->lam[cur];
     float2* lout = tp->lam[1 - cur];
     if (tp->dim == 2) {
-      if (tp->integrator == 1) launch_reverse<2, 1>(tp, m, ts, lin, lout, st);
-      else if (tp->integrator == 2) launch_reverse<2, 2>(tp, m, ts, lin, lout, st);
-      else launch_reverse<2, 4>(tp, m, ts, lin, lout, st);
+      if (tp->integrator == 1) launch_reverse<2, 1>(tp, m, s, ts, lin, lout, st);
+      else if (tp->integrator == 2) launch_reverse<2, 2>(tp, m, s, ts, lin, lout, st);
+      else launch_reverse<2, 4>(tp, m, s, ts, lin, lout, st);
     } else {
-      if (tp->integrator == 1) launch_reverse<3, 1>(tp, m, ts, lin, lout, st);
-      else if (tp->integrator == 2) launch_reverse<3, 2>(tp, m, ts, lin, lout, st);
-      else launch_reverse<3, 4>(tp, m, ts, lin, lout, st);
+      if (tp->integrator == 1) launch_reverse<3, 1>(tp, m, s, ts, lin, lout, st);
+      else if (tp->integrator == 2) launch_reverse<3, 2>(tp, m, s, ts, lin, lout, st);
+      else launch_reverse<3, 4>(tp, m, s, ts, lin, lout, st);
     }
     count_launches(1);
     PIC_CUDA(cudaGetLastError());

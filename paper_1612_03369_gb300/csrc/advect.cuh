@@ -131,6 +131,19 @@ struct NoHook {
   __device__ __forceinline__ void stage(int, uint32_t, const df*) {}
 };
 
+// Writes stage p's cell and x-hat of the particle in slot i to the stage
+// records (the StageRec layout).
+struct RecordHook {
+  StageRec r;
+  uint32_t i;
+  template <int D>
+  __device__ __forceinline__ void stage(int p, uint32_t K, const df* t) {
+    r.cell[(size_t)p * r.cap + i] = K;
+#pragma unroll
+    for (int a = 0; a < D; ++a) r.t[((size_t)a * 4 + p) * r.cap + i] = make_float2(t[a].hi, t[a].lo);
+  }
+};
+
 // One time step of particle i of store s in mesh m, starting in cell K.
 // TWO: the mesh carries a second field (time interpolation).
 // Writes the new x and x-hat in place when the particle survives and returns

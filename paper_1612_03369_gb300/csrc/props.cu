@@ -27,17 +27,6 @@ struct OdeArgs {
   df alpha, beta;
 };
 
-struct RecordHook {
-  StageRec r;
-  uint32_t i;
-  template <int D>
-  __device__ __forceinline__ void stage(int p, uint32_t K, const df* t) {
-    r.cell[(size_t)p * r.cap + i] = K;
-#pragma unroll
-    for (int a = 0; a < D; ++a) r.t[((size_t)a * 4 + p) * r.cap + i] = make_float2(t[a].hi, t[a].lo);
-  }
-};
-
 // Phase 1: the particle step of pic_advect (the same advect_particle, so
 // positions, cells and order are bit for bit those of pic_advect), leaving
 // each stage's (cell, x-hat) behind.

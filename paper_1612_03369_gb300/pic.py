@@ -21,6 +21,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CAPACITY, PIC_ERR_CUDA, PIC_ERR_NOT_CO
 PIC_EULER, PIC_RK2, PIC_RK4 = 1, 2, 4
 PIC_FP64, PIC_FP32_BASIS = 0, 1
 PIC_AVG_ARITHMETIC, PIC_AVG_GEOMETRIC, PIC_AVG_HARMONIC = 0, 1, 2
+PIC_TAPE_STAGES, PIC_TAPE_CHECKPOINTS = 0, 1
 PIC_STATUS_NEWTON_NONCONV, PIC_STATUS_CAPACITY, PIC_STATUS_GLOBAL_SEARCH, PIC_STATUS_BOUNDS = 1, 2, 4, 8
 LOST = 0xFFFFFFFF
 
@@ -43,6 +44,7 @@ SIGNATURES = {
     "pic_advect_properties": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
     "pic_locate": (_I, [_P, _P, _P]),
     "pic_advect_record": (_I, [_P, _P, _F64, _I, _I, _P, _P]),
+    "pic_advect_record_tape": (_I, [_P, _P, _F64, _I, _I, _I, _P, _P]),
     "pic_tape_adjoint": (_I, [_P, _P, _P, _P, _P]),
     "pic_destroy_tape": (_I, [_P]),
     "pic_rebin": (_I, [_P, _P]),
@@ -205,6 +207,14 @@ def pic_advect_record(parts: int, mesh: int, dt: float, integrator: int, n_steps
     out = C.c_void_p()
     _check(_lib.pic_advect_record(parts, mesh, float(dt), int(integrator), int(n_steps), _stream(stream), C.byref(out)),
            "pic_advect_record")
+    return out.value
+
+
+def pic_advect_record_tape(parts: int, mesh: int, dt: float, integrator: int, n_steps: int, kind: int,
+                           stream=None) -> int:
+    out = C.c_void_p()
+    _check(_lib.pic_advect_record_tape(parts, mesh, float(dt), int(integrator), int(n_steps), int(kind),
+                                       _stream(stream), C.byref(out)), "pic_advect_record_tape")
     return out.value
 
 
@@ -537,18 +547,20 @@ def _advect_function():
     import torch
 
     class AdvectFunction(torch.autograd.Function):
-        """x_final, ids = AdvectFunction.apply(U, parts, dt, integrator, n_steps)
+        """x_final, ids = AdvectFunction.apply(U, parts, dt, integrator, n_steps, tape_kind)
 
         Forward: sets the mesh velocity to U ([dim][nnodes] float64, CUDA) and
         advances `parts` n_steps with a recorded tape; returns the final
         positions [dim][N_final] and ids [N_final] in store order.
         Backward: the adjoint sweep (pic_tape_adjoint) turns dL/dx_final into
-        dL/dU.  The particle store is advanced in place by the forward."""
+        dL/dU.  The particle store is advanced in place by the forward.
+        tape_kind: PIC_TAPE_STAGES (faster sweep) or PIC_TAPE_CHECKPOINTS
+        (about half the tape memory); the gradient is the same bit for bit."""
 
         @staticmethod
-        def forward(ctx, U, parts, dt, integrator, n_steps):
+        def forward(ctx, U, parts, dt, integrator, n_steps, tape_kind):
             pic_set_velocity_dofs(parts.mesh.h, U.detach().contiguous())
-            tape = _Tape(pic_advect_record(parts.h, parts.mesh.h, dt, integrator, n_steps))
+            tape = _Tape(pic_advect_record_tape(parts.h, parts.mesh.h, dt, integrator, n_steps, tape_kind))
             st = parts.export()
             ctx.tape = tape
             ctx.U_shape = U.shape
@@ -559,15 +571,17 @@ def _advect_function():
         def backward(ctx, grad_x, grad_ids):
             dU = torch.empty(ctx.U_shape, dtype=torch.float64, device="cuda")
             pic_tape_adjoint(ctx.tape.h, grad_x.contiguous(), dU)
-            return dU, None, None, None, None
+            return dU, None, None, None, None, None
 
     return AdvectFunction
 
 
-def advect_differentiable(U, parts: "Particles", dt: float, integrator: int = PIC_RK4, n_steps: int = 1):
+def advect_differentiable(U, parts: "Particles", dt: float, integrator: int = PIC_RK4, n_steps: int = 1,
+                          tape_kind: int = 0):
     """Differentiable advection: returns (x_final [dim][N], ids [N]); gradients
-    flow from x_final back to the nodal velocities U."""
-    return _advect_function().apply(U, parts, dt, integrator, n_steps)
+    flow from x_final back to the nodal velocities U.  tape_kind as in
+    pic_advect_record_tape (PIC_TAPE_STAGES or PIC_TAPE_CHECKPOINTS)."""
+    return _advect_function().apply(U, parts, dt, integrator, n_steps, int(tape_kind))
 
 
 # ------------------------------------------------------------- ensemble --

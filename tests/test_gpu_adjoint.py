@@ -10,9 +10,9 @@ import gpu_helpers as H
 pytestmark = pytest.mark.gpu
 
 # The GPU sums the same per-stage contributions as the oracle, in another
-# order (per cell, then per node) and with stage points recomputed from
-# double-float checkpoints; differences stay at rounding level, bounded here
-# relative to the largest gradient entry.
+# order (per cell, then per node), with the forward's double-float stage
+# points and double-float G and lambda; differences stay at rounding level,
+# bounded here relative to the largest gradient entry.
 TOL_GRAD = 1e-11
 
 
@@ -30,11 +30,14 @@ def _targets_by_id(wl, n_total, x_like, seed=3):
     return x_like + h * g.standard_normal(x_like.shape)
 
 
-def _gpu_grad(P, wl, steps, dt, integrator, targets_by_id, weight_by_id=None):
+def _gpu_grad(P, wl, steps, dt, integrator, targets_by_id, weight_by_id=None, kind=None, dx0=None):
     import torch
 
     mesh, parts = H.gpu_seed(wl, n_props=0)
-    tape = P.pic_advect_record(parts.h, mesh.h, dt, integrator, steps)
+    if kind is None:
+        tape = P.pic_advect_record(parts.h, mesh.h, dt, integrator, steps)
+    else:
+        tape = P.pic_advect_record_tape(parts.h, mesh.h, dt, integrator, steps, kind)
     st = parts.export()
     ids = st["id"].cpu().numpy()
     x = st["x"].cpu().numpy()
@@ -43,7 +46,7 @@ def _gpu_grad(P, wl, steps, dt, integrator, targets_by_id, weight_by_id=None):
     if weight_by_id is not None:
         lam = lam * weight_by_id[ids][None, :]
     dU = torch.empty((wl.dim, wl.U.shape[1]), dtype=torch.float64, device="cuda")
-    P.pic_tape_adjoint(tape, torch.as_tensor(np.ascontiguousarray(lam), device="cuda"), dU)
+    P.pic_tape_adjoint(tape, torch.as_tensor(np.ascontiguousarray(lam), device="cuda"), dU, dx0)
     P.pic_destroy_tape(tape)
     loss = float((r * r).sum())
     return loss, dU.cpu().numpy(), ids, x, parts
@@ -81,6 +84,44 @@ def test_adjoint_is_reproducible(P):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("case", ["3d_rk4", "2d_rk2", "3d_losses"])
+def test_checkpoint_tape_equals_stage_tape(P, case):
+    """A checkpoint tape replays each step from the store at its start with
+    the forward's own particle step, so dL/dU and dL/dx0 equal those of the
+    stage tape bit for bit, also when particles leave through the walls."""
+    import torch
+
+    if case == "3d_rk4":
+        wl, steps, dt, rk = W.curl_cube(6, 5, 4, 5, n_props=0), 4, None, 4
+    elif case == "2d_rk2":
+        wl, steps, dt, rk = W.c5_member(9, 31), 3, None, 2
+    else:
+        wl, steps, dt, rk = W.curl_cube(6, 6, 3, 9, n_props=0), 3, "12x", 4
+    dt = 12 * wl.dt if dt == "12x" else wl.dt  # CFL ~6: about a sixth of the particles leave
+    tg = _targets_by_id(wl, wl.n_particles, np.full((wl.dim, wl.n_particles), 0.5))
+    out = {}
+    for kind in (P.PIC_TAPE_STAGES, P.PIC_TAPE_CHECKPOINTS):
+        dx0 = torch.empty((wl.dim, wl.n_particles), dtype=torch.float64, device="cuda")
+        L, g, ids, x, parts = _gpu_grad(P, wl, steps, dt, rk, tg, kind=kind, dx0=dx0)
+        out[kind] = (L, g, ids, x, dx0.cpu().numpy(), parts.state()[1])
+    a, b = out[P.PIC_TAPE_STAGES], out[P.PIC_TAPE_CHECKPOINTS]
+    assert a[0] == b[0]
+    for k in (1, 2, 3, 4):
+        np.testing.assert_array_equal(a[k], b[k])
+    if case == "3d_losses":
+        assert a[5] > 0  # some particles were lost
+    assert np.abs(a[1]).max() > 0
+
+
+def test_tape_kind_errors(P):
+    wl = W.curl_cube(3, 2, 2, 2, n_props=0)
+    mesh, parts = H.gpu_seed(wl, n_props=0)
+    with pytest.raises(P.PicError):
+        P.pic_advect_record_tape(parts.h, mesh.h, wl.dt, 4, 2, 7)
+    with pytest.raises(P.PicError):
+        P.pic_advect_record_tape(parts.h, mesh.h, wl.dt, 4, 0, P.PIC_TAPE_CHECKPOINTS)
+
+
 def test_autograd_function(P):
     import torch
 
@@ -95,6 +136,12 @@ def test_autograd_function(P):
     loss.backward()
     assert float(loss.detach()) == pytest.approx(ref_loss, rel=1e-14)
     assert np.array_equal(U.grad.cpu().numpy(), ref_g)
+    # the same through a checkpoint tape
+    mesh2, parts2 = H.gpu_seed(wl, n_props=0)
+    U2 = torch.as_tensor(wl.U, device="cuda").clone().requires_grad_(True)
+    x2, ids2 = P.advect_differentiable(U2, parts2, wl.dt, P.PIC_RK4, 3, tape_kind=P.PIC_TAPE_CHECKPOINTS)
+    (((x2 - torch.as_tensor(tg, device="cuda")[:, ids2]) ** 2).sum()).backward()
+    assert np.array_equal(U2.grad.cpu().numpy(), ref_g)
 
 
 def test_c4_full_size(P, oracle_mod):
