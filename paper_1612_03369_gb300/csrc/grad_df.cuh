@@ -1,7 +1,7 @@
 // grad_df.cuh -- the velocity gradient G = du_h/dx = (du_h/dx-hat) J^{-1} at a
 // located point, in double-float arithmetic on the FP32 pipe (the FP64 pipe
 // of GB300 issues ~1/75 of the FP32 rate).  Used by the property ODEs of
-// Sec. 2.6 and by the adjoint sweep; G is handed back in FP64.
+// Sec. 2.6 and by the adjoint sweep.
 //
 //   du/dx-hat   from the cell's monomial coefficients about its centre
 //               (u_c = sum c_pqr s0^p s1^q s2^r, s = x-hat - 1/2, so
@@ -179,17 +179,6 @@ __device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t
       for (int j = 0; j < D; ++j) acc_mad(s, Gu[c][j], Ji[j][q]);
       G[c][q] = acc_result(s);
     }
-}
-
-// The same, handed back in FP64.
-template <int D>
-__device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], double G[D][D]) {
-  df g[D][D];
-  velocity_gradient_df<D>(m, K, t, g);
-#pragma unroll
-  for (int c = 0; c < D; ++c)
-#pragma unroll
-    for (int q = 0; q < D; ++q) G[c][q] = df_to_double(g[c][q]);
 }
 
 // sqrt(a), a >= 0: FP32 root refined by one Newton step in double-float.
