@@ -8,7 +8,7 @@
 //   counts[K]   particles whose new cell is K (filled by the locate kernel)
 //   scan        cell_off = exclusive prefix sum of counts; cursor = cell_off
 //   scatter     (id, old slot) of each particle to a free slot of its cell
-//   rank        warp per cell: slot of each particle = its rank by id
+//   rank        slot of each particle = segment start + its rank by id
 //   gather      every field copied from the old slot to the new slot
 // The result is a function of the particle set alone (no dependence on the
 // order the atomics of the scatter were served in).
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) scatter_keys_kernel(const uint32_t* __res
                 gridDim.x * blockDim.x);
 }
 
-// Warp per cell rank by id.  cell_out may be NULL.  When publish_dst is
+// Rank by id within each cell.  cell_out may be NULL.  When publish_dst is
 // given, block 0 copies *publish_src there (the new particle count).
 __global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
                                                          const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,

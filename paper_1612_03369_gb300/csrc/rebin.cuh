@@ -7,7 +7,7 @@
 //          blockDim.x * kScanItems cells: tile sums, one block scans them,
 //          then every tile applies its offset
 //   scatter (id, old slot) of each particle to a free slot of its new cell
-//   rank   warp per cell: new slot = segment start + rank of the id
+//   rank   new slot = segment start + rank of the id among the cell's ids
 //   gather every field copied from its old slot to its new slot
 #pragma once
 
@@ -140,35 +140,54 @@ __device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_
   }
 }
 
-// Warp per cell (warp w of nw): new slot = segment start + number of smaller
-// ids in the segment (ids are unique within a cell).
+// New slot = segment start + number of smaller ids in the segment (ids are
+// unique within a cell).  Warp w of nw takes G consecutive cells at a time
+// (G a power of two <= 32, the largest with C / G >= nw, so that small meshes
+// still spread over all warps): lane q < G holds the segment start of cell
+// K0 + q, and the particles of the G segments are ranked 32 at a time, each
+// lane finding its slot's cell among the G starts (a shuffle binary search)
+// and counting the smaller ids of that segment.  All lanes work whatever the
+// cells' sizes, where one warp per cell left most lanes idle at ~10-20
+// particles per cell.
 __device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off, const uint64_t* __restrict__ key_id,
                                            const uint32_t* __restrict__ key_src, uint32_t* __restrict__ perm,
                                            uint32_t* __restrict__ cell_out, uint32_t C, size_t cap,
                                            unsigned int* __restrict__ status, uint32_t w, uint32_t nw) {
   const int lane = threadIdx.x & 31;
-  for (uint32_t K = w; K < C; K += nw) {
-    const uint32_t beg = cell_off[K], end = cell_off[K + 1];
-    if (end > cap || beg > end) {
+  const uint32_t per_warp = C / (nw ? nw : 1u);
+  uint32_t G = 1;
+  while (G < 32u && 2u * G <= per_warp) G *= 2u;
+  for (uint32_t K0 = w * G; K0 < C; K0 += nw * G) {
+    const int nc = (C - K0) < G ? (int)(C - K0) : (int)G;  // cells in this group
+    const uint32_t start = cell_off[K0 + (uint32_t)(lane < nc ? lane : nc)];  // lanes >= nc: the group's end
+    const uint32_t end_all = cell_off[K0 + (uint32_t)nc];
+    const uint32_t beg_all = __shfl_sync(0xffffffffu, start, 0);
+    // segment starts must be non-decreasing and inside the store
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, start, 1);
+    const bool bad = end_all > cap || (lane > 0 && lane < nc && start < prev) || (lane == nc - 1 && end_all < start);
+    if (__any_sync(0xffffffffu, bad)) {
       if (lane == 0) atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
     }
-    const uint32_t n = end - beg;
-    for (uint32_t e0 = 0; e0 < n; e0 += 32) {
-      const uint32_t e = e0 + lane;
-      const uint64_t my = e < n ? key_id[beg + e] : ~0ull;
-      uint32_t rank = 0;
-      for (uint32_t f0 = 0; f0 < n; f0 += 32) {
-        const uint64_t other = (f0 + lane < n) ? key_id[beg + f0 + lane] : ~0ull;
-        const uint32_t lim = (n - f0) < 32u ? (n - f0) : 32u;
-        for (uint32_t q = 0; q < lim; ++q) {
-          const uint64_t o = __shfl_sync(0xffffffffu, other, q);
-          rank += (o < my) ? 1u : 0u;
-        }
+    for (uint32_t j0 = beg_all; j0 < end_all; j0 += 32u) {
+      const uint32_t j = j0 + lane;
+      // c = the last of the nc cells whose segment starts at or before j
+      int c = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const uint32_t sc = __shfl_sync(0xffffffffu, start, (c + step) & 31);
+        if (c + step < nc && sc <= j) c += step;
       }
-      if (e < n) {
-        perm[beg + rank] = key_src[beg + e];
-        if (cell_out) cell_out[beg + rank] = K;
+      const uint32_t beg = __shfl_sync(0xffffffffu, start, c);
+      const uint32_t nxt = __shfl_sync(0xffffffffu, start, (c + 1) & 31);
+      const uint32_t end = c + 1 < nc ? nxt : end_all;
+      if (j < end_all) {
+        const uint64_t my = key_id[j];
+        uint32_t rank = 0;
+#pragma unroll 4
+        for (uint32_t f = beg; f < end; ++f) rank += (key_id[f] < my) ? 1u : 0u;
+        perm[beg + rank] = key_src[j];
+        if (cell_out) cell_out[beg + rank] = K0 + (uint32_t)c;
       }
     }
   }
