@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "advect.cuh"
+#include "rebin.cuh"
 
 namespace pic {
 
@@ -27,6 +28,7 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(Mesh
     const uint32_t j = base + threadIdx.x;
     int iters = 0;
     unsigned flags = 0, lost = 0, steps = 0;
+    uint32_t Kc = PIC_LOST;  // the new cell to count
     if (j < n) {
       steps = 1;
       uint32_t i = j, K;
@@ -46,11 +48,10 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(Mesh
       }
       const uint32_t Kn = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, iters, flags);
       cell_new[j] = Kn;
-      if (Kn != PIC_LOST)
-        atomicAdd(counts + Kn, 1u);
-      else
-        lost = 1;
+      Kc = Kn;
+      lost = Kn == PIC_LOST ? 1u : 0u;
     }
+    (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
   }
 }

@@ -120,11 +120,12 @@ __device__ __forceinline__ void load_ensemble(EnsShared& sh, const MeshView* vie
 // of s advances in place (d is s); otherwise slot j of d takes particle
 // perm[j] of s, whose global cell the previous rebin left in d.cell[j], with
 // its id and properties (the previous step's order applied on the way).
+// Returns the new global cell (PIC_LOST if none), which the caller counts.
 template <int D, int RK>
-__device__ __forceinline__ void ensemble_particle(const EnsShared& sh, int P, const StoreView& s, const StoreView& d,
-                                                  const uint32_t* __restrict__ perm, uint32_t j,
-                                                  uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts,
-                                                  int& iters, unsigned& flags, unsigned& lost) {
+__device__ __forceinline__ uint32_t ensemble_particle(const EnsShared& sh, int P, const StoreView& s,
+                                                      const StoreView& d, const uint32_t* __restrict__ perm, uint32_t j,
+                                                      uint32_t* __restrict__ cell_new, int& iters, unsigned& flags,
+                                                      unsigned& lost) {
   uint32_t i = j, g;
   if (perm) {
     i = perm[j];
@@ -150,10 +151,8 @@ __device__ __forceinline__ void ensemble_particle(const EnsShared& sh, int P, co
     flags |= kFlagBounds;
   }
   cell_new[j] = out;
-  if (out != PIC_LOST)
-    atomicAdd(counts + out, 1u);
-  else
-    lost = 1;
+  if (out == PIC_LOST) lost = 1;
+  return out;
 }
 
 template <int D, int RK>
@@ -168,10 +167,12 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_adv
     const uint32_t i = b0 + threadIdx.x;
     int iters = 0;
     unsigned flags = 0, lost = 0, steps = 0;
+    uint32_t Kc = PIC_LOST;
     if (i < n) {
       steps = 1;
-      ensemble_particle<D, RK>(sh, P, s, d, perm, i, cell_new, counts, iters, flags, lost);
+      Kc = ensemble_particle<D, RK>(sh, P, s, d, perm, i, cell_new, iters, flags, lost);
     }
+    (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
   }
 }
@@ -229,10 +230,12 @@ __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_per
         const uint32_t i = b0 + threadIdx.x;
         int iters = 0;
         unsigned flags = 0, lost = 0, steps = 0;
+        uint32_t Kc = PIC_LOST;
         if (i < t1) {
           steps = 1;
-          ensemble_particle<D, RK>(sh, A.P, src, dst, perm, i, A.cell_new, A.counts, iters, flags, lost);
+          Kc = ensemble_particle<D, RK>(sh, A.P, src, dst, perm, i, A.cell_new, iters, flags, lost);
         }
+        (void)aggregated_increment(A.counts, Kc, Kc != PIC_LOST);
         flush_counters(A.ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u,
                        flags);
       }

@@ -18,6 +18,7 @@
 
 #include "advect.cuh"
 #include "grad_df.cuh"
+#include "rebin.cuh"
 
 namespace pic {
 
@@ -42,16 +43,16 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kern
     const uint32_t i = base + threadIdx.x;
     int iters = 0;
     unsigned flags = 0, lost = 0, steps = 0;
+    uint32_t Kc = PIC_LOST;  // the new cell to count
     if (i < n) {
       steps = 1;
       RecordHook hook{rec, i};
       const uint32_t Kn = advect_particle<D, RK, false, false>(m, s, i, s.cell[i], dt, iters, flags, hook);
       cell_new[i] = Kn;
-      if (Kn != PIC_LOST)
-        atomicAdd(counts + Kn, 1u);
-      else
-        lost = 1;
+      Kc = Kn;
+      lost = Kn == PIC_LOST ? 1u : 0u;
     }
+    (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
   }
 }

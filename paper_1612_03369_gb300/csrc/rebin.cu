@@ -135,15 +135,19 @@ pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
 __global__ void identity_cells_kernel(const uint32_t* __restrict__ cell, uint32_t* __restrict__ cell_new,
                                       uint32_t* __restrict__ counts, uint32_t C, DevCounters* __restrict__ ctr) {
   const uint32_t n = ctr->n_alive;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t K = cell[i];
-    if (K >= C) {
-      latch_status(ctr, PIC_STATUS_BOUNDS);
-      K = PIC_LOST;
-    } else {
-      atomicAdd(counts + K, 1u);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gridDim.x * blockDim.x) {
+    const uint32_t i = base + lane;
+    uint32_t K = PIC_LOST;
+    if (i < n) {
+      K = cell[i];
+      if (K >= C) {
+        latch_status(ctr, PIC_STATUS_BOUNDS);
+        K = PIC_LOST;
+      }
+      cell_new[i] = K;
     }
-    cell_new[i] = K;
+    (void)aggregated_increment(counts, K, K != PIC_LOST);
   }
 }
 
@@ -151,12 +155,12 @@ __global__ void identity_cells_kernel(const uint32_t* __restrict__ cell, uint32_
 // entries other than PIC_LOST that are >= C are flagged).
 __global__ void count_cells_kernel(const uint32_t* __restrict__ cell, uint32_t n, uint32_t C,
                                    uint32_t* __restrict__ counts, unsigned int* __restrict__ status) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t K = cell[i];
-    if (K < C)
-      atomicAdd(counts + K, 1u);
-    else if (K != PIC_LOST)
-      atomicOr(status, PIC_STATUS_BOUNDS);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t base = blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += gridDim.x * blockDim.x) {
+    const uint32_t i = base + lane;
+    const uint32_t K = i < n ? cell[i] : PIC_LOST;
+    if (K != PIC_LOST && K >= C) atomicOr(status, PIC_STATUS_BOUNDS);
+    (void)aggregated_increment(counts, K, K < C);
   }
 }
 

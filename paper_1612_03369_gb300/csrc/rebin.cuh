@@ -118,19 +118,37 @@ __device__ __forceinline__ void scan_phase_apply(const uint32_t* __restrict__ in
   }
 }
 
-// (id, old slot) of every located particle i < n into a free slot of its new cell.
+// Warp-aggregated increment of ctr[K]: the lanes of a warp holding the same K
+// (all 32 lanes call this; lanes with take == false only vote) share one
+// atomic, issued by the lowest of them.  Returns the counter's old value plus
+// the lane's rank among its peers.  The particles arrive sorted by their old
+// cell and most stay in it, so a warp usually holds two or three distinct
+// cells: a few atomics per warp instead of 32 on the same addresses.
+__device__ __forceinline__ uint32_t aggregated_increment(uint32_t* __restrict__ ctr, uint32_t K, bool take) {
+  const unsigned peers = __match_any_sync(0xffffffffu, take ? K : 0xFFFFFFFFu);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (take && lane == leader) base = atomicAdd(ctr + K, (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
+// (id, old slot) of every located particle i < n into a free slot of its new
+// cell.  first - lane and stride must be multiples of 32 (whole warps), so
+// that every lane of a warp takes part in the aggregated increments.
 __device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_new, const uint64_t* __restrict__ id,
                                               uint32_t* __restrict__ cursor, uint64_t* __restrict__ key_id,
                                               uint32_t* __restrict__ key_src, uint32_t C, size_t cap, uint32_t n,
                                               unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
-  for (uint32_t i = first; i < n; i += stride) {
-    const uint32_t K = cell_new[i];
-    if (K == PIC_LOST) continue;
-    if (K >= C) {
-      atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
-    }
-    const uint32_t slot = atomicAdd(cursor + K, 1u);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t base = first - lane; base < n; base += stride) {
+    const uint32_t i = base + lane;
+    const uint32_t K = i < n ? cell_new[i] : PIC_LOST;
+    if (K != PIC_LOST && K >= C) atomicOr(status, PIC_STATUS_BOUNDS);
+    const bool take = K < C;
+    const uint32_t slot = aggregated_increment(cursor, K, take);
+    if (!take) continue;
     if (slot >= cap) {
       atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
