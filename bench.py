@@ -66,7 +66,7 @@ def advect_bytes(dim: int, ppc: float, n_props: int, xhat_bytes: int = 8) -> flo
 # flops executed per particle-step (FFMA counted as 2) and DRAM bytes per
 # particle per launch.  They describe that kernel on that workload only.
 ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 9074.6
-ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 1563.81e6 / 5242880
+ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 1566.81e6 / 5242880
 # FP32 peak derived from unit counts and the maximum SM clock: 152 SMs x 128
 # FP32 lanes x 2 flops (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
