@@ -35,13 +35,42 @@ __device__ __forceinline__ df df_recip(df a) {
   return fast_two_sum(r, __fmul_rn(r, e));
 }
 
+// One coefficient slice (the nine c_pq r of a fixed r, index 3 q + p, as
+// q2_eval_df reads them) at s0, s1: its value g and its derivatives g0 along
+// s0 and g1 along s1.  Along s0 each row q gives its value h and derivative
+// h' = c_1 + 2 c_2 s0; along s1 the rows combine the same way.
+__device__ __forceinline__ void grad_slice_df(const float4* __restrict__ sl, df s0, df s1, df& g, df& g0, df& g1) {
+  float f[20];  // ten high parts, then ten low parts
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const float4 v = __ldg(sl + k);
+    f[4 * k] = v.x;
+    f[4 * k + 1] = v.y;
+    f[4 * k + 2] = v.z;
+    f[4 * k + 3] = v.w;
+  }
+  df c[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) c[e] = df_make(f[e], f[10 + e]);
+  df h[3], h0[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    h[q] = df_horner(df_horner(c[3 * q + 2], s0, c[3 * q + 1]), s0, c[3 * q]);
+    h0[q] = df_horner(df_scale2(c[3 * q + 2], 2.0f), s0, c[3 * q + 1]);
+  }
+  g = df_horner(df_horner(h[2], s1, h[1]), s1, h[0]);
+  g0 = df_horner(df_horner(h0[2], s1, h0[1]), s1, h0[0]);
+  g1 = df_horner(df_scale2(h[2], 2.0f), s1, h[1]);
+}
+
 // Gu[c][j] = d u_c / d t_j in cell K at double-float reference coordinates
-// t, from the coefficient slices q2_eval_df reads (slice r holds the nine
-// c_pq r, index 3 q + p).  Along s0 each row (q, r) gives its value h and
-// derivative h' = c_1 + 2 c_2 s0; along s1 each slice gives its value g and
-// the derivatives g0 (of the h') and g1 (of the h); along s2 the slices
-// combine the same way.  47 double-float Horner steps per component.
-template <int D>
+// t, from the cell's coefficient slices (u_c = sum_r slice_r(s0, s1) s2^r).
+// Along s2 the slices combine as d0 = sum g0_r s2^r, d1 = sum g1_r s2^r,
+// d2 = g_1 + 2 g_2 s2: 47 double-float Horner steps per component.
+// ROLLED takes one slice per loop iteration and combines them by Horner's
+// scheme with its derivative recurrence (one step more per component, a
+// third of the code): for kernels whose instruction footprint is the limit.
+template <int D, bool ROLLED = false>
 __device__ __forceinline__ void q2_grad_mono_df(const float4* __restrict__ Qc, uint32_t K, const df t[D],
                                                 df Gu[D][D]) {
   constexpr int NS = (D == 3 ? 3 : 1);
@@ -52,38 +81,40 @@ __device__ __forceinline__ void q2_grad_mono_df(const float4* __restrict__ Qc, u
 #pragma unroll 1
   for (int comp = 0; comp < D; ++comp) {
     const float4* cq = cell + comp * (5 * NS);
-    df g[NS], g0[NS], g1[NS];
-#pragma unroll
-    for (int r = 0; r < NS; ++r) {
-      float f[20];  // ten high parts, then ten low parts
-#pragma unroll
-      for (int k = 0; k < 5; ++k) {
-        const float4 v = __ldg(cq + 5 * r + k);
-        f[4 * k] = v.x;
-        f[4 * k + 1] = v.y;
-        f[4 * k + 2] = v.z;
-        f[4 * k + 3] = v.w;
+    if constexpr (ROLLED && D == 3) {
+      // highest slice first: A0, A1 gather the s0- and s1-derivatives, V the
+      // values and Dz the derivative of V along s2
+      df A0 = df_make(0.f, 0.f), A1 = A0, V = A0, Dz = A0;
+#pragma unroll 1
+      for (int r = NS - 1; r >= 0; --r) {
+        df g, g0, g1;
+        grad_slice_df(cq + 5 * r, s[0], s[1], g, g0, g1);
+        if (r == NS - 1) {
+          A0 = g0;
+          A1 = g1;
+          V = g;
+        } else {
+          Dz = (r == NS - 2) ? V : df_horner(Dz, s[2], V);
+          A0 = df_horner(A0, s[2], g0);
+          A1 = df_horner(A1, s[2], g1);
+          if (r > 0) V = df_horner(V, s[2], g);
+        }
       }
-      df c[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) c[e] = df_make(f[e], f[10 + e]);
-      df h[3], h0[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        h[q] = df_horner(df_horner(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
-        h0[q] = df_horner(df_scale2(c[3 * q + 2], 2.0f), s[0], c[3 * q + 1]);
-      }
-      g[r] = df_horner(df_horner(h[2], s[1], h[1]), s[1], h[0]);
-      g0[r] = df_horner(df_horner(h0[2], s[1], h0[1]), s[1], h0[0]);
-      g1[r] = df_horner(df_scale2(h[2], 2.0f), s[1], h[1]);
-    }
-    if constexpr (D == 3) {
-      Gu[comp][0] = df_norm(df_horner(df_horner(g0[2], s[2], g0[1]), s[2], g0[0]));
-      Gu[comp][1] = df_norm(df_horner(df_horner(g1[2], s[2], g1[1]), s[2], g1[0]));
-      Gu[comp][2] = df_norm(df_horner(df_scale2(g[2], 2.0f), s[2], g[1]));
+      Gu[comp][0] = df_norm(A0);
+      Gu[comp][1] = df_norm(A1);
+      Gu[comp][2] = df_norm(Dz);
     } else {
-      Gu[comp][0] = df_norm(g0[0]);
-      Gu[comp][1] = df_norm(g1[0]);
+      df g[NS], g0[NS], g1[NS];
+#pragma unroll
+      for (int r = 0; r < NS; ++r) grad_slice_df(cq + 5 * r, s[0], s[1], g[r], g0[r], g1[r]);
+      if constexpr (D == 3) {
+        Gu[comp][0] = df_norm(df_horner(df_horner(g0[2], s[2], g0[1]), s[2], g0[0]));
+        Gu[comp][1] = df_norm(df_horner(df_horner(g1[2], s[2], g1[1]), s[2], g1[0]));
+        Gu[comp][2] = df_norm(df_horner(df_scale2(g[2], 2.0f), s[2], g[1]));
+      } else {
+        Gu[comp][0] = df_norm(g0[0]);
+        Gu[comp][1] = df_norm(g1[0]);
+      }
     }
   }
 }
@@ -162,10 +193,10 @@ __device__ __forceinline__ void invert_df(const df J[D][D], df Ji[D][D]) {
 }
 
 // G = du_h/dx at double-float reference coordinates t of cell K.
-template <int D>
+template <int D, bool ROLLED = false>
 __device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], df G[D][D]) {
   df Gu[D][D], J[D][D], Ji[D][D];
-  q2_grad_mono_df<D>(m.Qc, K, t, Gu);
+  q2_grad_mono_df<D, ROLLED>(m.Qc, K, t, Gu);
   CellBlock<D> cb;
   load_block<D>(m, K, cb);
   map_jacobian_df<D>(cb, t, J);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(Me
         t[a] = df_make(v.x, v.y);
       }
       df G[D][D];
-      velocity_gradient_df<D>(m, K, t, G);
+      velocity_gradient_df<D, true>(m, K, t, G);  // rolled: this kernel is bound by its instruction fetch
       const float c = p == 0 ? 0.f : TB::c(p);
       df zs[NZ];
 #pragma unroll
