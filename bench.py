@@ -513,9 +513,10 @@ def run_props(args):
 
 
 # FP32 flops (FADD + FMUL + 2 FFMA) per particle-step of the property-ODE
-# kernel (G and the stage arithmetic in double-float), counted by ncu on the
-# 64^3 x 20 workload (profiles/next_rows_c2_64cubed.md).
-PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 18488.0
+# work beyond the plain step: the stage-gradient kernel (13,768) and the ODE
+# kernel (4,480), both in double-float, counted by ncu on the 64^3 x 20
+# workload (profiles/next_rows_c2_64cubed.md).
+PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 18248.0
 
 # FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
 # counted by ncu on the 64^3 x 20 workload; profiles/next_rows_c2_64cubed.md).
@@ -597,11 +598,11 @@ def run_next(args):
     op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=10)
     op = op.subset(np.arange(op.n) % 5000 == 0)
     op.props[:, 1:10] = eye
-    ode_ms = ms - steady  # the ODE kernel: the step's time beyond the plain advect + rebin
+    ode_ms = ms - steady  # the gradient and ODE kernels: the step's time beyond the plain advect + rebin
     ach = PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP * N / (ode_ms / 1e3) / 1e12
     rows["f2_property_odes"] = {
         "value": N / (ms / 1e3), "unit": "particle-steps/s", "ms_per_step": ms,
-        "roofline": {"kernel": "props_ode_kernel<3,RK4>", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+        "roofline": {"kernel": "props_grad_kernel<3> + props_ode_kernel<3,RK4>", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
                      "fp32_flops_per_particle_step": PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP,
                      "kernel_ms": ode_ms, "kernel_ms_how": "step with ODEs minus the plain step",

@@ -217,7 +217,7 @@ pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integra
  * with G = grad u_h at the particle.  Both ride on the position as one
  * system, stepped by the same integrator over the same located stage points,
  * so positions, cells and order are exactly those of pic_advect (FP64 form);
- * G is evaluated in FP64 at every stage.
+ * G is evaluated in double-float arithmetic (~2^-44 relative) at every stage.
  *   damage       property slot of d, or -1
  *   alpha, beta  material parameters of the damage law (finite)
  *   deformation  first of dim*dim consecutive property slots holding F
@@ -230,10 +230,12 @@ typedef struct {
 
 /* n_steps of pic_advect (FP64 form) that also advance the properties of
  * `odes` (host struct, read during the call).  Other properties ride along.
+ * Scratch: 4 (4 + 8 dim + 8 dim^2) bytes per particle of capacity (stage
+ * records and gradients), allocated with the store on the first call.
  * Errors: PIC_ERR_ARG (as pic_advect; a slot outside the store's properties;
  * damage overlapping the deformation slots), PIC_ERR_STATE (the mesh carries
  * a second velocity field: the property ODEs take the steady field),
- * PIC_ERR_CUDA. */
+ * PIC_ERR_OOM (the scratch), PIC_ERR_CUDA. */
 pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
                                  int n_steps, const pic_property_odes *odes, void *stream);
 

@@ -67,10 +67,7 @@ __device__ __forceinline__ void grad_slice_df(const float4* __restrict__ sl, df 
 // t, from the cell's coefficient slices (u_c = sum_r slice_r(s0, s1) s2^r).
 // Along s2 the slices combine as d0 = sum g0_r s2^r, d1 = sum g1_r s2^r,
 // d2 = g_1 + 2 g_2 s2: 47 double-float Horner steps per component.
-// ROLLED takes one slice per loop iteration and combines them by Horner's
-// scheme with its derivative recurrence (one step more per component, a
-// third of the code): for kernels whose instruction footprint is the limit.
-template <int D, bool ROLLED = false>
+template <int D>
 __device__ __forceinline__ void q2_grad_mono_df(const float4* __restrict__ Qc, uint32_t K, const df t[D],
                                                 df Gu[D][D]) {
   constexpr int NS = (D == 3 ? 3 : 1);
@@ -81,40 +78,16 @@ __device__ __forceinline__ void q2_grad_mono_df(const float4* __restrict__ Qc, u
 #pragma unroll 1
   for (int comp = 0; comp < D; ++comp) {
     const float4* cq = cell + comp * (5 * NS);
-    if constexpr (ROLLED && D == 3) {
-      // highest slice first: A0, A1 gather the s0- and s1-derivatives, V the
-      // values and Dz the derivative of V along s2
-      df A0 = df_make(0.f, 0.f), A1 = A0, V = A0, Dz = A0;
-#pragma unroll 1
-      for (int r = NS - 1; r >= 0; --r) {
-        df g, g0, g1;
-        grad_slice_df(cq + 5 * r, s[0], s[1], g, g0, g1);
-        if (r == NS - 1) {
-          A0 = g0;
-          A1 = g1;
-          V = g;
-        } else {
-          Dz = (r == NS - 2) ? V : df_horner(Dz, s[2], V);
-          A0 = df_horner(A0, s[2], g0);
-          A1 = df_horner(A1, s[2], g1);
-          if (r > 0) V = df_horner(V, s[2], g);
-        }
-      }
-      Gu[comp][0] = df_norm(A0);
-      Gu[comp][1] = df_norm(A1);
-      Gu[comp][2] = df_norm(Dz);
-    } else {
-      df g[NS], g0[NS], g1[NS];
+    df g[NS], g0[NS], g1[NS];
 #pragma unroll
-      for (int r = 0; r < NS; ++r) grad_slice_df(cq + 5 * r, s[0], s[1], g[r], g0[r], g1[r]);
-      if constexpr (D == 3) {
-        Gu[comp][0] = df_norm(df_horner(df_horner(g0[2], s[2], g0[1]), s[2], g0[0]));
-        Gu[comp][1] = df_norm(df_horner(df_horner(g1[2], s[2], g1[1]), s[2], g1[0]));
-        Gu[comp][2] = df_norm(df_horner(df_scale2(g[2], 2.0f), s[2], g[1]));
-      } else {
-        Gu[comp][0] = df_norm(g0[0]);
-        Gu[comp][1] = df_norm(g1[0]);
-      }
+    for (int r = 0; r < NS; ++r) grad_slice_df(cq + 5 * r, s[0], s[1], g[r], g0[r], g1[r]);
+    if constexpr (D == 3) {
+      Gu[comp][0] = df_norm(df_horner(df_horner(g0[2], s[2], g0[1]), s[2], g0[0]));
+      Gu[comp][1] = df_norm(df_horner(df_horner(g1[2], s[2], g1[1]), s[2], g1[0]));
+      Gu[comp][2] = df_norm(df_horner(df_scale2(g[2], 2.0f), s[2], g[1]));
+    } else {
+      Gu[comp][0] = df_norm(g0[0]);
+      Gu[comp][1] = df_norm(g1[0]);
     }
   }
 }
@@ -193,10 +166,10 @@ __device__ __forceinline__ void invert_df(const df J[D][D], df Ji[D][D]) {
 }
 
 // G = du_h/dx at double-float reference coordinates t of cell K.
-template <int D, bool ROLLED = false>
+template <int D>
 __device__ __forceinline__ void velocity_gradient_df(const MeshView& m, uint32_t K, const df t[D], df G[D][D]) {
   df Gu[D][D], J[D][D], Ji[D][D];
-  q2_grad_mono_df<D, ROLLED>(m.Qc, K, t, Gu);
+  q2_grad_mono_df<D>(m.Qc, K, t, Gu);
   CellBlock<D> cb;
   load_block<D>(m, K, cb);
   map_jacobian_df<D>(cb, t, J);

@@ -102,7 +102,7 @@ struct pic_particles_s {
   uint32_t* perm;         // [capacity]
   pic::DevCounters* ctr;  // device counters and status word
   double* xfer;           // [2 * 2^dim][C] per-cell partial sums of the vertex averages, allocated on first use
-  void* stage_rec;        // property ODEs: StageRec arrays, cell [4][cap] u32 then x-hat [dim][4][cap] float2, on first use
+  void* stage_rec;        // property ODEs, on first use: StageRec cell [4][cap] u32, x-hat [dim][4][cap] float2, then G [4][dim^2][cap] float2
   cudaStream_t stream;
   // optional event timing of pic_advect (instrumentation)
   int timing;

@@ -4,16 +4,18 @@
 //   deformation gradient F' = G F,                         G = grad u_h
 // with |.| the Frobenius norm.  The properties and the position form one
 // system z = (x, d, F) stepped by the same RK tableau over the same located
-// stage points.  Each time step runs in two kernels:
+// stage points.  Each time step runs in three kernels:
 //   1. the particle step of pic_advect (the same advect_particle, so
 //      positions, cells and order are those of pic_advect bit for bit),
 //      recording every stage's (cell, x-hat);
-//   2. the ODEs over the recorded stages, G and the stage arithmetic in
-//      double-float on the FP32 pipe, without the locate code, so this
-//      kernel keeps few registers live and many warps resident;
-// then the rebin carries the properties with the particles.  The stage
-// records take 4 (4 + 8 dim) bytes per particle of scratch, allocated with
-// the store on first use.
+//   2. G = grad u_h at every recorded stage point, thread per (stage,
+//      particle), in double-float on the FP32 pipe;
+//   3. the ODEs over the stages with those G, in double-float.
+// Kept apart, each kernel fits the instruction cache (one kernel doing 2
+// and 3 stalled on instruction fetch) and 2 runs without the ODE state live.
+// Then the rebin carries the properties with the particles.  The stage
+// records and gradients take 4 (4 + 8 dim + 8 dim^2) bytes per particle of
+// scratch, allocated with the store on first use.
 #include <cmath>
 
 #include "advect.cuh"
@@ -57,7 +59,39 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kern
   }
 }
 
-// Phase 2, thread per surviving particle: the property ODEs over the recorded
+// Phase 2, thread per (stage, surviving particle): G_p = grad u_h at the
+// recorded stage point, in double-float, stored as G[(p D^2 + e) cap + i].
+// A kernel of its own, so that neither it nor the ODE kernel outgrows the
+// instruction cache.
+template <int D>
+__global__ void __launch_bounds__(128, 4) props_grad_kernel(MeshView m, StageRec rec, int S,
+                                                           const uint32_t* __restrict__ cell_new,
+                                                           const DevCounters* __restrict__ ctr,
+                                                           float2* __restrict__ Gs) {
+  const uint32_t n = ctr->n_alive;
+  const size_t items = (size_t)S * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < items; k += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(k / n);
+    const uint32_t i = (uint32_t)(k - (size_t)p * n);
+    if (cell_new[i] == PIC_LOST) continue;
+    const uint32_t K = rec.cell[(size_t)p * rec.cap + i];
+    if (K >= m.C) continue;  // cannot happen for a survivor
+    df t[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const float2 v = rec.t[((size_t)a * 4 + p) * rec.cap + i];
+      t[a] = df_make(v.x, v.y);
+    }
+    df G[D][D];
+    velocity_gradient_df<D>(m, K, t, G);
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+      for (int q = 0; q < D; ++q) Gs[((size_t)p * D * D + r * D + q) * rec.cap + i] = make_float2(G[r][q].hi, G[r][q].lo);
+  }
+}
+
+// Phase 3, thread per surviving particle: the property ODEs over the recorded
 // stages, in double-float.  For stage p: z_p = z + c_p k_{p-1},
 // k_p = dt f(G_p, z_p), and z' = z + sum_p w_p k_p (/ 6 for RK4), with
 //   f_d = alpha |(G + G^T)/2|_F - beta d,   f_F = G F.
@@ -68,9 +102,10 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kern
 #endif
 
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(MeshView m, StoreView s, df dt, OdeArgs o, StageRec rec,
-                                                        const uint32_t* __restrict__ cell_new,
-                                                        const DevCounters* __restrict__ ctr) {
+__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(StoreView s, df dt, OdeArgs o,
+                                                                              const float2* __restrict__ Gs,
+                                                                              const uint32_t* __restrict__ cell_new,
+                                                                              const DevCounters* __restrict__ ctr) {
   using TB = Tableau<RK>;
   constexpr int NZ = 1 + D * D;  // z = (d, F_00, F_01, ...)
   const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);
@@ -86,16 +121,14 @@ __global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(Me
     for (int q = 0; q < NZ; ++q) k[q] = acc[q] = df_make(0.f, 0.f);
 #pragma unroll 1
     for (int p = 0; p < TB::S; ++p) {
-      const uint32_t K = rec.cell[(size_t)p * rec.cap + i];
-      if (K >= m.C) break;  // cannot happen for a survivor
-      df t[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const float2 v = rec.t[((size_t)a * 4 + p) * rec.cap + i];
-        t[a] = df_make(v.x, v.y);
-      }
       df G[D][D];
-      velocity_gradient_df<D, true>(m, K, t, G);  // rolled: this kernel is bound by its instruction fetch
+#pragma unroll
+      for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          const float2 v = Gs[((size_t)p * D * D + r * D + q) * s.cap + i];
+          G[r][q] = df_make(v.x, v.y);
+        }
       const float c = p == 0 ? 0.f : TB::c(p);
       df zs[NZ];
 #pragma unroll
@@ -146,6 +179,11 @@ __global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(Me
   }
 }
 
+// The stage gradients follow the stage records in the store's scratch.
+static float2* stage_gradients(pic_particles_s* p) {
+  return (float2*)((char*)p->stage_rec + (size_t)4 * p->capacity * (sizeof(uint32_t) + sizeof(float2) * p->dim));
+}
+
 static int props_grid(size_t n) {
   const size_t want = (n + 127) / 128;
   const size_t cap = (size_t)num_sms() * 16;
@@ -158,9 +196,12 @@ static void launch_props_rk(pic_particles_s* p, const MeshView& m, df dt, const 
                             cudaStream_t st) {
   const StoreView s = store_view(p, p->cur);
   const int g = props_grid(p->capacity);
+  float2* Gs = stage_gradients(p);
   advect_record_kernel<D, RK><<<g, 128, 0, st>>>(m, s, dt, rec, p->cell_new, p->counts, p->ctr);
-  props_ode_kernel<D, RK><<<g, 128, 0, st>>>(m, s, dt, o, rec, p->cell_new, p->ctr);
-  count_launches(2);
+  props_grad_kernel<D><<<props_grid((size_t)Tableau<RK>::S * p->capacity), 128, 0, st>>>(m, rec, Tableau<RK>::S,
+                                                                                        p->cell_new, p->ctr, Gs);
+  props_ode_kernel<D, RK><<<g, 128, 0, st>>>(s, dt, o, Gs, p->cell_new, p->ctr);
+  count_launches(3);
 }
 
 template <int D>
@@ -238,11 +279,12 @@ extern "C" pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, 
   cudaStream_t st = (cudaStream_t)stream;
   const MeshView m = mesh_view(mesh);
   if (!parts->stage_rec) {
-    const size_t bytes = (size_t)4 * parts->capacity * (sizeof(uint32_t) + sizeof(float2) * d);
+    const size_t bytes = (size_t)4 * parts->capacity * (sizeof(uint32_t) + sizeof(float2) * d + sizeof(float2) * d * d);
     if (cudaMalloc(&parts->stage_rec, bytes) != cudaSuccess) {
       cudaGetLastError();
       parts->stage_rec = nullptr;
-      return (set_error("pic_advect_properties: cannot allocate %zu bytes of stage records", bytes), PIC_ERR_OOM);
+      return (set_error("pic_advect_properties: cannot allocate %zu bytes of stage records and gradients", bytes),
+              PIC_ERR_OOM);
     }
   }
   const StageRec rec = {(uint32_t*)parts->stage_rec,
