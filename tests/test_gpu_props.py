@@ -86,6 +86,23 @@ def test_props_match_oracle(P, oracle_mod, case, integrator):
     _check_props(g, op, wl.dim)
 
 
+def test_props_with_losses(P, oracle_mod):
+    """CFL ~6: stage points leave the domain and their particles are dropped;
+    the survivors' properties still match the oracle."""
+    wl = W.curl_cube(6, 6, 1, 9)
+    mesh, parts, om, op = _setup(P, oracle_mod, wl)
+    dt = 12 * wl.dt
+    parts.advect_properties(dt, 4, 2, damage=0, alpha=0.8, beta=0.6, deformation=1)
+    op = oracle_mod.advect_properties(om, op, dt, 4, 2, damage=0, alpha=0.8, beta=0.6, defgrad=1)
+    g = H.gpu_state(parts)
+    n_alive, n_lost, status = parts.state()
+    assert n_lost > 0 and n_alive == op.n and n_lost == op.n_lost
+    np.testing.assert_array_equal(g["id"], op.id)
+    np.testing.assert_array_equal(g["cell"], op.cell)
+    assert np.abs(g["x"] - op.x).max() <= H.TOL_X
+    _check_props(g, op, wl.dim)
+
+
 def test_positions_identical_to_plain_advect(P, oracle_mod):
     wl = W.curl_cube(6, 8, 1, 5)
     mesh, a = H.gpu_seed(wl, n_props=11)
