@@ -77,6 +77,8 @@ def _load():
     lib.orc_seed_mh.argtypes = [P, P, P, u32, u64, u64, P, P, P, P]
     lib.orc_import.restype = i64
     lib.orc_import.argtypes = [P, i64, P, u64, P, P, P, P]
+    lib.orc_advect_tangent.restype = None
+    lib.orc_advect_tangent.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P, P, P]
     lib.orc_advect_loss.restype = f64
     lib.orc_advect_loss.argtypes = [P, i64, P, P, P, f64, C.c_int, C.c_int, P]
     _lib = lib
@@ -339,6 +341,18 @@ def advect_adjoint(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_s
     L = _load().orc_advect_adjoint(mesh._h, parts.n, _p(parts.x), _p(parts.xhat), _p(parts.cell), float(dt),
                                    int(integrator), int(n_steps), _p(t), _p(g))
     return float(L), g
+
+
+def advect_tangent(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, V):
+    """(dx [N][dim], alive [N]): the derivative of each particle's final
+    position in the direction V ([dim][nnodes]) of the nodal velocities, by
+    forward (tangent-linear) mode; 0 for particles lost on the way."""
+    Vc = np.ascontiguousarray(V, dtype=np.float64)
+    dx = np.zeros((parts.n, mesh.dim))
+    alive = np.zeros(parts.n, dtype=np.int32)
+    _load().orc_advect_tangent(mesh._h, parts.n, _p(parts.x), _p(parts.xhat), _p(parts.cell), float(dt),
+                               int(integrator), int(n_steps), _p(Vc), _p(dx), _p(alive))
+    return dx, alive.astype(bool)
 
 
 def advect_loss(mesh: Mesh, parts: Particles, dt: float, integrator: int, n_steps: int, targets) -> float:

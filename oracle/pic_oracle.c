@@ -379,10 +379,8 @@ static double lagrange2(int a, double t) {
   return t * (2.0 * t - 1.0);
 }
 
-/* u_h(x) = sum_i U_i phi-hat_i(x-hat) over the 3^d Q2 nodes of cell K: the
- * finite-element field evaluated at the stored reference coordinates
- * (Sec. 2.3, "evaluation of the velocity field", and Remark 2.1). */
-void orc_q2_eval(const orc_mesh *m, int64_t K, const double *xhat, double *u) {
+/* The Q2 field with nodal values F ([dim][nnodes]) at x-hat in cell K. */
+static void q2_eval_field(const orc_mesh *m, const double *F, int64_t K, const double *xhat, double *u) {
   int d = m->dim;
   int64_t i, j, k;
   cell_ijk(m, K, &i, &j, &k);
@@ -395,11 +393,16 @@ void orc_q2_eval(const orc_mesh *m, int64_t K, const double *xhat, double *u) {
           int64_t node = (2 * i + a) + m->nq[0] * ((2 * j + b) + m->nq[1] * (2 * k + c));
           double w = lagrange2(a, xhat[0]) * lagrange2(b, xhat[1]);
           if (d == 3) w = w * lagrange2(c, xhat[2]);
-          s = s + m->U[(int64_t)comp * m->nnodes + node] * w;
+          s = s + F[(int64_t)comp * m->nnodes + node] * w;
         }
     u[comp] = s;
   }
 }
+
+/* u_h(x) = sum_i U_i phi-hat_i(x-hat) over the 3^d Q2 nodes of cell K: the
+ * finite-element field evaluated at the stored reference coordinates
+ * (Sec. 2.3, "evaluation of the velocity field", and Remark 2.1). */
+void orc_q2_eval(const orc_mesh *m, int64_t K, const double *xhat, double *u) { q2_eval_field(m, m->U, K, xhat, u); }
 
 /* ------------------------------------------------ seeding (Sec. 2.2) --- */
 
@@ -791,6 +794,81 @@ double orc_advect_adjoint(const orc_mesh *m, int64_t N, const double *x, const d
   free(ts);
   free(ks);
   return loss;
+}
+
+/* Forward (tangent-linear) mode of the same map: the derivative of each
+ * surviving particle's final position in the direction V of the nodal
+ * velocities ([dim][nnodes]).  Per step, with the stage points re-formed from
+ * the step's start as in the reverse sweep and v_h the Q2 field of V,
+ *   delta-y_s = delta-x + a_s delta-k_{s-1},
+ *   delta-k_s = dt (G_s delta-y_s + v_h(y_s)),
+ *   delta-x'  = delta-x + sum_s b_s delta-k_s
+ * (cells held fixed, R12); the trajectory itself is stepped by step_particle.
+ * Written apart from the reverse sweep, it checks that sweep through
+ * <J V, W> = <V, J^T W>.  Inputs particle-major; dx [N][dim] (0 for lost
+ * particles) and alive [N] are written. */
+void orc_advect_tangent(const orc_mesh *m, int64_t N, const double *x, const double *xhat, const int64_t *cell,
+                        double dt, int integrator, int n_steps, const double *V, double *dx, int32_t *alive) {
+  int d = m->dim;
+  int S = integrator == 1 ? 1 : (integrator == 2 ? 2 : 4);
+  double a_[4] = {0.0, 0.5, 0.5, 1.0}, b_[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  if (S == 1) b_[0] = 1.0;
+  if (S == 2) {
+    b_[0] = 0.0;
+    b_[1] = 1.0;
+  }
+  for (int64_t p = 0; p < N; ++p) {
+    orc_particle P;
+    double props_dummy = 0.0;
+    P.id = 0;
+    P.cell = cell[p];
+    P.props = &props_dummy;
+    double dxp[3] = {0, 0, 0};
+    for (int j = 0; j < d; ++j) {
+      P.x[j] = x[p * d + j];
+      P.xhat[j] = xhat[p * d + j];
+    }
+    int ok = 1;
+    for (int n = 0; n < n_steps && ok; ++n) {
+      double k[4][3] = {{0}}, dk[4][3] = {{0}}, dnew[3];
+      for (int j = 0; j < d; ++j) dnew[j] = dxp[j];
+      for (int s = 0; s < S && ok; ++s) {
+        double y[3] = {0, 0, 0}, dy[3] = {0, 0, 0}, th[3] = {0, 0, 0}, u[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+        double G[3][3] = {{0}};
+        int64_t K;
+        for (int j = 0; j < d; ++j) {
+          y[j] = s == 0 ? P.x[j] : P.x[j] + a_[s] * k[s - 1][j];
+          dy[j] = s == 0 ? dxp[j] : dxp[j] + a_[s] * dk[s - 1][j];
+        }
+        if (s == 0) {
+          K = P.cell;
+          for (int j = 0; j < d; ++j) th[j] = P.xhat[j];
+        } else {
+          K = orc_owner(m, y, th);
+          if (K < 0) {
+            ok = 0;
+            break;
+          }
+        }
+        orc_q2_eval(m, K, th, u);
+        q2_eval_field(m, V, K, th, v);
+        velocity_jacobian(m, K, th, G);
+        for (int c = 0; c < d; ++c) {
+          double gd = 0.0;
+          for (int q = 0; q < d; ++q) gd = gd + G[c][q] * dy[q];
+          k[s][c] = dt * u[c];
+          dk[s][c] = dt * (gd + v[c]);
+          dnew[c] = dnew[c] + b_[s] * dk[s][c];
+        }
+      }
+      if (!ok) break;
+      step_particle(m, &P, dt, integrator);
+      if (P.cell < 0) ok = 0;
+      for (int j = 0; j < d; ++j) dxp[j] = dnew[j];
+    }
+    alive[p] = ok;
+    for (int j = 0; j < d; ++j) dx[p * d + j] = ok ? dxp[j] : 0.0;
+  }
 }
 
 /* The loss alone (the forward of the adjoint), for finite differences. */

@@ -58,3 +58,39 @@ def test_adjoint_lost_particles_contribute_nothing(oracle_mod):
     L2, grad2 = O.advect_adjoint(m, p.subset(keep), dt, 2, steps, tg[keep])
     assert L == pytest.approx(L2, rel=1e-14)
     np.testing.assert_allclose(grad, grad2, rtol=0, atol=1e-14 * np.abs(grad).max())
+
+
+@pytest.mark.parametrize("dim,integrator,losses", [(3, 4, False), (3, 2, False), (2, 4, False), (2, 1, False),
+                                                   (3, 4, True)])
+def test_dot_product_reverse_against_tangent(oracle_mod, dim, integrator, losses):
+    """<J V, W> = <V, J^T W> for the map U -> final positions: the tangent-
+    linear sweep (forward mode, written apart) against the reverse sweep, with
+    lambda_final = W through targets x_final - W/2.  Both are exact
+    derivatives of the same discrete map, so they agree to rounding."""
+    O = oracle_mod
+    if dim == 3:
+        wl = W.curl_cube(4, 3, 3, 4) if not losses else W.curl_cube(5, 4, 2, 9)
+    else:
+        wl = W.c5_member(5, 3)
+        wl.per_cell[:] = 3
+    m = O.Mesh(wl.n, wl.X, wl.U)
+    p = O.seed_particles(m, per_cell=wl.per_cell, uniform_count=wl.ppc or 0, seed=wl.pseed)
+    g = np.random.default_rng(5)
+    steps, dt = 3, (12 if losses else 2) * wl.dt
+    V = g.standard_normal(wl.U.shape)
+    Wt = g.standard_normal(p.x.shape)
+    dx, alive = O.advect_tangent(m, p, dt, integrator, steps, V)
+    assert alive.any()
+    if losses:
+        assert not alive.all()
+    fin = O.advect(m, p, dt, integrator, steps)
+    x_final = dict(zip((int(i) for i in fin.id), fin.x))
+    assert set(x_final) == set(int(i) for i in p.id[alive])
+    tg = np.zeros_like(p.x)
+    for q in np.nonzero(alive)[0]:
+        tg[q] = x_final[int(p.id[q])] - 0.5 * Wt[q]
+    _, grad = O.advect_adjoint(m, p, dt, integrator, steps, tg)
+    lhs = float(np.sum(Wt[alive] * dx[alive]))
+    rhs = float(np.sum(V * grad))
+    mag = float(np.sum(np.abs(Wt[alive] * dx[alive])) + np.sum(np.abs(V * grad)))
+    assert abs(lhs - rhs) <= 1e-12 * mag, (lhs, rhs, mag)
