@@ -397,7 +397,7 @@ def run_adjoint(args):
         "checkpoint_tape": {"record_ms": ck_r, "reverse_ms": ck_a, "gradient_ms": ck_r + ck_a,
                             "particle_steps_per_s": psteps / ((ck_r + ck_a) / 1e3),
                             "bytes_per_particle_step": 56},
-        "accuracy": "dL/dU within 1e-11 of max|dL/dU| of the oracle's reverse mode (tests/test_gpu_adjoint.py)",
+        "accuracy": "dL/dU within 1e-12 of max|dL/dU| of the oracle's reverse mode (tests/test_gpu_adjoint.py)",
     }
 
 

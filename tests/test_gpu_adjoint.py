@@ -11,9 +11,10 @@ pytestmark = pytest.mark.gpu
 
 # The GPU sums the same per-stage contributions as the oracle, in another
 # order (per cell, then per node), with the forward's double-float stage
-# points and double-float G and lambda; differences stay at rounding level,
-# bounded here relative to the largest gradient entry.
-TOL_GRAD = 1e-11
+# points and double-float G and lambda; differences stay at rounding level
+# (measured 2e-14 on the small cases and 1e-13 after the 20 steps of the
+# 32^3 case), bounded here relative to the largest gradient entry.
+TOL_GRAD = 1e-12
 
 
 @pytest.fixture(scope="module")
