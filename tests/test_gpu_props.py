@@ -52,14 +52,14 @@ def _setup(P, O, wl, seed=17):
     return mesh, parts, om, op
 
 
-def _check_props(g, o, dim):
+def _check_props(g, o, dim, tol=TOL_PROP):
     nP = 2 + dim * dim
     gp, opr = g["props"][:, :nP], o.props
     scale = np.maximum(1.0, np.abs(opr[:, 1:1 + dim * dim]).max(axis=1))
     dF = np.abs(gp[:, 1:1 + dim * dim] - opr[:, 1:1 + dim * dim]).max(axis=1)
-    assert (dF <= TOL_PROP * scale).all(), (dF / scale).max()
+    assert (dF <= tol * scale).all(), (dF / scale).max()
     dd = np.abs(gp[:, 0] - opr[:, 0])
-    assert (dd <= TOL_PROP * np.maximum(1.0, np.abs(opr[:, 0]))).all(), dd.max()
+    assert (dd <= tol * np.maximum(1.0, np.abs(opr[:, 0]))).all(), dd.max()
     np.testing.assert_array_equal(gp[:, -1], opr[:, -1])
 
 
@@ -100,7 +100,10 @@ def test_props_with_losses(P, oracle_mod):
     np.testing.assert_array_equal(g["id"], op.id)
     np.testing.assert_array_equal(g["cell"], op.cell)
     assert np.abs(g["x"] - op.x).max() <= H.TOL_X
-    _check_props(g, op, wl.dim)
+    # a rounding error dG in a stage's gradient enters F as dt dG F: with dt
+    # twelve times the CFL-0.5 step the bound grows by the same factor
+    # (measured 2.0e-12 relative)
+    _check_props(g, op, wl.dim, tol=12 * TOL_PROP)
 
 
 def test_positions_identical_to_plain_advect(P, oracle_mod):
