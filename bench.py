@@ -326,6 +326,15 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+# FP32 flops (FADD + FMUL + 2 FFMA) per reverse step of the 32^3 x 32 adjoint
+# (1,048,576 particles, RK4), counted by ncu (profiles/adjoint_c4_32cubed.md):
+# reverse_lambda_kernel (G and lambda at 4.19M stage points, double-float)
+# and cell_partial_kernel (the per-cell sums, double-float).
+ADJOINT_C4_FP32_FLOPS_PER_REVERSE_STEP = 1.572e10 + 6.538e9
+# DRAM bytes (read + write) of the same two kernels per reverse step, same capture.
+ADJOINT_C4_DRAM_BYTES_PER_REVERSE_STEP = (204.5e6 + 148.8e6) + (220.1e6 + 15.9e6)
+
+
 def run_adjoint(args):
     """c4: the adjoint (pic_advect_record + pic_tape_adjoint) against the
     plain FP64-form forward of the same run, on one GPU."""
@@ -380,6 +389,7 @@ def run_adjoint(args):
             rec_ms.append(r)
             adj_ms.append(a)
     f, r, a = statistics.median(fwd_ms), statistics.median(rec_ms), statistics.median(adj_ms)
+    rev_tf = ADJOINT_C4_FP32_FLOPS_PER_REVERSE_STEP * steps / (a / 1e3) / 1e12
     # the same gradient through a checkpoint tape (about half the memory)
     ck = [gradient(P.PIC_TAPE_CHECKPOINTS) for _ in range(1 + max(1, args.steps))][1:]
     ck_r, ck_a = statistics.median(c[0] for c in ck), statistics.median(c[1] for c in ck)
@@ -392,6 +402,12 @@ def run_adjoint(args):
         "config": {"workload": wl.name, "particles": N, "time_steps": steps, "integrator": "RK4",
                    "one_benchmark_step": "one full gradient: %d recorded steps + reverse sweep" % steps},
         "forward_plain_ms": f, "record_ms": r, "reverse_ms": a,
+        "roofline": {"kernel": "reverse sweep: reverse_lambda_kernel<3,4> + cell_partial_kernel<3> (with the record "
+                               "sort and node sums in the time)", "bound": "alu", "achieved": rev_tf,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": rev_tf / FP32_PEAK_TFLOPS,
+                     "fp32_flops_per_reverse_step": ADJOINT_C4_FP32_FLOPS_PER_REVERSE_STEP,
+                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                     "traffic": ADJOINT_C4_DRAM_BYTES_PER_REVERSE_STEP, "traffic_per": "reverse step, both kernels"},
         "forward_plain_particle_steps_per_s": psteps / (f / 1e3),
         "tape": "stage records (116 B per particle-step)",
         "checkpoint_tape": {"record_ms": ck_r, "reverse_ms": ck_a, "gradient_ms": ck_r + ck_a,
