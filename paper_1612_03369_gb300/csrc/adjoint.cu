@@ -6,8 +6,10 @@
 // pic_advect_record advances the store like pic_advect and keeps, for every
 // step, each particle's stage records (the located cell and double-float
 // x-hat of every stage point, exactly as the step used them) and the rebin's
-// permutation (new slot -> old slot).  pic_tape_adjoint then sweeps the
-// steps backwards.  For one step, with y_s = x + a_s k_{s-1}, k_s = dt u(y_s),
+// permutation (new slot -> old slot).  A checkpoint tape keeps instead the
+// store at the start of each step and replays the step in the sweep with the
+// same particle step, which rewrites the same records (half the memory, one
+// more advect per step).  pic_tape_adjoint then sweeps the steps backwards.  For one step, with y_s = x + a_s k_{s-1}, k_s = dt u(y_s),
 // x' = x + sum_s b_s k_s and G_s = du/dx at y_s (cell held fixed):
 //   lambda_k_s = b_s lambda' + a_{s+1} lambda_y_{s+1}
 //   lambda_y_s = dt G_s^T lambda_k_s,       lambda = lambda' + sum_s lambda_y_s
