@@ -141,20 +141,32 @@ __device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_
                                               uint32_t* __restrict__ cursor, uint64_t* __restrict__ key_id,
                                               uint32_t* __restrict__ key_src, uint32_t C, size_t cap, uint32_t n,
                                               unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
+  // four particles per thread and pass, their cells loaded before the first
+  // increment (memory-level parallelism when the grid is small, as in a
+  // persistent kernel)
+  constexpr int U = 4;
   const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t base = first - lane; base < n; base += stride) {
-    const uint32_t i = base + lane;
-    const uint32_t K = i < n ? cell_new[i] : PIC_LOST;
-    if (K != PIC_LOST && K >= C) atomicOr(status, PIC_STATUS_BOUNDS);
-    const bool take = K < C;
-    const uint32_t slot = aggregated_increment(cursor, K, take);
-    if (!take) continue;
-    if (slot >= cap) {
-      atomicOr(status, PIC_STATUS_BOUNDS);
-      continue;
+  for (size_t base = (size_t)first - lane; base < n; base += (size_t)U * stride) {
+    uint32_t K[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const size_t i = base + (size_t)u * stride + lane;
+      K[u] = i < n ? cell_new[i] : PIC_LOST;
     }
-    key_id[slot] = id[i];
-    key_src[slot] = i;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t i = (uint32_t)(base + (size_t)u * stride + lane);
+      if (K[u] != PIC_LOST && K[u] >= C) atomicOr(status, PIC_STATUS_BOUNDS);
+      const bool take = K[u] < C;
+      const uint32_t slot = aggregated_increment(cursor, K[u], take);
+      if (!take) continue;
+      if (slot >= cap) {
+        atomicOr(status, PIC_STATUS_BOUNDS);
+        continue;
+      }
+      key_id[slot] = id[i];
+      key_src[slot] = i;
+    }
   }
 }
 
