@@ -321,6 +321,7 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
+        res["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(wl, seconds=min(args.cpu_seconds, 10.0))
     parts.close()
     mesh.close()
     return res
@@ -739,6 +740,59 @@ def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
     return {"value": done / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": "%d random particles of %s advanced one step at a time for %.1f s (%d particle-steps)"
                       % (len(pick), wl.name, el, done)}
+
+
+# The oracle on all host cores: the sample split into one chunk per core, each
+# advanced in its own process (spawned, so nothing of the GPU context is
+# inherited).  The oracle is unchanged; only the particles are divided, which
+# is exact because they move independently.
+_ORC_WORKER = None
+
+
+def _orc_worker_init(n, X, U, dt, integrator):
+    global _ORC_WORKER
+    import oracle as O
+
+    _ORC_WORKER = (O, O.Mesh(n, X, U), dt, integrator)
+
+
+def _orc_worker_run(task):
+    x, xhat, cell, ids, props, seconds = task
+    O, om, dt, integrator = _ORC_WORKER
+    sub = O.Particles(x, xhat, cell, ids, props)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        before = sub.n
+        sub = O.advect(om, sub, dt, integrator, 1)
+        done += before
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(wl, seconds: float = 10.0, per_core: int = 2000):
+    """The same sample rate with one oracle process per host core."""
+    import multiprocessing as mp
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    om = O.Mesh(wl.n, wl.X, wl.U)
+    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(op.n, min(per_core * cores, op.n), replace=False))
+    sub = op.subset(pick)
+    chunks = np.array_split(np.arange(sub.n), cores)
+    tasks = [(sub.x[c], sub.xhat[c], sub.cell[c], sub.id[c], sub.props[c], seconds) for c in chunks]
+    ctx = mp.get_context("spawn")
+    try:
+        with ctx.Pool(cores, initializer=_orc_worker_init, initargs=(wl.n, wl.X, wl.U, wl.dt, wl.integrator)) as pool:
+            res = pool.map_async(_orc_worker_run, tasks, chunksize=1).get(timeout=seconds + 180)
+    except Exception as e:  # a worker that cannot start must not hold the benchmark
+        return {"unavailable": "%s: %s" % (type(e).__name__, e), "cores": cores, "kind": "oracle"}
+    done = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return {"value": done / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d random particles of %s in %d processes of %d particles, each advanced one step at a time "
+                      "for %.1f s" % (sub.n, wl.name, cores, len(chunks[0]), el)}
 
 
 def run_reference(args, rank, world):
