@@ -89,8 +89,8 @@ pic_status pic_create_mesh(int dim, const int *n_cells, const double *vertices, 
                            pic_mesh *out);
 pic_status pic_destroy_mesh(pic_mesh mesh);
 
-/* Q2 nodal velocity u_h (Sec. 2.3: the finite-element field whose evaluation
- * at particle positions is "the primary expense").
+/* Q2 nodal velocity u_h (Sec. 2.3: the finite-element field; evaluating it at
+ * the particle positions is where the paper says the advection spends most).
  *   U       [dim][nnodes] FP64, device or host, nnodes = prod(2*n_cells[a]+1):
  *           the field at the start of a time step, u_h^n
  *   U_next  NULL for a steady field, or the field at the end of the step,

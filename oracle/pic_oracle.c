@@ -273,8 +273,9 @@ static int solve_cramer(int d, double J[3][3], const double *r, double *delta) {
   return 1;
 }
 
-/* x-hat = Phi_K^{-1}(x) by Newton's method (the "iterative inversion" of
- * Sec. 2.2 and Remark 2.1; reading R2 for start, tolerance and iteration cap).
+/* x-hat = Phi_K^{-1}(x) by Newton's method (the iterative inversion that
+ * Sec. 2.2 and Remark 2.1 call for; reading R2 for start, tolerance and
+ * iteration cap).
  * Returns 1 if converged; *iters receives the iteration count. */
 int orc_newton(const orc_mesh *m, int64_t K, const double *x, const double *start, double *xhat, int *iters) {
   int d = m->dim;
@@ -401,7 +402,7 @@ static void q2_eval_field(const orc_mesh *m, const double *F, int64_t K, const d
 
 /* u_h(x) = sum_i U_i phi-hat_i(x-hat) over the 3^d Q2 nodes of cell K: the
  * finite-element field evaluated at the stored reference coordinates
- * (Sec. 2.3, "evaluation of the velocity field", and Remark 2.1). */
+ * (the velocity evaluation of Sec. 2.3, and Remark 2.1). */
 void orc_q2_eval(const orc_mesh *m, int64_t K, const double *xhat, double *u) { q2_eval_field(m, m->U, K, xhat, u); }
 
 /* ------------------------------------------------ seeding (Sec. 2.2) --- */
@@ -415,7 +416,7 @@ uint64_t orc_splitmix64(uint64_t seed, uint64_t n) {
   return z ^ (z >> 31);
 }
 
-/* R11: local-coordinate generation (Remark "local generation"): walk the
+/* R11: local-coordinate generation (the remark of Sec. 2.2): walk the
  * cells in order, draw x-hat uniform in [0,1)^d, x = Phi_K(x-hat), ids in
  * creation order.  per_cell may be NULL (then uniform_count in every cell).
  * Outputs particle-major: x[N][dim], xhat[N][dim], cell[N], id[N].
@@ -1297,8 +1298,9 @@ void orc_draw_cell_counts(int64_t C, const double *w, int64_t N, uint64_t seed, 
  * of particles of the cells before K) draws SplitMix64 outputs
  * g (dim+1) + j: j < dim the proposal's coordinates (top 53 bits times
  * 2^-53), j = dim the acceptance uniform u.  The proposal y is accepted
- * when u rho-hat(current) < rho-hat(y) (reading R20: the fixed thinning J
- * stands for the paper's "J larger than the longest run of equal samples").
+ * when u rho-hat(current) < rho-hat(y) (reading R20: a fixed thinning J
+ * stands in for the paper's J chosen above the longest stretch of repeated
+ * states, which is known only after the run).
  * x = Phi_K(xhat), ids first_id + (creation index).  Outputs particle-major
  * as in orc_seed.  Returns N. */
 int64_t orc_seed_mh(const orc_mesh *m, const uint32_t *per_cell, const double *rho, uint32_t thinning,

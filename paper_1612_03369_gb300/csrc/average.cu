@@ -1,6 +1,6 @@
 // average.cu -- particle -> cell transfer, scheme (ii) of Sec. 2.7
-// (arithmetic average of the particles of each cell; optimal complexity
-// because the store is sorted by cell).
+// (arithmetic average of the particles of each cell; linear in the particle
+// count because the store is sorted by cell).
 #include "pic_internal.cuh"
 
 namespace pic {

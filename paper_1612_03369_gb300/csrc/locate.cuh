@@ -76,7 +76,7 @@ __device__ __forceinline__ uint32_t lowest_owner(const MeshView& m, const double
   return best;
 }
 
-// All-cells search (Sec. 2.4: "a complete search over all cells"), entered
+// All-cells search (the last resort of Sec. 2.4, every cell tried), entered
 // only when no vertex neighbour holds the point.  The cells around the point's
 // position in a uniform background grid are tried first; a hit there is then
 // settled by the lowest-index rule, which covers every other cell that can

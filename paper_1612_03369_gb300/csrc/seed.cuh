@@ -22,8 +22,9 @@ static __global__ void fill_counts_kernel(const uint32_t* __restrict__ per_cell,
     counts[K] = per_cell ? per_cell[K] : uniform;
 }
 
-// Remark "local generation" (Sec. 2.2): loop over cells in order and over
-// local coordinates inside each; only the forward map Phi_K is needed.
+// The remark on generating in local coordinates (Sec. 2.2): loop over cells
+// in order and over local coordinates inside each; only the forward map
+// Phi_K is needed.
 //
 // The mesh's cells occupy store cells cell_base .. cell_base + C - 1 (an
 // ensemble packs several meshes into one store); ordinals, ids and random

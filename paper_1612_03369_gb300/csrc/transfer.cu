@@ -1,5 +1,6 @@
 // transfer.cu -- particle -> field transfers of Sec. 2.7 beyond cell
-// averages, both of optimal complexity because the store is sorted by cell:
+// averages, both linear in the number of particles because the store is
+// sorted by cell:
 //   (iv) shape-function-weighted averages at the mesh vertices,
 //        p_v = sum_i phi_v(x_i) p_i / sum_i phi_v(x_i) over the particles of
 //        the cells around v, phi_v the (bi/tri)linear nodal basis function
