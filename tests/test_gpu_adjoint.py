@@ -114,6 +114,25 @@ def test_checkpoint_tape_equals_stage_tape(P, case):
     assert np.abs(a[1]).max() > 0
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_adjoint_when_every_particle_is_lost(P, kind):
+    """All particles leave during the recorded run: no survivor, so dL/dU and
+    dL/dx0 are zero, through either tape kind."""
+    import torch
+
+    wl = W.c1(n=4, ppc=2)
+    mesh, parts = H.gpu_seed(wl, n_props=0)
+    N0 = parts.state()[0]
+    tape = P.pic_advect_record_tape(parts.h, mesh.h, 40.0, 4, 2, kind)
+    assert parts.state()[0] == 0
+    dU = torch.full((wl.dim, wl.U.shape[1]), 7.0, dtype=torch.float64, device="cuda")
+    dx0 = torch.full((wl.dim, N0), 7.0, dtype=torch.float64, device="cuda")
+    # dL/dx_final has no column; a one-column array stands in (the sweep reads no entry)
+    P.pic_tape_adjoint(tape, torch.zeros((wl.dim, 1), dtype=torch.float64, device="cuda"), dU, dx0)
+    P.pic_destroy_tape(tape)
+    assert not dU.any() and not dx0.any()
+
+
 def test_tape_kind_errors(P):
     wl = W.curl_cube(3, 2, 2, 2, n_props=0)
     mesh, parts = H.gpu_seed(wl, n_props=0)

@@ -106,6 +106,18 @@ def test_props_with_losses(P, oracle_mod):
     _check_props(g, op, wl.dim, tol=12 * TOL_PROP)
 
 
+def test_props_on_an_emptied_store(P, oracle_mod):
+    """Every particle leaves in the first step; further property steps run on
+    an empty store and leave it empty."""
+    wl = W.c1(n=2, ppc=4)
+    mesh, parts, om, op = _setup(P, oracle_mod, wl)
+    parts.advect_properties(50.0, 4, 1, damage=0, alpha=0.8, beta=0.6, deformation=1)
+    n_alive, n_lost, status = parts.state()
+    assert n_alive == 0 and n_lost == 16
+    parts.advect_properties(wl.dt, 4, 2, damage=0, alpha=0.8, beta=0.6, deformation=1)
+    assert parts.state()[:2] == (0, 16)
+
+
 def test_positions_identical_to_plain_advect(P, oracle_mod):
     wl = W.curl_cube(6, 8, 1, 5)
     mesh, a = H.gpu_seed(wl, n_props=11)
