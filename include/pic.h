@@ -380,14 +380,22 @@ pic_status pic_sort_by_cell(size_t n, const uint32_t *cell, const uint64_t *id, 
  * results are those of pic_sort_by_cell.
  *   Limits: n <= 524288 items and n_cells <= 131072 cells; larger requests
  *   return PIC_ERR_ARG with a message and enqueue nothing.
- *   Scratch: a fixed 7 MiB device array inside the library, held by every
- *   GPU that loads the library until the process exits.  The first call on a
- *   device looks up the array's address on that device (cudaGetSymbolAddress);
- *   make that first call outside any stream capture.
- *   All calls share the array, so calls whose work overlaps on the GPU (on
- *   different streams, or from host threads without ordering) race; order
- *   them, for example on one stream.
- * Calls no allocation routine.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+ *   Scratch: a fixed device array of 7,340,544 bytes inside the library
+ *   (the scratch of one sort at both limits).  Under CUDA's lazy module
+ *   loading (the default) a device receives the array on this entry point's
+ *   first call there, which looks up its address (cudaGetSymbolAddress): make
+ *   that first call (n = 0 is enough) before the application reserves the
+ *   device's memory for itself, and outside any stream capture.  The device
+ *   then holds the array until the process exits.  Calls outside a capture
+ *   look the address up again (no allocation once loaded; correct after a
+ *   cudaDeviceReset); a call on a capturing stream uses the address of the
+ *   device's last call outside capture, and fails with PIC_ERR_STATE if
+ *   there was none.
+ *   All calls share the array, and it keeps the last call's contents (each
+ *   call clears what it needs at zero), so calls whose work overlaps on the
+ *   GPU (on different streams, or from host threads without ordering) race;
+ *   order them, for example on one stream.
+ * Calls no allocation routine.  Errors: PIC_ERR_ARG, PIC_ERR_STATE, PIC_ERR_CUDA. */
 pic_status pic_sort_by_cell_noalloc(size_t n, const uint32_t *cell, const uint64_t *id, uint32_t n_cells,
                                     uint32_t *perm, uint32_t *cell_off, void *stream);
 

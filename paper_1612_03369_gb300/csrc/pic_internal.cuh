@@ -388,7 +388,19 @@ struct SortScratch {
   uint64_t* key_id;
   uint32_t* key_src;
 };
-size_t sort_scratch_bytes(size_t n, uint32_t C);
+// Cells per tile of the offset scan (scan_u32): its tile-sum array holds
+// scan_block_count(C) entries.
+constexpr uint32_t kScanTileCells = 4096;
+constexpr uint32_t scan_tiles(uint32_t n) { return (n + kScanTileCells - 1) / kScanTileCells; }
+// Bytes of the stateless sort's scratch for n items and C cells, in the order
+// sort_scratch_layout carves them (each piece rounded up to 256 B): status
+// words, counts[C], cursor[C], tile sums, key_id[n] u64, key_src[n] u32.
+constexpr size_t sort_scratch_up(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t sort_scratch_bytes(size_t n, uint32_t C) {
+  return sort_scratch_up(sizeof(uint32_t) * 4) + 2 * sort_scratch_up(sizeof(uint32_t) * (size_t)C) +
+         sort_scratch_up(sizeof(uint32_t) * ((size_t)scan_tiles(C) + 1)) +
+         sort_scratch_up(sizeof(uint64_t) * (n ? n : 1)) + sort_scratch_up(sizeof(uint32_t) * (n ? n : 1));
+}
 SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C);
 pic_status sort_by_cell_check(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, const uint32_t* perm,
                               const uint32_t* cell_off, const char* who);

@@ -19,8 +19,9 @@ namespace pic {
 
 constexpr int kScanThreads = 1024;
 constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileCells, "scan tile size and the scratch layout disagree");
 
-uint32_t scan_block_count(uint32_t n) { return (n + kScanTile - 1) / kScanTile; }
+uint32_t scan_block_count(uint32_t n) { return scan_tiles(n); }
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n,
                                                                    uint32_t* __restrict__ block_sums) {
@@ -164,17 +165,10 @@ __global__ void count_cells_kernel(const uint32_t* __restrict__ cell, uint32_t n
   }
 }
 
-// Scratch of the stateless sort, carved from one block of device memory.
-size_t sort_scratch_bytes(size_t n, uint32_t C) {
-  const size_t nb = scan_block_count(C) + 1;
-  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  return up(sizeof(uint32_t) * 4) + 2 * up(sizeof(uint32_t) * (size_t)C) + up(sizeof(uint32_t) * nb) +
-         up(sizeof(uint64_t) * (n ? n : 1)) + up(sizeof(uint32_t) * (n ? n : 1));
-}
-
 SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C) {
+  // the pieces and their order are those counted by sort_scratch_bytes
   const size_t nb = scan_block_count(C) + 1;
-  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  auto up = sort_scratch_up;
   char* p = (char*)base;
   SortScratch sc;
   sc.misc = (uint32_t*)p;  // [0] n, [1] status, [2] kept
