@@ -74,6 +74,7 @@ typedef enum { PIC_AVG_ARITHMETIC = 0, PIC_AVG_GEOMETRIC = 1, PIC_AVG_HARMONIC =
 #define PIC_STATUS_CAPACITY 0x2u       /* a store or list overflowed; data past capacity dropped */
 #define PIC_STATUS_GLOBAL_SEARCH 0x4u  /* the all-cells search ran for some point */
 #define PIC_STATUS_BOUNDS 0x8u         /* a bounds check caught an out-of-range index; access skipped */
+#define PIC_STATUS_TIMEOUT 0x10u       /* a bounded device wait ran out; the kernel carried on without it */
 
 /* Mesh of (bi/tri)linear cells with a Q2 velocity field (Sec. 2.1, 2.3).
  *   dim       2 or 3
@@ -453,9 +454,11 @@ pic_status pic_get_stats(pic_particles parts, uint64_t *particle_steps, uint64_t
 /* All device counters since seeding, in this order (up to n_values of them):
  * particle-steps, neighbour walks, all-cells searches, Newton iterations,
  * particles lost, particle-steps where some cell needed the FP64 Newton
- * fallback, particle-steps whose walk went past the predicted neighbour.
- * Synchronises. */
-#define PIC_N_COUNTERS 7
+ * fallback, particle-steps whose walk went past the predicted neighbour,
+ * particle-steps that pic_advect redid on its full path because the fast
+ * path needed a rare one (FP64 Newton, lowest-index test across a nearby
+ * facet, neighbour walk, all-cells search).  Synchronises. */
+#define PIC_N_COUNTERS 8
 pic_status pic_get_counters(pic_particles parts, uint64_t *values, int n_values);
 
 /* Copy the store out in (cell, id) order.  Synchronises `stream` first to
@@ -467,6 +470,15 @@ pic_status pic_export(pic_particles parts, double *x, double *xhat, uint64_t *id
 /* Cell offsets of the sorted store: off[K]..off[K+1] are the particles of
  * cell K.  off is [n_cells + 1] u32, device or host. */
 pic_status pic_cell_offsets(pic_particles parts, uint32_t *off, void *stream);
+
+/* Where pic_advect's kernel reads the cells' map and coefficient blocks
+ * (Sec. 2.3: every particle evaluates the field of its cell).  on != 0: each
+ * warp stages the blocks of the cells its 32 particles start in into shared
+ * memory with bulk copies (at most three cells, double-buffered; other cells
+ * from the mesh arrays); 0 (the default): all through the read-only cache.
+ * Applies to 3D meshes with a single field; the results are bit-identical
+ * either way.  Synchronous, enqueues nothing.  Errors: PIC_ERR_ARG. */
+pic_status pic_set_advect_staging(pic_particles parts, int on);
 
 /* Instrumentation (no counterpart in the paper).
  * pic_timing_enable: while on, pic_advect records CUDA events on its stream

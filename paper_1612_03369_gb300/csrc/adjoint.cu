@@ -109,7 +109,7 @@ struct TapeStep {
 // records of particles that did not survive the step stay PIC_LOST.
 template <int D, int RK>
 __global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_kernel(
-    MeshView m, TapeStep tp, size_t cap, df dt, const float2* __restrict__ lam_in, float2* __restrict__ lam_out,
+    const __grid_constant__ MeshView m, const __grid_constant__ TapeStep tp, size_t cap, df dt, const float2* __restrict__ lam_in, float2* __restrict__ lam_out,
     uint32_t* __restrict__ rec_cell, uint64_t* __restrict__ rec_key, float2* __restrict__ rec_w,
     DevCounters* __restrict__ ctr) {
   using TB = AdjTableau<RK>;
@@ -186,9 +186,9 @@ __global__ void __launch_bounds__(128, PIC_REVERSE_MIN_BLOCKS) reverse_lambda_ke
 // advect_particle (so the stage records are the forward's bit for bit); the
 // new positions go to a sink.
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) replay_step_kernel(MeshView m, StoreView s, StoreView sink,
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) replay_step_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s, const __grid_constant__ StoreView sink,
                                                                                 const uint32_t* __restrict__ n_start,
-                                                                                df dt, StageRec rec) {
+                                                                                df dt, const __grid_constant__ StageRec rec) {
   const uint32_t n = *n_start;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int iters = 0;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256) cell_partial_kernel(uint32_t C, const uin
 // Thread per (node, component): add the blocks of the cells that share the
 // node, in increasing cell order.
 template <int D>
-__global__ void node_reduce_kernel(MeshView m, const double* __restrict__ partial, double* __restrict__ grad) {
+__global__ void node_reduce_kernel(const __grid_constant__ MeshView m, const double* __restrict__ partial, double* __restrict__ grad) {
   constexpr int NN = (D == 3 ? 27 : 9);
   const size_t total = (size_t)m.nnodes * D;
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {

@@ -8,57 +8,222 @@
 #include <cmath>
 
 #include "advect.cuh"
+#include "bulk.cuh"
 #include "rebin.cuh"
 
 namespace pic {
 
+// ------------------------------------------------------ the step kernel --
+// A persistent grid walks the (cell, id)-sorted store in warp tiles of 32
+// particles, one particle per lane.  Warps take tiles from a work counter
+// (one atomic per tile), two tiles ahead, so that warps that finish early
+// take more and the grid ends together (a static split ran 13% slower).
+//
+// The kernel runs the fast path, which has no out-of-line calls, so the
+// register allocation of the hot code carries no spill code around them: a
+// particle whose fast path would enter a rare path (FP64 Newton, the
+// lowest-index test across a nearby facet, the neighbour walk) is redone by
+// advect_particle_full, called from the tile loop where few values are live.
+// Both run the same arithmetic, so a particle's result does not depend on
+// which ran it.  (With the rare paths called from inside the fast path the
+// kernel spent 1.2x (FP64 form) to 1.5x (FP32-basis form) the time.)
+//
+// STAGE: each warp copies the map and coefficient blocks of the cells its
+// tile starts in (at most kWarpStageCells) into its own slice of shared
+// memory with one bulk copy per table (TMA, cp.async.bulk) counted on its own
+// mbarrier, double-buffered (the copy for the warp's next tile is issued
+// before the current tile is computed), and reads them from there; stage
+// points that leave those cells read the mesh arrays.  Every wait on a copy
+// is bounded (kStageWaitNs); if one runs out, the warp latches
+// PIC_STATUS_TIMEOUT and reads the mesh arrays from then on.  Without STAGE
+// the blocks are read through the read-only cache, where the ~20 particles of
+// a cell find them; that is the faster of the two (the staged loads are
+// generic, and the kernel is bound by instruction issue, not by the cell
+// data's latency).
+constexpr int kAdvectThreads = 128;
+constexpr int kAdvectWarps = kAdvectThreads / 32;
+constexpr int kWarpStageCells = 3;
+constexpr unsigned long long kStageWaitNs = 2000000000ull;
+
+template <int D, bool F32B>
+struct StageLayout {
+  static constexpr int NB = block_float4s<D>();
+  static constexpr int NQ = F32B ? qf_float4s<D>() : qc_float4s<D>();
+  static constexpr int BUF = kWarpStageCells * (NB + NQ);  // float4 per buffer: the map blocks, then the coefficients
+  static constexpr size_t bytes() { return (size_t)kAdvectWarps * 2 * BUF * sizeof(float4); }
+};
+
+// The full step of one particle (every rare path of the locate available),
+// out of line.
+struct FullStep {
+  uint32_t K;
+  int iters;
+  unsigned flags;
+};
 template <int D, int RK, bool F32B, bool TWO>
-__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_kernel(MeshView m, StoreView s, StoreView d,
-                                                                          const uint32_t* __restrict__ perm, df dt,
-                                                                          uint32_t* __restrict__ cell_new,
-                                                                          uint32_t* __restrict__ counts,
-                                                                          DevCounters* __restrict__ ctr) {
-  // perm == nullptr: particle j of s advances in place (d is s).  Otherwise
-  // the previous step's reordering is applied on the way: slot j of d takes
-  // particle perm[j] of s (its cell is already in d.cell[j], written by the
-  // previous rebin), with its id and properties.
+__device__ __noinline__ FullStep advect_particle_full(const MeshView& m, const StoreView& s, uint32_t i,
+                                                      const StoreView& d, uint32_t j, uint32_t K, df dt) {
+  FullStep o;
+  o.iters = 0;
+  o.flags = 0;
+  o.K = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, o.iters, o.flags);
+  return o;
+}
+
+// One particle of a tile: slot j of d, from particle perm[j] of s when perm
+// is given (the previous step's order applied on the way: its cell is in
+// d.cell[j], its id and properties are carried over), else slot j of s in
+// place.  Returns the new cell (PIC_LOST if none); *full is set when the full
+// path redid it.
+template <int D, int RK, bool F32B, bool TWO, class Cells>
+__device__ __forceinline__ uint32_t tile_particle(const Cells& cs, const MeshView& m, const StoreView& s,
+                                                  const StoreView& d, const uint32_t* __restrict__ perm, df dt,
+                                                  uint32_t j, int& iters, unsigned& flags, uint32_t& full) {
+  uint32_t i = j, K;
+  if (perm) {
+    i = perm[j];
+    K = d.cell[j];
+    if (i >= s.cap) {
+      flags |= kFlagBounds;
+      return PIC_LOST;
+    }
+    d.id[j] = s.id[i];
+    for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
+  } else {
+    K = s.cell[j];
+  }
+  uint32_t Kn = advect_particle_cells<D, RK, F32B, TWO, NoHook, true>(cs, m, s, i, d, j, K, dt, iters, flags);
+  if (Kn == kDefer) {
+    const FullStep f = advect_particle_full<D, RK, F32B, TWO>(m, s, i, d, j, K, dt);
+    Kn = f.K;
+    iters = f.iters;
+    flags = f.flags;
+    full = 1;
+  }
+  return Kn;
+}
+
+template <int D, int RK, bool F32B, bool TWO, bool STAGE>
+__global__ void __launch_bounds__(kAdvectThreads, PIC_ADVECT_MIN_BLOCKS)
+    advect_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s,
+                  const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm, df dt,
+                  uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
+  using L = StageLayout<D, F32B>;
+  extern __shared__ float4 stage_smem[];  // STAGE: [warp][2 buffers][BUF]
+  __shared__ __align__(8) uint64_t bars[kAdvectWarps][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4* const wbuf = stage_smem + (size_t)warp * 2 * L::BUF;
+  uint64_t* const bar = bars[warp];
+
   const uint32_t n = ctr->n_alive;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t j = base + threadIdx.x;
+  const uint32_t ntiles = (n + 31) / 32;
+  const uint32_t* __restrict__ start_cell = perm ? d.cell : s.cell;
+  auto grab = [&]() -> uint32_t {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(&ctr->tile_next, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+  };
+  auto start_of = [&](uint32_t t) -> uint32_t {
+    const uint32_t j = t * 32 + lane;
+    return (t < ntiles && j < n) ? start_cell[j] : PIC_LOST;
+  };
+  // the warp: copy the blocks of the cells its tile starts in (kc: each
+  // lane's start cell) into buffer b; k0, cnt receive the first staged cell
+  // and the number staged (the same in every lane)
+  auto issue = [&](uint32_t kc, int b, uint32_t& k0, uint32_t& cnt) {
+    const bool ok = kc < m.C;
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, ok ? kc : 0xffffffffu);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, ok ? kc : 0u);
+    k0 = lo;
+    cnt = lo <= hi ? (hi - lo + 1 < (uint32_t)kWarpStageCells ? hi - lo + 1 : (uint32_t)kWarpStageCells) : 0u;
+    if (lane == 0) {
+      fence_proxy_async_shared();
+      mbar_arrive_expect_tx(&bar[b], cnt * (L::NB + L::NQ) * (uint32_t)sizeof(float4));
+      if (cnt) {
+        float4* dst = wbuf + b * L::BUF;
+        bulk_copy_g2s(dst, m.blk + (size_t)k0 * L::NB, cnt * L::NB * (uint32_t)sizeof(float4), &bar[b]);
+        bulk_copy_g2s(dst + kWarpStageCells * L::NB, (F32B ? m.Qf : m.Qc) + (size_t)k0 * L::NQ,
+                      cnt * L::NQ * (uint32_t)sizeof(float4), &bar[b]);
+      }
+    }
+  };
+
+  if constexpr (STAGE) {
+    if (lane == 0) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+      mbar_init_fence();
+    }
+    __syncwarp();
+  }
+  bool staging = STAGE;
+  uint32_t t = grab(), tn = grab();
+  bool need = staging && t < ntiles;  // a copy into the current buffer is in flight
+  uint32_t k0_cur = 0, n_cur = 0, k0_nxt = 0, n_nxt = 0;
+  if (need) issue(start_of(t), 0, k0_cur, n_cur);
+  uint32_t kc_n = staging ? start_of(tn) : PIC_LOST;  // start cells of the next tile
+  uint32_t it = 0;
+  uint32_t stuck = 0, stuck_parity = 0;  // per buffer (bit b): a wait that ran out, and its phase
+  while (t < ntiles) {
+    const int b = (int)(it & 1u);
+    const bool need_next = staging && tn < ntiles;
+    if (need_next) issue(kc_n, b ^ 1, k0_nxt, n_nxt);
+    // the tile after next (and its start cells): their latency hides behind
+    // this tile
+    const uint32_t tnn = tn < ntiles ? grab() : tn;
+    if (staging) kc_n = start_of(tnn);
+    bool ok = true;
+    if (need) {
+      ok = __all_sync(0xffffffffu, mbar_wait_bounded(&bar[b], (it >> 1) & 1u, kStageWaitNs));
+      if (!ok) {
+        staging = false;
+        if (lane == 0) latch_status(ctr, PIC_STATUS_TIMEOUT);
+        stuck |= 1u << b;
+        stuck_parity = (stuck_parity & ~(1u << b)) | (((it >> 1) & 1u) << b);
+      }
+    }
+
+    const uint32_t j = t * 32 + lane;
     int iters = 0;
     unsigned flags = 0, lost = 0, steps = 0;
-    uint32_t Kc = PIC_LOST;  // the new cell to count
+    uint32_t Kc = PIC_LOST, full = 0;  // the new cell to count
     if (j < n) {
       steps = 1;
-      uint32_t i = j, K;
-      if (perm) {
-        i = perm[j];
-        K = d.cell[j];
-        if (i >= s.cap) {
-          flags |= kFlagBounds;
-          K = PIC_LOST;
-          i = 0;
-        } else {
-          d.id[j] = s.id[i];
-          for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
-        }
+      uint32_t Kn;
+      if constexpr (STAGE) {
+        const StagedCells<D, F32B, kWarpStageCells> cs{m, wbuf + b * L::BUF, k0_cur, (need && ok) ? n_cur : 0u};
+        Kn = tile_particle<D, RK, F32B, TWO>(cs, m, s, d, perm, dt, j, iters, flags, full);
       } else {
-        K = s.cell[j];
+        Kn = tile_particle<D, RK, F32B, TWO>(GlobalCells<D, F32B>{m}, m, s, d, perm, dt, j, iters, flags, full);
       }
-      const uint32_t Kn = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, iters, flags);
       cell_new[j] = Kn;
       Kc = Kn;
       lost = Kn == PIC_LOST ? 1u : 0u;
     }
+    {
+      const unsigned dc = __reduce_add_sync(0xffffffffu, full);
+      if (dc && lane == 0) atomicAdd(&ctr->deferred, (unsigned long long)dc);
+    }
     (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
     flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
+    if constexpr (STAGE) __syncwarp();  // this buffer is free for the copy issued one tile on
+    need = need_next;
+    k0_cur = k0_nxt;
+    n_cur = n_nxt;
+    t = tn;
+    tn = tnn;
+    ++it;
   }
+  // a copy whose wait ran out may still be in flight: give it one more
+  // bounded wait before the block's shared memory is released
+  if (STAGE && lane == 0)
+    for (int b = 0; b < 2; ++b)
+      if ((stuck >> b) & 1u) (void)mbar_wait_bounded(&bar[b], (stuck_parity >> b) & 1u, kStageWaitNs);
 }
 
 // Relocate every particle at its current x (hint: its current cell).
 template <int D>
-__global__ void __launch_bounds__(128) relocate_kernel(MeshView m, StoreView s, uint32_t* __restrict__ cell_new,
+__global__ void __launch_bounds__(128) relocate_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s, uint32_t* __restrict__ cell_new,
                                                        uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
   const uint32_t n = ctr->n_alive;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -91,7 +256,7 @@ __global__ void __launch_bounds__(128) relocate_kernel(MeshView m, StoreView s, 
 // Stateless location of n points.  Without hints, the start cell is the
 // point's cell in a uniform background grid over the mesh's bounding box.
 template <int D>
-__global__ void __launch_bounds__(128) locate_points_kernel(MeshView m, size_t n, const double* __restrict__ x,
+__global__ void __launch_bounds__(128) locate_points_kernel(const __grid_constant__ MeshView m, size_t n, const double* __restrict__ x,
                                                             const uint32_t* __restrict__ hint, uint32_t* __restrict__ cell_out,
                                                             double* __restrict__ xhat_out) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -133,18 +298,32 @@ static int grid_for(size_t n, int block) {
 // One advect launch.  With `fused` the previous step's reordering (perm,
 // sorted cells in the other buffer) is applied on the way: the step reads
 // buffer cur and writes buffer 1 - cur, which becomes cur.
+// Persistent grid: PIC_ADVECT_MIN_BLOCKS blocks per SM (the register
+// budget's residency), fewer when the store has fewer warp tiles.
+static int advect_grid(size_t n) {
+  const size_t blocks = (n + kAdvectThreads - 1) / kAdvectThreads;
+  const size_t cap = (size_t)num_sms() * PIC_ADVECT_MIN_BLOCKS;
+  const size_t g = blocks < cap ? blocks : cap;
+  return (int)(g > 0 ? g : 1);
+}
+
 template <int D, int RK, bool F32B>
 static void launch_advect(pic_particles_s* p, const MeshView& m, double dt, bool fused, cudaStream_t st) {
   const float hi = (float)dt;
   const df dtd = {hi, (float)(dt - (double)hi)};
   const StoreView s = store_view(p, p->cur), d = fused ? store_view(p, 1 - p->cur) : s;
   const uint32_t* perm = fused ? p->perm : nullptr;
-  if (m.has_next)
-    advect_kernel<D, RK, F32B, true><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
-                                                                                 p->counts, p->ctr);
-  else
-    advect_kernel<D, RK, F32B, false><<<grid_for(p->capacity, 128), 128, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
-                                                                                  p->counts, p->ctr);
+  const int grid = advect_grid(p->capacity);
+  if (m.has_next) {
+    advect_kernel<D, RK, F32B, true, false><<<grid, kAdvectThreads, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
+                                                                             p->counts, p->ctr);
+  } else if (D == 3 && p->stage_cells) {
+    advect_kernel<D, RK, F32B, false, D == 3><<<grid, kAdvectThreads, StageLayout<D, F32B>::bytes(), st>>>(
+        m, s, d, perm, dtd, p->cell_new, p->counts, p->ctr);
+  } else {
+    advect_kernel<D, RK, F32B, false, false><<<grid, kAdvectThreads, 0, st>>>(m, s, d, perm, dtd, p->cell_new,
+                                                                              p->counts, p->ctr);
+  }
   count_launches(1);
   if (fused) p->cur = 1 - p->cur;
 }
@@ -190,6 +369,10 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
     return (set_error("pic_advect: unknown precision %d", (int)precision), PIC_ERR_ARG);
   if (!mesh->has_velocity) return (set_error("pic_advect: velocity not set"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  if (precision == PIC_FP32_BASIS) {
+    const pic_status r = ensure_fp32_coefficients(mesh, st);
+    if (r != PIC_OK) return r;
+  }
   const MeshView m = mesh_view(mesh);
   // Each step's rebin computes the new order (perm, sorted cells); the
   // particles themselves move with the next step's advect, which reads them
@@ -198,6 +381,7 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
   bool pending = false;
   for (int step = 0; step < n_steps; ++step) {
     PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
+    PIC_CUDA(cudaMemsetAsync(&parts->ctr->tile_next, 0, sizeof(unsigned int), st));
     cudaEvent_t* ev = parts->timing ? timing_slot(parts) : nullptr;
     if (ev) PIC_CUDA(cudaEventRecord(ev[0], st));
     const bool f32 = precision == PIC_FP32_BASIS;

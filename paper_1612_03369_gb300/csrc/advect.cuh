@@ -45,26 +45,40 @@ __device__ __forceinline__ void flush_counters(DevCounters* ctr, unsigned steps,
 // The Q2 evaluation (per-cell monomial form, Horner) is in double-float, or
 // FP32 for the precision form; it sits in a rolled loop over the (one or two)
 // fields so the kernel holds one copy of it.
-template <int D, bool F32B, bool TWO>
-__device__ __forceinline__ void velocity(const MeshView& m, uint32_t K, const df t[D], int tcode, df u[D]) {
+template <int D, bool F32B, bool TWO, class Cells>
+__device__ __forceinline__ void velocity(const Cells& cs, const MeshView& m, uint32_t K, const df t[D], int tcode,
+                                         df u[D]) {
   if constexpr (!TWO) {
     if constexpr (F32B)
-      q2_eval_f32<D>(m, m.Qc, K, t, u);
+      q2_eval_f32<D>(cs, cs.coef(K), t, u);
     else
-      q2_eval_df<D>(m, m.Qc, K, t, u);
+      q2_eval_df<D>(cs, cs.coef(K), t, u);
     return;
-  }
-  const bool two = m.has_next && tcode == 1;
-  const float4* first = (m.has_next && tcode == 2) ? m.Qcn : m.Qc;
+  } else {
+    // the first field's blocks through the source, the second field's from
+    // the mesh arrays
+    constexpr int NQ = F32B ? qf_float4s<D>() : qc_float4s<D>();
+    const GlobalCells<D, F32B> g{m};
+    const float4* second = (F32B ? m.Qfn : m.Qcn) + (size_t)K * NQ;
+    const bool two = m.has_next && tcode == 1;
+    const bool only_next = m.has_next && tcode == 2;
 #pragma unroll 1
-  for (int f = 0; f < (two ? 2 : 1); ++f) {
-    df v[D];
-    if constexpr (F32B)
-      q2_eval_f32<D>(m, f == 0 ? first : m.Qcn, K, t, v);
-    else
-      q2_eval_df<D>(m, f == 0 ? first : m.Qcn, K, t, v);
+    for (int f = 0; f < (two ? 2 : 1); ++f) {
+      df v[D];
+      if (f == 1 || only_next) {
+        if constexpr (F32B)
+          q2_eval_f32<D>(g, second, t, v);
+        else
+          q2_eval_df<D>(g, second, t, v);
+      } else {
+        if constexpr (F32B)
+          q2_eval_f32<D>(cs, cs.coef(K), t, v);
+        else
+          q2_eval_df<D>(cs, cs.coef(K), t, v);
+      }
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[a] = (f == 0) ? v[a] : df_scale2(df_add(u[a], v[a]), 0.5f);
+      for (int a = 0; a < D; ++a) u[a] = (f == 0) ? v[a] : df_scale2(df_add(u[a], v[a]), 0.5f);
+    }
   }
 }
 
@@ -148,17 +162,20 @@ struct RecordHook {
 // TWO: the mesh carries a second field (time interpolation).
 // Writes the new x and x-hat in place when the particle survives and returns
 // its new cell, or PIC_LOST.
-// advect_particle_to reads particle i of store s and writes its new x and
+// advect_particle_cells reads particle i of store s and writes its new x and
 // x-hat to slot j of store d (the same slot of the same store for the
 // in-place step; another buffer when the step also applies the previous
-// step's reordering).
-template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>
-__device__ __forceinline__ uint32_t advect_particle_to(const MeshView& m, const StoreView& s, uint32_t i,
-                                                       const StoreView& d, uint32_t j, uint32_t K, df dt, int& iters,
-                                                       unsigned& flags, Hook&& hook = Hook()) {
+// step's reordering), reading the cells' blocks from the source cs.
+// kFast: the fast path only; returns kDefer (and writes nothing) where a
+// rare path would be needed.
+template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook, bool kFast = false, class Cells>
+__device__ __forceinline__ uint32_t advect_particle_cells(const Cells& cs, const MeshView& m, const StoreView& s,
+                                                          uint32_t i, const StoreView& d, uint32_t j, uint32_t K,
+                                                          df dt, int& iters, unsigned& flags, Hook&& hook = Hook()) {
   using TB = Tableau<RK>;
   const df sixth = df_make(0.16666667163372039795f, -4.967053879312289e-09f);  // 1/6 = hi + lo
   if (K >= m.C) {
+    if constexpr (kFast) return kDefer;
     flags |= kFlagBounds;
     return PIC_LOST;
   }
@@ -183,13 +200,15 @@ __device__ __forceinline__ uint32_t advect_particle_to(const MeshView& m, const 
         y[a] = df_add(xd[a], p < TB::S ? df_scale2(k[a], TB::c(p)) : acc[a]);
       }
       // the FP32-basis form needs double-float x-hat only where it is stored
-      Ks = locate_df<D>(m, y, Ks, hint, ts, iters, flags, !F32B || p == TB::S);
+      Ks = locate_df<D, kFast>(cs, m, y, Ks, hint, ts, iters, flags, !F32B || p == TB::S);
       if (Ks == PIC_LOST) return PIC_LOST;
+      if constexpr (kFast)
+        if (Ks == kDefer) return kDefer;
       if (p == TB::S) break;
     }
     hook.template stage<D>(p, Ks, ts);
     df u[D];
-    velocity<D, F32B, TWO>(m, Ks, ts, TB::tcode(p), u);
+    velocity<D, F32B, TWO>(cs, m, Ks, ts, TB::tcode(p), u);
     const float w = TB::w(p);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -207,6 +226,15 @@ __device__ __forceinline__ uint32_t advect_particle_to(const MeshView& m, const 
     d.xhat[a * d.cap + j] = make_float2(ts[a].hi, ts[a].lo);
   }
   return Ks;
+}
+
+// The same reading every block from the mesh arrays.
+template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>
+__device__ __forceinline__ uint32_t advect_particle_to(const MeshView& m, const StoreView& s, uint32_t i,
+                                                       const StoreView& d, uint32_t j, uint32_t K, df dt, int& iters,
+                                                       unsigned& flags, Hook&& hook = Hook()) {
+  return advect_particle_cells<D, RK, F32B, TWO>(GlobalCells<D, F32B>{m}, m, s, i, d, j, K, dt, iters, flags,
+                                                 static_cast<Hook&&>(hook));
 }
 
 template <int D, int RK, bool F32B, bool TWO = false, class Hook = NoHook>

@@ -37,6 +37,12 @@ extern "C" pic_status pic_timing_enable(pic_particles p, int on) {
   return PIC_OK;
 }
 
+extern "C" pic_status pic_set_advect_staging(pic_particles p, int on) {
+  if (!p) return (set_error("pic_set_advect_staging: null handle"), PIC_ERR_ARG);
+  p->stage_cells = on ? 1 : 0;
+  return PIC_OK;
+}
+
 extern "C" pic_status pic_timing_read(pic_particles p, double* advect_ms, double* rebin_ms, uint64_t* steps) {
   if (!p) return (set_error("pic_timing_read: null handle"), PIC_ERR_ARG);
   double a = 0.0, r = 0.0;

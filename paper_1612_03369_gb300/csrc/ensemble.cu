@@ -39,12 +39,6 @@ struct GridBarrier {
   unsigned int pad;
 };
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Grid-wide barrier for co-resident blocks (sense by generation count).  The
 // wait of each block is bounded by timeout_ns; on expiry (or when another
 // block has flagged an error) it sets b->err and returns false, and callers
@@ -158,7 +152,7 @@ __device__ __forceinline__ uint32_t ensemble_particle(const EnsShared& sh, int P
 template <int D, int RK>
 __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_advect_kernel(
     const MeshView* __restrict__ views, const uint32_t* __restrict__ base, const df* __restrict__ dts, int P,
-    StoreView s, StoreView d, const uint32_t* __restrict__ perm, uint32_t* __restrict__ cell_new,
+    const __grid_constant__ StoreView s, const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm, uint32_t* __restrict__ cell_new,
     uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
   __shared__ EnsShared sh;
   load_ensemble(sh, views, base, dts, P);

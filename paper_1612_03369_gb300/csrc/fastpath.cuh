@@ -10,6 +10,16 @@
 //   U2           Q2 nodal values as double-floats, node-major [node][dim]
 //                (the source of the coefficient slices below)
 //
+// Qc, the Q2 field's per-cell monomial coefficients about the cell centre
+// (double-float, 720 B per hex), and Qf, their high parts alone for the
+// FP32-basis form (336 B per hex), are built with the field (mesh.cu).
+//
+// Where a cell's blocks are read from is a template parameter: GlobalCells
+// reads the mesh arrays; StagedCells a shared-memory copy of the cells a
+// warp's particles start in (advect.cu), and the mesh arrays for any other
+// cell.  The arithmetic is the same either way, so every kernel that inlines
+// it computes the same bits.
+//
 // Inverse map (Newton, Sec. 2.2 / Remark 2.1): FP32 iterations on the local
 // offset y - X_0 until the update falls below 1e-5, then one Newton step
 // whose residual (y - X_0) - sum_k a_k m_k(t) is evaluated in double-float
@@ -47,16 +57,66 @@ template <int D>
 __host__ __device__ constexpr int block_float4s() {
   return (2 * D + 2 * D * ((1 << D) - 1)) / 4;  // 12 (3D) or 4 (2D)
 }
+// float4 per cell of Qc: per component NS slices of 5 float4 (ten high
+// parts, then ten low parts; the tenth of each is zero).
+template <int D>
+__host__ __device__ constexpr int qc_float4s() {
+  return D * 5 * (D == 3 ? 3 : 1);  // 45 (3D) or 10 (2D)
+}
+// Qf: per component the 3^D high parts in the order r*9 + q*3 + p (the
+// coefficient of s2^r s1^q s0^p), padded to 28 (3D) or 12 (2D) floats.
+template <int D>
+__host__ __device__ constexpr int qf_floats_per_comp() {
+  return D == 3 ? 28 : 12;
+}
+template <int D>
+__host__ __device__ constexpr int qf_float4s() {
+  return D * qf_floats_per_comp<D>() / 4;  // 21 (3D) or 6 (2D)
+}
+
+// ------------------------------------------------------ cell data source --
+
+template <int D, bool F32B>
+struct GlobalCells {
+  static constexpr int NB = block_float4s<D>();
+  static constexpr int NQ = F32B ? qf_float4s<D>() : qc_float4s<D>();
+  const MeshView& m;
+  __device__ __forceinline__ const float4* block(uint32_t K) const { return m.blk + (size_t)K * NB; }
+  __device__ __forceinline__ const float4* coef(uint32_t K) const { return (F32B ? m.Qf : m.Qc) + (size_t)K * NQ; }
+  __device__ __forceinline__ float4 ld(const float4* p) const { return __ldg(p); }
+};
+
+// Cells [K0, K0 + n) from shared memory (sbase: their map blocks in order,
+// then from sbase + kStage * NB their coefficient blocks), every other cell
+// from the mesh arrays.  Loads are generic, so one instruction serves both.
+template <int D, bool F32B, int kStage>
+struct StagedCells {
+  static constexpr int NB = block_float4s<D>();
+  static constexpr int NQ = F32B ? qf_float4s<D>() : qc_float4s<D>();
+  const MeshView& m;
+  const float4* sbase;
+  uint32_t K0, n;
+  __device__ __forceinline__ const float4* block(uint32_t K) const {
+    const uint32_t o = K - K0;
+    return o < n ? sbase + o * NB : m.blk + (size_t)K * NB;
+  }
+  __device__ __forceinline__ const float4* coef(uint32_t K) const {
+    const uint32_t o = K - K0;
+    return o < n ? sbase + kStage * NB + o * NQ : (F32B ? m.Qf : m.Qc) + (size_t)K * NQ;
+  }
+  __device__ __forceinline__ float4 ld(const float4* p) const { return *p; }
+};
 
 // Block layout per cell: NF = D + (2^D - 1) D high parts (X_0, then a_k,c in
-// (k, c) order), then the NF low parts in the same order.
-template <int D>
-__device__ __forceinline__ void load_block_half(const MeshView& m, uint32_t K, int half, float f[]) {
+// (k, c) order), then the NF low parts in the same order.  B points at the
+// cell's block, read through the source's loader.
+template <int D, class Cells>
+__device__ __forceinline__ void load_block_half(const Cells& cs, const float4* B, int half, float f[]) {
   constexpr int NH = block_float4s<D>() / 2;
-  const float4* p = m.blk + (size_t)K * block_float4s<D>() + half * NH;
+  const float4* p = B + half * NH;
 #pragma unroll
   for (int q = 0; q < NH; ++q) {
-    const float4 v = __ldg(p + q);
+    const float4 v = cs.ld(p + q);
     f[4 * q] = v.x;
     f[4 * q + 1] = v.y;
     f[4 * q + 2] = v.z;
@@ -64,10 +124,10 @@ __device__ __forceinline__ void load_block_half(const MeshView& m, uint32_t K, i
   }
 }
 
-template <int D>
-__device__ __forceinline__ void load_block32(const MeshView& m, uint32_t K, CellBlock32<D>& cb) {
+template <int D, class Cells>
+__device__ __forceinline__ void load_block32(const Cells& cs, const float4* B, CellBlock32<D>& cb) {
   float f[2 * block_float4s<D>()];
-  load_block_half<D>(m, K, 0, f);
+  load_block_half<D>(cs, B, 0, f);
 #pragma unroll
   for (int a = 0; a < D; ++a) cb.x0[a] = f[a];
 #pragma unroll
@@ -79,9 +139,11 @@ __device__ __forceinline__ void load_block32(const MeshView& m, uint32_t K, Cell
 template <int D>
 __device__ __forceinline__ void load_block(const MeshView& m, uint32_t K, CellBlock<D>& cb) {
   constexpr int NF = 2 * block_float4s<D>();  // floats per half
+  const GlobalCells<D, false> cs{m};
+  const float4* B = cs.block(K);
   float hi[NF], lo[NF];
-  load_block_half<D>(m, K, 0, hi);
-  load_block_half<D>(m, K, 1, lo);
+  load_block_half<D>(cs, B, 0, hi);
+  load_block_half<D>(cs, B, 1, lo);
 #pragma unroll
   for (int a = 0; a < D; ++a) cb.x0[a] = df_make(hi[a], lo[a]);
 #pragma unroll
@@ -188,8 +250,39 @@ __device__ __forceinline__ void residual_df(const CellBlock32<D>& cb, const floa
   }
 }
 
-// Outcome of the inverse map in one cell.
-enum : int { kCellOut = 0, kCellIn = 1, kCellFail = -1 };
+// Outcome of the inverse map in one cell (kCellDefer: the fast path alone
+// cannot decide, see kDefer).
+enum : int { kCellOut = 0, kCellIn = 1, kCellFail = -1, kCellDefer = -2 };
+
+// Returned instead of a cell by the fast-path-only locate (kFast == true)
+// where the full locate would enter a rare path (the FP64 Newton, the
+// lowest-index test of the cells across a nearby facet, the FP64 walk): the
+// caller hands the particle to a second kernel that runs the full step.  A
+// kernel without those out-of-line calls needs no spill code around them.
+constexpr uint32_t kDefer = 0xFFFFFFFEu;
+
+// Points and results passed by value to and from the out-of-line rare paths,
+// so that no variable of the hot loop has its address taken (an address-
+// taken variable lives in local memory for its whole life).
+template <int D>
+struct DfPt {
+  df v[D];
+};
+template <int D>
+struct RarePath {
+  DfPt<D> t;       // reference coordinates found
+  uint32_t K;      // cell found (PIC_LOST: none)
+  int r;           // kCellIn / kCellOut / kCellFail (single-cell tests)
+  int iters;       // Newton iterations spent
+  unsigned flags;  // flags raised
+};
+template <int D>
+__device__ __forceinline__ DfPt<D> pack(const df a[D]) {
+  DfPt<D> p;
+#pragma unroll
+  for (int i = 0; i < D; ++i) p.v[i] = a[i];
+  return p;
+}
 
 // Inverse map of y in cell K (fast path).  t32 holds the FP32 start on entry;
 // on return t holds the double-float reference coordinates.
@@ -198,16 +291,17 @@ enum : int { kCellOut = 0, kCellIn = 1, kCellFail = -1 };
 // then good to ~1e-7, which is what an FP32 basis evaluation can use.
 constexpr float kSettle32Tight = 1e-5f;
 
-template <int D>
-__device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
+template <int D, class Cells>
+__device__ __forceinline__ int solve_cell_df(const Cells& cs, uint32_t K, const df y[D], float t32[D], df t[D],
                                              int& iters, bool accurate = true) {
+  const float4* B = cs.block(K);
   CellBlock32<D> cb;
-  load_block32<D>(m, K, cb);
+  load_block32<D>(cs, B, cb);
   df dloc[D];
   float d32[D];
   {
     // X_0's low parts lead the block's second half
-    const float4 x0lo = __ldg(m.blk + (size_t)K * block_float4s<D>() + block_float4s<D>() / 2);
+    const float4 x0lo = cs.ld(B + block_float4s<D>() / 2);
     const float l[3] = {x0lo.x, x0lo.y, x0lo.z};
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -262,7 +356,7 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
   map32<D>(cb, t32, phi, J);
   {
     float lo[2 * block_float4s<D>()];
-    load_block_half<D>(m, K, 1, lo);
+    load_block_half<D>(cs, B, 1, lo);
     residual_df<D>(cb, lo, dloc, t32, r);
   }
   if (!solve32<D>(J, r, dt)) return kCellFail;
@@ -281,82 +375,105 @@ __device__ __forceinline__ int solve_cell_df(const MeshView& m, uint32_t K, cons
 }
 
 // FP64 Newton for a cell the fast path could not settle (rare; out of line
-// so that the hot loop stays small in the instruction cache).
+// so that the hot loop stays small in the instruction cache); s32 holds the
+// FP32 start in its high parts.
 template <int D>
-__device__ __noinline__ int test_cell_fp64(const MeshView& m, uint32_t K, const df* y, float* t32, df* t, int* iters,
-                                           unsigned* flags) {
+__device__ __noinline__ RarePath<D> test_cell_fp64(const MeshView& m, uint32_t K, DfPt<D> y, DfPt<D> s32) {
+  RarePath<D> o;
+  o.iters = 0;
+  o.flags = 0;
+  o.K = K;
   double yd[D], tt[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    yd[a] = df_to_double(y[a]);
-    tt[a] = isfinite(t32[a]) && fabsf(t32[a]) < 4.f ? (double)t32[a] : 0.5;
+    yd[a] = df_to_double(y.v[a]);
+    const float st = s32.v[a].hi;
+    tt[a] = isfinite(st) && fabsf(st) < 4.f ? (double)st : 0.5;
   }
   bool conv = false;
-  const bool in = try_cell<D>(m, K, yd, tt, *iters, *flags, &conv);
+  const bool in = try_cell<D>(m, K, yd, tt, o.iters, o.flags, &conv);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    t[a] = df_from_double(tt[a]);
-    t32[a] = t[a].hi;
-  }
-  if (!conv) return kCellFail;
-  return in ? kCellIn : kCellOut;
+  for (int a = 0; a < D; ++a) o.t.v[a] = df_from_double(tt[a]);
+  o.r = !conv ? kCellFail : (in ? kCellIn : kCellOut);
+  return o;
 }
 
 // Fast path, then the FP64 Newton when the fast path does not settle.
+// y inside cell K's padded bounding box (padding 1e-6 of the cell's extent,
+// far wider than the kInsideEps band in reference coordinates): a point
+// outside it is not in K.  The FP32 copy of the box is widened outward, so
+// the test on y's high parts is conservative, with no FP64 instruction.
 template <int D>
-__device__ __forceinline__ int test_cell(const MeshView& m, uint32_t K, const df y[D], float t32[D], df t[D],
-                                         int& iters, unsigned& flags, bool accurate = true) {
-  float s[D];
+__device__ __forceinline__ bool in_cell_box(const MeshView& m, uint32_t K, const df y[D]) {
+  const float4 lo = __ldg(m.bbox32 + 2 * (size_t)K), hi = __ldg(m.bbox32 + 2 * (size_t)K + 1);
+  const float l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+  bool in = true;
 #pragma unroll
-  for (int a = 0; a < D; ++a) s[a] = t32[a];
-  const int r = solve_cell_df<D>(m, K, y, t32, t, iters, accurate);
+  for (int a = 0; a < D; ++a) in = in && y[a].hi >= l[a] && y[a].hi <= h[a];
+  return in;
+}
+
+template <int D, bool kFast = false, class Cells>
+__device__ __forceinline__ int test_cell(const Cells& cs, const MeshView& m, uint32_t K, const df y[D], float t32[D],
+                                         df t[D], int& iters, unsigned& flags, bool accurate = true) {
+  DfPt<D> s;
+#pragma unroll
+  for (int a = 0; a < D; ++a) s.v[a] = df_make(t32[a], 0.f);
+  const int r = solve_cell_df<D>(cs, K, y, t32, t, iters, accurate);
   if (r != kCellFail) return r;
-  flags |= kFlagFallback64;
+  if constexpr (kFast) return kCellDefer;
+  const RarePath<D> o = test_cell_fp64<D>(m, K, pack<D>(y), s);
+  iters += o.iters;
+  flags |= o.flags | kFlagFallback64;
 #pragma unroll
-  for (int a = 0; a < D; ++a) t32[a] = s[a];
-  return test_cell_fp64<D>(m, K, y, t32, t, &iters, &flags);
+  for (int a = 0; a < D; ++a) {
+    t[a] = o.t.v[a];
+    t32[a] = t[a].hi;
+  }
+  return o.r;
 }
 
 // Lowest-index rule (see lowest_owner in locate.cuh) on the fast path.  The
-// band test is inline; the neighbour tests (rare) are out of line.
+// band test is inline; the neighbour tests (rare) are out of line and read
+// the cells from the mesh arrays.
 template <int D>
-__device__ __noinline__ uint32_t lowest_owner_df_slow(const MeshView& m, const df* y, uint32_t found, df* t, int* iters,
-                                                      unsigned* flags) {
+__device__ __noinline__ RarePath<D> lowest_owner_df_slow(const MeshView& m, DfPt<D> y, uint32_t found, DfPt<D> t) {
+  RarePath<D> o;
+  o.iters = 0;
+  o.flags = 0;
+  o.r = kCellIn;
   int c[3];
   cell_ijk<D>(m, found, c);
   int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    lo[a] = (t[a].hi < (float)kTieBand && c[a] > 0) ? -1 : 0;
-    hi[a] = (t[a].hi > 1.0f - (float)kTieBand && c[a] < m.n[a] - 1) ? 1 : 0;
+    lo[a] = (t.v[a].hi < (float)kTieBand && c[a] > 0) ? -1 : 0;
+    hi[a] = (t.v[a].hi > 1.0f - (float)kTieBand && c[a] < m.n[a] - 1) ? 1 : 0;
   }
   uint32_t best = found;
-  df tb[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) tb[a] = t[a];
+  DfPt<D> tb = t;
   for (int o2 = (D == 3 ? lo[2] : 0); o2 <= (D == 3 ? hi[2] : 0); ++o2)
     for (int o1 = lo[1]; o1 <= hi[1]; ++o1)
       for (int o0 = lo[0]; o0 <= hi[0]; ++o0) {
         if (o0 == 0 && o1 == 0 && o2 == 0) continue;
         const uint32_t K = cell_index<D>(m, c[0] + o0, c[1] + o1, c[2] + o2);
         if (K >= best) continue;
-        const int o[3] = {o0, o1, o2};
+        const int off[3] = {o0, o1, o2};
         float s[D];
         df tt[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) s[a] = t[a].hi - (float)o[a];
-        if (test_cell<D>(m, K, y, s, tt, *iters, *flags) == kCellIn) {
+        for (int a = 0; a < D; ++a) s[a] = t.v[a].hi - (float)off[a];
+        if (test_cell<D>(GlobalCells<D, false>{m}, m, K, y.v, s, tt, o.iters, o.flags) == kCellIn) {
           best = K;
-#pragma unroll
-          for (int a = 0; a < D; ++a) tb[a] = tt[a];
+          tb = pack<D>(tt);
         }
       }
-#pragma unroll
-  for (int a = 0; a < D; ++a) t[a] = tb[a];
-  return best;
+  o.K = best;
+  o.t = tb;
+  return o;
 }
 
-template <int D>
+template <int D, bool kFast = false>
 __device__ __forceinline__ uint32_t lowest_owner_df(const MeshView& m, const df y[D], uint32_t found, df t[D],
                                                     int& iters, unsigned& flags) {
   // band test first (cheap); the cell's (i,j,k), which needs integer
@@ -372,25 +489,129 @@ __device__ __forceinline__ uint32_t lowest_owner_df(const MeshView& m, const df 
   for (int a = 0; a < D; ++a)
     any = any || (t[a].hi < (float)kTieBand && c[a] > 0) || (t[a].hi > 1.0f - (float)kTieBand && c[a] < m.n[a] - 1);
   if (!any) return found;
-  return lowest_owner_df_slow<D>(m, y, found, t, &iters, &flags);
+  if constexpr (kFast) return kDefer;
+  const RarePath<D> o = lowest_owner_df_slow<D>(m, pack<D>(y), found, pack<D>(t));
+  iters += o.iters;
+  flags |= o.flags;
+#pragma unroll
+  for (int a = 0; a < D; ++a) t[a] = o.t.v[a];
+  return o.K;
 }
 
-// Past the hint cell and its predicted neighbour: the FP64 walk over the
-// other vertex neighbours (paper's a.b order) and the all-cells search.
+// Past the hint cell and its predicted neighbour: the walk over the hint's
+// other vertex neighbours in the paper's order (Sec. 2.4: v the vertex of the
+// hint closest to y, descending (y - v).(c_K' - v) over the neighbours' centres
+// c_K'), each cell tested with the double-float inverse map (FP64 Newton only
+// where that does not settle), then the all-cells search.  The order only
+// affects the cost: the first cell found is settled by the lowest-index
+// rule, so the ordering heuristic is computed in FP32.  Each candidate's
+// Newton starts from the cell centre.
 template <int D>
-__device__ __noinline__ uint32_t locate_df_slow(const MeshView& m, const df* y, uint32_t hintK, df* t, int* iters,
-                                                unsigned* flags) {
-  double yd[D], th[D], to[D];
+__device__ __noinline__ RarePath<D> locate_df_slow(const MeshView& m, DfPt<D> y, uint32_t hintK) {
+  RarePath<D> o;
+  o.iters = 0;
+  o.flags = 0;
+  o.r = kCellIn;
+  double yd[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    yd[a] = df_to_double(y[a]);
-    th[a] = 0.5;
+  for (int a = 0; a < D; ++a) yd[a] = df_to_double(y.v[a]);
+  bool inside_box = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) inside_box = inside_box && yd[a] >= m.dlo[a] && yd[a] <= m.dhi[a];
+  if (!inside_box) {
+    // outside the padded domain box: in no cell (see locate in locate.cuh)
+    o.K = PIC_LOST;
+#pragma unroll
+    for (int a = 0; a < D; ++a) o.t.v[a] = df_make(0.f, 0.f);
+    return o;
   }
-  const uint32_t K = hintK < m.C ? locate<D>(m, yd, hintK, th, to, *iters, *flags)
-                                 : global_search<D>(m, yd, to, *iters, *flags);
+  if (hintK < m.C) {
+    o.flags |= kFlagWalk;
+    int c[3];
+    cell_ijk<D>(m, hintK, c);
+    // corner positions of cell (i,j,k) from the vertex array, in FP32
+    auto vertex = [&](int i, int j, int k, float p[D]) {
+      const int64_t v = (int64_t)i + (int64_t)m.nv[0] * ((int64_t)j + (D == 3 ? (int64_t)m.nv[1] * k : 0));
 #pragma unroll
-  for (int a = 0; a < D; ++a) t[a] = df_from_double(to[a]);
-  return K;
+      for (int a = 0; a < D; ++a) p[a] = (float)__ldg(m.X + a * m.nverts + v);
+    };
+    float yf[D], v[D], best = 3.4e38f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) yf[a] = y.v[a].hi;
+    for (int q = 0; q < (1 << D); ++q) {
+      float p[D], d2 = 0.f;
+      vertex(c[0] + (q & 1), c[1] + ((q >> 1) & 1), D == 3 ? c[2] + ((q >> 2) & 1) : 0, p);
+#pragma unroll
+      for (int a = 0; a < D; ++a) d2 += (yf[a] - p[a]) * (yf[a] - p[a]);
+      if (d2 < best) {
+        best = d2;
+#pragma unroll
+        for (int a = 0; a < D; ++a) v[a] = p[a];
+      }
+    }
+    constexpr int NN = (D == 3 ? 27 : 9);
+    float score[NN];
+    uint32_t cand = 0;  // bit mask of the neighbours still to test
+    for (int q = 0; q < NN; ++q) {
+      const int o0 = q % 3 - 1, o1 = (q / 3) % 3 - 1, o2 = (D == 3 ? q / 9 - 1 : 0);
+      score[q] = 0.f;
+      if (o0 == 0 && o1 == 0 && o2 == 0) continue;
+      const int i = c[0] + o0, j = c[1] + o1, k = c[2] + o2;
+      if (i < 0 || j < 0 || i >= m.n[0] || j >= m.n[1]) continue;
+      if (D == 3 && (k < 0 || k >= m.n[2])) continue;
+      float ctr[D] = {};
+      for (int w = 0; w < (1 << D); ++w) {
+        float p[D];
+        vertex(i + (w & 1), j + ((w >> 1) & 1), D == 3 ? k + ((w >> 2) & 1) : 0, p);
+#pragma unroll
+        for (int a = 0; a < D; ++a) ctr[a] += p[a] * (1.f / (1 << D));
+      }
+      float sc = 0.f;
+#pragma unroll
+      for (int a = 0; a < D; ++a) sc += (yf[a] - v[a]) * (ctr[a] - v[a]);
+      score[q] = sc;
+      cand |= 1u << q;
+    }
+    const GlobalCells<D, false> cs{m};
+    while (cand) {
+      int qb = __ffs(cand) - 1;  // a valid candidate even if every score is NaN
+      float sb = score[qb];
+      for (int q = qb + 1; q < NN; ++q)
+        if (((cand >> q) & 1u) && score[q] > sb) {
+          sb = score[q];
+          qb = q;
+        }
+      cand &= ~(1u << qb);
+      const int off[3] = {qb % 3 - 1, (qb / 3) % 3 - 1, D == 3 ? qb / 9 - 1 : 0};
+      const uint32_t K = cell_index<D>(m, c[0] + off[0], c[1] + off[1], c[2] + off[2]);
+      if (!in_cell_box<D>(m, K, y.v)) continue;  // cannot hold y: no Newton there
+      float s32[D];
+      df tt[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) s32[a] = 0.5f;  // from the cell centre (R2)
+      if (test_cell<D>(cs, m, K, y.v, s32, tt, o.iters, o.flags) == kCellIn) {
+        o.K = lowest_owner_df<D>(m, y.v, K, tt, o.iters, o.flags);
+        o.t = pack<D>(tt);
+        return o;
+      }
+    }
+  }
+  double to[D];
+  o.K = global_search<D>(m, yd, to, o.iters, o.flags);
+#pragma unroll
+  for (int a = 0; a < D; ++a) o.t.v[a] = df_from_double(to[a]);
+  return o;
+}
+
+template <int D>
+__device__ __forceinline__ uint32_t locate_slow(const MeshView& m, const df y[D], uint32_t hintK, df t[D], int& iters,
+                                                unsigned& flags) {
+  const RarePath<D> o = locate_df_slow<D>(m, pack<D>(y), hintK);
+  iters += o.iters;
+  flags |= o.flags;
+#pragma unroll
+  for (int a = 0; a < D; ++a) t[a] = o.t.v[a];
+  return o.K;
 }
 
 // Owner of y (lowest index) and its double-float reference coordinates.
@@ -402,12 +623,14 @@ __device__ __noinline__ uint32_t locate_df_slow(const MeshView& m, const df* y, 
 // rule.
 constexpr int kPredictedHops = 2;
 
-template <int D>
-__device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], uint32_t hintK, const float hint_t[D],
-                                              df t[D], int& iters, unsigned& flags, bool accurate = true) {
+template <int D, bool kFast = false, class Cells>
+__device__ __forceinline__ uint32_t locate_df(const Cells& cs, const MeshView& m, const df y[D], uint32_t hintK,
+                                              const float hint_t[D], df t[D], int& iters, unsigned& flags,
+                                              bool accurate = true) {
   if (hintK >= m.C) {
+    if constexpr (kFast) return kDefer;
     flags |= kFlagBounds;
-    return locate_df_slow<D>(m, y, hintK, t, &iters, &flags);
+    return locate_slow<D>(m, y, hintK, t, iters, flags);
   }
   float t32[D];
 #pragma unroll
@@ -415,8 +638,10 @@ __device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], 
   uint32_t K = hintK;
 #pragma unroll 1
   for (int pass = 0; pass <= kPredictedHops; ++pass) {
-    const int r = test_cell<D>(m, K, y, t32, t, iters, flags, accurate);
-    if (r == kCellIn) return lowest_owner_df<D>(m, y, K, t, iters, flags);
+    const int r = test_cell<D, kFast>(cs, m, K, y, t32, t, iters, flags, accurate);
+    if constexpr (kFast)
+      if (r == kCellDefer) return kDefer;
+    if (r == kCellIn) return lowest_owner_df<D, kFast>(m, y, K, t, iters, flags);
     if (pass == kPredictedHops || r != kCellOut) break;
     flags |= kFlagWalk;
     int c[3], pred[3] = {0, 0, 0};
@@ -432,8 +657,16 @@ __device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], 
     if (!have_pred) break;
     K = cell_index<D>(m, c[0] + pred[0], c[1] + pred[1], c[2] + pred[2]);
   }
+  if constexpr (kFast) return kDefer;
   flags |= kFlagWalk | kFlagWalk64;
-  return locate_df_slow<D>(m, y, hintK, t, &iters, &flags);
+  return locate_slow<D>(m, y, hintK, t, iters, flags);
+}
+
+// The same reading every block from the mesh arrays.
+template <int D>
+__device__ __forceinline__ uint32_t locate_df(const MeshView& m, const df y[D], uint32_t hintK, const float hint_t[D],
+                                              df t[D], int& iters, unsigned& flags, bool accurate = true) {
+  return locate_df<D>(GlobalCells<D, false>{m}, m, y, hintK, hint_t, t, iters, flags, accurate);
 }
 
 // ---------------------------------------------------------- Q2 velocity --
@@ -478,14 +711,13 @@ __device__ __forceinline__ df centred(df t) {
   return fast_two_sum(d.hi, __fadd_rn(d.lo, t.lo));
 }
 
-template <int D>
-__device__ __forceinline__ void q2_eval_df(const MeshView& m, const float4* __restrict__ Qc, uint32_t K, const df t[D],
-                                           df u[D]) {
+// From the cell's Qc block `cell`, read through ld.ld().
+template <int D, class Ld>
+__device__ __forceinline__ void q2_eval_df(const Ld& ld, const float4* cell, const df t[D], df u[D]) {
   constexpr int NS = (D == 3 ? 3 : 1);
   df s[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) s[a] = centred(t[a]);
-  const float4* cell = Qc + (size_t)K * D * (5 * NS);
 #pragma unroll 1
   for (int comp = 0; comp < D; ++comp) {
     const float4* cq = cell + comp * (5 * NS);
@@ -495,7 +727,7 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, const float4* __re
       float f[20];  // ten high parts, then ten low parts
 #pragma unroll
       for (int k = 0; k < 5; ++k) {
-        const float4 v = __ldg(cq + 5 * r + k);
+        const float4 v = ld.ld(cq + 5 * r + k);
         f[4 * k] = v.x;
         f[4 * k + 1] = v.y;
         f[4 * k + 2] = v.z;
@@ -509,44 +741,51 @@ __device__ __forceinline__ void q2_eval_df(const MeshView& m, const float4* __re
       for (int q = 0; q < 3; ++q) h[q] = df_horner(df_horner(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
       g[r] = df_horner(df_horner(h[2], s[1], h[1]), s[1], h[0]);
     }
+    df rr;
     if constexpr (D == 3)
-      u[comp] = df_norm(df_horner(df_horner(g[2], s[2], g[1]), s[2], g[0]));
+      rr = df_norm(df_horner(df_horner(g[2], s[2], g[1]), s[2], g[0]));
     else
-      u[comp] = df_norm(g[0]);
+      rr = df_norm(g[0]);
+    // constant indices keep u in registers under the rolled loop
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a == comp) u[a] = rr;
   }
 }
 
-// FP32 basis and contraction (precision form): the same monomial form on
-// the high parts, FP32 Horner steps.
-template <int D>
-__device__ __forceinline__ void q2_eval_f32(const MeshView& m, const float4* __restrict__ Qc, uint32_t K, const df t[D],
-                                            df u[D]) {
+// FP32 basis and contraction (precision form) from the cell's Qf block: the
+// same monomial form on the high parts, FP32 Horner steps.
+template <int D, class Ld>
+__device__ __forceinline__ void q2_eval_f32(const Ld& ld, const float4* cell, const df t[D], df u[D]) {
   constexpr int NS = (D == 3 ? 3 : 1);
+  constexpr int NF4 = qf_floats_per_comp<D>() / 4;  // float4 per component
   float s[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) s[a] = t[a].hi - 0.5f;
-  const float4* cell = Qc + (size_t)K * D * (5 * NS);
 #pragma unroll
   for (int comp = 0; comp < D; ++comp) {
-    const float4* cq = cell + comp * (5 * NS);
+    float c[4 * NF4];
+#pragma unroll
+    for (int k = 0; k < NF4; ++k) {
+      const float4 v = ld.ld(cell + comp * NF4 + k);
+      c[4 * k] = v.x;
+      c[4 * k + 1] = v.y;
+      c[4 * k + 2] = v.z;
+      c[4 * k + 3] = v.w;
+    }
     float g[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) {
-      float c[12];  // the high parts lead the slice: three float4
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const float4 v = __ldg(cq + 5 * r + k);
-        c[4 * k] = v.x;
-        c[4 * k + 1] = v.y;
-        c[4 * k + 2] = v.z;
-        c[4 * k + 3] = v.w;
-      }
       float h[3];
 #pragma unroll
-      for (int q = 0; q < 3; ++q) h[q] = fmaf(fmaf(c[3 * q + 2], s[0], c[3 * q + 1]), s[0], c[3 * q]);
+      for (int q = 0; q < 3; ++q) h[q] = fmaf(fmaf(c[9 * r + 3 * q + 2], s[0], c[9 * r + 3 * q + 1]), s[0], c[9 * r + 3 * q]);
       g[r] = fmaf(fmaf(h[2], s[1], h[1]), s[1], h[0]);
     }
-    u[comp] = df_make((D == 3) ? fmaf(fmaf(g[2], s[2], g[1]), s[2], g[0]) : g[0], 0.f);
+    const df rr = df_make((D == 3) ? fmaf(fmaf(g[2], s[2], g[1]), s[2], g[0]) : g[0], 0.f);
+    // constant indices keep u in registers under a rolled loop
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      if (a == comp) u[a] = rr;
   }
 }
 

@@ -101,7 +101,7 @@ __device__ __forceinline__ double unit53(uint64_t r) { return (double)(r >> 11) 
 // ------------------------------------------------------------ cell weights
 
 template <int D>
-__global__ void __launch_bounds__(128) cell_weights_kernel(MeshView m, const double* __restrict__ rho,
+__global__ void __launch_bounds__(128) cell_weights_kernel(const __grid_constant__ MeshView m, const double* __restrict__ rho,
                                                            double* __restrict__ w) {
   const double g0 = __dsub_rn(0.5, __ddiv_rn(0.5, __dsqrt_rn(3.0)));
   const double g1 = __dadd_rn(0.5, __ddiv_rn(0.5, __dsqrt_rn(3.0)));
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) draw_cells_kernel(const double* __restric
 // g (D+1) + a (proposal coordinate a) and g (D+1) + D (acceptance uniform).
 // States J, 2J, ... become the cell's particles, in order.
 template <int D>
-__global__ void __launch_bounds__(128) mh_seed_kernel(MeshView m, StoreView s, const uint32_t* __restrict__ cell_off,
+__global__ void __launch_bounds__(128) mh_seed_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s, const uint32_t* __restrict__ cell_off,
                                                       const double* __restrict__ rho, uint32_t J, uint64_t seed,
                                                       uint64_t first_id) {
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
@@ -259,7 +259,7 @@ __global__ void import_ids_kernel(const uint32_t* __restrict__ rank, size_t n, u
 }
 
 template <int D>
-__global__ void import_gather_kernel(StoreView s, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ kept_p,
+__global__ void import_gather_kernel(const __grid_constant__ StoreView s, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ kept_p,
                                      size_t n, const double* __restrict__ x, const double* __restrict__ xh,
                                      const uint32_t* __restrict__ cell, const uint64_t* __restrict__ id) {
   const uint32_t kept = *kept_p;

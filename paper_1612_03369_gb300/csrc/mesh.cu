@@ -6,17 +6,34 @@
 #include <vector>
 
 #include "df.cuh"
+#include "fastpath.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
 
 // Padded bounding box of every cell (lo xyz, hi xyz): the all-cells search
 // of Sec. 2.4 only runs the inverse map in cells whose box holds the point.
+// The FP32 copy is rounded outward and widened by four ulps, so that a test
+// of a double-float point's high part against it never rejects a point of
+// the FP64 box.
+__device__ __forceinline__ float widen_down(double v) {
+  float f = __double2float_rd(v);
+  for (int k = 0; k < 4; ++k) f = nextafterf(f, -INFINITY);
+  return f;
+}
+__device__ __forceinline__ float widen_up(double v) {
+  float f = __double2float_ru(v);
+  for (int k = 0; k < 4; ++k) f = nextafterf(f, INFINITY);
+  return f;
+}
+
 template <int D>
-__global__ void cell_bbox_kernel(MeshView m, double* __restrict__ bbox) {
+__global__ void cell_bbox_kernel(const __grid_constant__ MeshView m, double* __restrict__ bbox,
+                                 float4* __restrict__ bbox32) {
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
     CellGeom<D> g;
     load_cell<D>(m, K, g);
+    float lo32[3], hi32[3];
     for (int a = 0; a < 3; ++a) {
       double lo = 0.0, hi = 0.0;
       if (a < D) {
@@ -31,7 +48,11 @@ __global__ void cell_bbox_kernel(MeshView m, double* __restrict__ bbox) {
       }
       bbox[6 * (size_t)K + a] = lo;
       bbox[6 * (size_t)K + 3 + a] = hi;
+      lo32[a] = widen_down(lo);
+      hi32[a] = widen_up(hi);
     }
+    bbox32[2 * (size_t)K] = make_float4(lo32[0], lo32[1], lo32[2], 0.f);
+    bbox32[2 * (size_t)K + 1] = make_float4(hi32[0], hi32[1], hi32[2], 0.f);
   }
 }
 
@@ -50,7 +71,7 @@ __device__ __forceinline__ float2 split_df(double v) {
 // the NF low parts in the same order, so that the FP32 Newton iterations
 // read only the first half.
 template <int D>
-__global__ void cell_block_kernel(MeshView m, float* __restrict__ blk) {
+__global__ void cell_block_kernel(const __grid_constant__ MeshView m, float* __restrict__ blk) {
   constexpr int NK = (1 << D) - 1;
   constexpr int NF = D + NK * D;
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
@@ -85,7 +106,7 @@ __global__ void cell_block_kernel(MeshView m, float* __restrict__ blk) {
 
 // Index of node (2i, 2j, 2k), the first Q2 node of cell (i, j, k).
 template <int D>
-__global__ void cell_qbase_kernel(MeshView m, uint32_t* __restrict__ qbase) {
+__global__ void cell_qbase_kernel(const __grid_constant__ MeshView m, uint32_t* __restrict__ qbase) {
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < m.C; K += gridDim.x * blockDim.x) {
     int c[3];
     cell_ijk<D>(m, K, c);
@@ -121,9 +142,12 @@ __device__ __forceinline__ void t_axis(df v0, df v1, df v2, df& c0, df& c1, df& 
   c2 = df_sub(df_scale2(df_add(v0, v2), 2.0f), df_scale2(v1, 4.0f));
 }
 
+// With Qf given, the block also writes the coefficients' high parts, per
+// cell and component in the order r*9 + q*3 + p, padded to 28 (3D) or 12
+// (2D) floats: the FP32-basis form's table.
 template <int D>
-__global__ void __launch_bounds__(32 * D) q2_coeff_kernel(MeshView m, const float2* __restrict__ U2,
-                                                          float4* __restrict__ Qc) {
+__global__ void __launch_bounds__(32 * D) q2_coeff_kernel(const __grid_constant__ MeshView m, const float2* __restrict__ U2,
+                                                          float4* __restrict__ Qc, float4* __restrict__ Qf) {
   // A block builds the coefficients of a group of 32 consecutive cells:
   // thread (comp, lane) does cell K0 + lane, component comp (neighbouring
   // lanes read neighbouring nodes of one component), leaves its 5 NS float4
@@ -131,7 +155,9 @@ __global__ void __launch_bounds__(32 * D) q2_coeff_kernel(MeshView m, const floa
   // which is contiguous ([K][comp][5 NS]), with coalesced float4 stores.
   constexpr int NS = (D == 3 ? 3 : 1);
   constexpr int PER = 5 * NS;  // float4 per (cell, component)
+  constexpr int PERF = qf_floats_per_comp<D>();  // floats per (cell, component) of Qf
   __shared__ float4 sh[32 * D * PER];
+  __shared__ __align__(16) float shf[32 * D * PERF];
   const int lane = threadIdx.x & 31, comp = threadIdx.x >> 5;
   const int64_t sy = m.nq[0], sz = (int64_t)m.nq[0] * m.nq[1];
   for (uint32_t K0 = blockIdx.x * 32u; K0 < m.C; K0 += gridDim.x * 32u) {
@@ -176,19 +202,33 @@ __global__ void __launch_bounds__(32 * D) q2_coeff_kernel(MeshView m, const floa
 #pragma unroll
         for (int k = 0; k < 5; ++k) out[5 * r + k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
       }
+      float* outf = shf + (lane * D + comp) * PERF;
+#pragma unroll
+      for (int r = 0; r < NS; ++r)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) outf[9 * r + e] = V[r][e / 3][e % 3].hi;
+#pragma unroll
+      for (int e = 9 * NS; e < PERF; ++e) outf[e] = 0.f;
     }
     __syncthreads();
     const uint32_t ncell = (m.C - K0) < 32u ? (m.C - K0) : 32u;
     const uint32_t nf4 = ncell * D * PER;
     float4* dst = Qc + (size_t)K0 * D * PER;
     for (uint32_t q = threadIdx.x; q < nf4; q += blockDim.x) dst[q] = sh[q];
+    if (Qf) {
+      const uint32_t nff = ncell * D * (PERF / 4);
+      float4* dstf = Qf + (size_t)K0 * D * (PERF / 4);
+      const float4* shf4 = reinterpret_cast<const float4*>(shf);
+      for (uint32_t q = threadIdx.x; q < nff; q += blockDim.x) dstf[q] = shf4[q];
+    }
     __syncthreads();
   }
 }
 
 // Coefficients of one field into Qc: the FP64 values U are first split into
 // the node-major double-float copy U2 (one conversion per nodal value).
-static void build_coefficients(const pic_mesh_s* m, const double* U, float2* U2, float4* Qc, cudaStream_t st) {
+static void build_coefficients(const pic_mesh_s* m, const double* U, float2* U2, float4* Qc, float4* Qf,
+                               cudaStream_t st) {
   const size_t n = (size_t)m->dim * (size_t)m->nnodes;
   const int gn = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   to_df_nodes_kernel<<<gn, 256, 0, st>>>(U, U2, m->dim, (size_t)m->nnodes);
@@ -197,13 +237,38 @@ static void build_coefficients(const pic_mesh_s* m, const double* U, float2* U2,
   const size_t cap = (size_t)num_sms() * 16;
   const int g = (int)(groups < cap ? groups : cap);
   if (m->dim == 2)
-    q2_coeff_kernel<2><<<g, 64, 0, st>>>(v, U2, Qc);
+    q2_coeff_kernel<2><<<g, 64, 0, st>>>(v, U2, Qc, Qf);
   else
-    q2_coeff_kernel<3><<<g, 96, 0, st>>>(v, U2, Qc);
+    q2_coeff_kernel<3><<<g, 96, 0, st>>>(v, U2, Qc, Qf);
   count_launches(2);
 }
 
 static size_t coeff_float4s(const pic_mesh_s* m) { return (size_t)m->C * m->dim * (m->dim == 3 ? 15 : 5); }
+static size_t coeff32_float4s(const pic_mesh_s* m) {
+  return (size_t)m->C * (m->dim == 3 ? qf_float4s<3>() : qf_float4s<2>());
+}
+
+pic_status ensure_fp32_coefficients(pic_mesh_s* m, cudaStream_t st) {
+  if (!m->has_velocity) return PIC_OK;
+  if (!m->Qf) {
+    if (cudaMalloc(&m->Qf, sizeof(float4) * coeff32_float4s(m)) != cudaSuccess) {
+      cudaGetLastError();
+      m->Qf = nullptr;
+      return (set_error("FP32 coefficient table: device allocation failed"), PIC_ERR_OOM);
+    }
+    build_coefficients(m, m->U, m->U2, m->Qc, m->Qf, st);
+  }
+  if (m->has_next && !m->Qfn) {
+    if (cudaMalloc(&m->Qfn, sizeof(float4) * coeff32_float4s(m)) != cudaSuccess) {
+      cudaGetLastError();
+      m->Qfn = nullptr;
+      return (set_error("FP32 coefficient table: device allocation failed"), PIC_ERR_OOM);
+    }
+    build_coefficients(m, m->Un, m->U2n, m->Qcn, m->Qfn, st);
+  }
+  PIC_CUDA(cudaGetLastError());
+  return PIC_OK;
+}
 
 
 }  // namespace pic
@@ -244,6 +309,7 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   const size_t blk_f4 = dim == 3 ? 12 : 4;
   if (cudaMalloc(&m->X, sizeof(double) * dim * nv) != cudaSuccess ||
       cudaMalloc(&m->bbox, sizeof(double) * 6 * C) != cudaSuccess ||
+      cudaMalloc(&m->bbox32, sizeof(float4) * 2 * C) != cudaSuccess ||
       cudaMalloc(&m->blk, sizeof(float4) * blk_f4 * C) != cudaSuccess ||
       cudaMalloc(&m->qbase, sizeof(uint32_t) * C) != cudaSuccess) {
     cudaGetLastError();
@@ -281,11 +347,11 @@ extern "C" pic_status pic_create_mesh(int dim, const int* n_cells, const double*
   const MeshView mv = mesh_view(m);
   const int grid = (int)((C + 255) / 256 < 4096 ? (C + 255) / 256 : 4096);
   if (dim == 2) {
-    cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox);
+    cell_bbox_kernel<2><<<grid, 256, 0, st>>>(mv, m->bbox, m->bbox32);
     cell_block_kernel<2><<<grid, 256, 0, st>>>(mv, (float*)m->blk);
     cell_qbase_kernel<2><<<grid, 256, 0, st>>>(mv, m->qbase);
   } else {
-    cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox);
+    cell_bbox_kernel<3><<<grid, 256, 0, st>>>(mv, m->bbox, m->bbox32);
     cell_block_kernel<3><<<grid, 256, 0, st>>>(mv, (float*)m->blk);
     cell_qbase_kernel<3><<<grid, 256, 0, st>>>(mv, m->qbase);
   }
@@ -304,6 +370,7 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->X);
   cudaFree(m->U);
   cudaFree(m->bbox);
+  cudaFree(m->bbox32);
   cudaFree(m->blk);
   cudaFree(m->qbase);
   cudaFree(m->U2);
@@ -311,6 +378,8 @@ extern "C" pic_status pic_destroy_mesh(pic_mesh m) {
   cudaFree(m->U2n);
   cudaFree(m->Qc);
   cudaFree(m->Qcn);
+  cudaFree(m->Qf);
+  cudaFree(m->Qfn);
   free(m);
   return PIC_OK;
 }
@@ -333,11 +402,18 @@ extern "C" pic_status pic_set_velocity_dofs(pic_mesh m, const double* U, const d
       return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
     }
   }
+  if (U_next && m->Qf && !m->Qfn) {
+    if (cudaMalloc(&m->Qfn, sizeof(float4) * coeff32_float4s(m)) != cudaSuccess) {
+      cudaGetLastError();
+      m->Qfn = nullptr;
+      return (set_error("pic_set_velocity_dofs: device allocation failed"), PIC_ERR_OOM);
+    }
+  }
   PIC_CUDA(cudaMemcpyAsync(m->U, U, sizeof(double) * n, cudaMemcpyDefault, st));
-  build_coefficients(m, m->U, m->U2, m->Qc, st);
+  build_coefficients(m, m->U, m->U2, m->Qc, m->Qf, st);
   if (U_next) {
     PIC_CUDA(cudaMemcpyAsync(m->Un, U_next, sizeof(double) * n, cudaMemcpyDefault, st));
-    build_coefficients(m, m->Un, m->U2n, m->Qcn, st);
+    build_coefficients(m, m->Un, m->U2n, m->Qcn, m->Qfn, st);
   }
   PIC_CUDA(cudaGetLastError());
   m->has_velocity = 1;
@@ -382,7 +458,7 @@ extern "C" pic_status pic_commit_velocity_dofs(pic_mesh m, void* stream) {
   double* t = m->U;
   m->U = m->Ustage;
   m->Ustage = t;
-  build_coefficients(m, m->U, m->U2, m->Qc, st);
+  build_coefficients(m, m->U, m->U2, m->Qc, m->Qf, st);
   PIC_CUDA(cudaGetLastError());
   PIC_CUDA(cudaEventRecord(m->ev_free, st));
   m->free_recorded = 1;

@@ -262,7 +262,7 @@ extern "C" pic_status pic_get_counters(pic_particles p, uint64_t* values, int n_
   pic_status r = read_counters(p, &h);
   if (r != PIC_OK) return r;
   const uint64_t v[PIC_N_COUNTERS] = {h.particle_steps, h.walks, h.global_searches, h.newton_iterations,
-                                      h.lost_total, h.fallback64, h.walk64};
+                                      h.lost_total, h.fallback64, h.walk64, h.deferred};
   for (int k = 0; k < n_values && k < PIC_N_COUNTERS; ++k) values[k] = v[k];
   return PIC_OK;
 }

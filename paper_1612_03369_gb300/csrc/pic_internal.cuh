@@ -42,10 +42,13 @@ struct DevCounters {
   unsigned long long lost_total;
   unsigned long long fallback64;  // particle-steps where a cell went to the FP64 Newton
   unsigned long long walk64;      // particle-steps where the walk went past the predicted neighbour
+  unsigned long long deferred;    // particle-steps the advect kernel redid on the full path (a rare path was needed)
   unsigned int status;
   unsigned int n_alive;  // particles in the store
   unsigned int n_next;   // particles after the pending rebin
   unsigned int fail_count;
+  unsigned int tile_next;  // work counter of the advect kernel's dynamic tiles (cleared before each launch)
+  unsigned int pad_;
 };
 
 }  // namespace pic
@@ -60,6 +63,7 @@ struct pic_mesh_s {
   double* X;     // [dim][nverts]
   double* U;     // [dim][nnodes]
   double* bbox;  // [C][6] padded cell bounding boxes: lo xyz, hi xyz
+  float4* bbox32;  // [C][2] the same in FP32, rounded outward and widened by a few ulps: lo xyz_, hi xyz_
   float4* blk;   // [C][12 (3D) or 4 (2D)] per-cell map blocks (double-float, see fastpath.cuh)
   uint32_t* qbase;  // [C] index of the cell's first Q2 node (2i, 2j, 2k)
   float2* U2;    // [nnodes][dim] Q2 nodal values as double-floats (hi, lo): the coefficients' source
@@ -67,6 +71,8 @@ struct pic_mesh_s {
   float2* U2n;   // its double-float nodal copy (the source of Qcn)
   float4* Qc;    // [C][dim][slices][5] per-cell monomial coefficients (double-float pairs, see fastpath.cuh)
   float4* Qcn;   // the same for the field at the end of the step
+  float4* Qf;    // [C][dim][28 or 12 floats] their high parts (FP32-basis form), allocated on first use
+  float4* Qfn;   // the same for the field at the end of the step
   int has_next;
   double dlo[3], dhi[3];  // padded domain bounding box
   int has_velocity;
@@ -91,6 +97,7 @@ struct pic_particles_s {
   uint32_t* cell[2];
   double* props[2];
   int cur;                // which buffer holds the sorted store
+  int stage_cells;        // pic_advect stages the cells' blocks in shared memory (pic_set_advect_staging)
   uint32_t* cell_off;     // [C+1]
   // scratch for the rebin
   uint32_t* cell_new;     // [capacity]
@@ -131,10 +138,13 @@ struct MeshView {
   const double* X;
   const double* U;
   const double* bbox;
+  const float4* bbox32;
   const float4* blk;
   const uint32_t* qbase;
   const float4* Qc;   // per-cell monomial coefficients of the field (and of the second field)
   const float4* Qcn;
+  const float4* Qf;   // their high parts (FP32-basis form; null until that form is first used)
+  const float4* Qfn;
   int has_next;
   double dlo[3], dhi[3];
 };
@@ -154,10 +164,13 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.X = m->X;
   v.U = m->U;
   v.bbox = m->bbox;
+  v.bbox32 = m->bbox32;
   v.blk = m->blk;
   v.qbase = m->qbase;
   v.Qc = m->Qc;
   v.Qcn = m->Qcn;
+  v.Qf = m->Qf;
+  v.Qfn = m->Qfn;
   v.has_next = m->has_next;
   return v;
 }
@@ -182,6 +195,13 @@ inline StoreView store_view(pic_particles_s* p, int buf) {
   s.cap = p->capacity;
   s.n_props = p->n_props;
   return s;
+}
+
+// Nanoseconds of the GPU's global timer (bounds every device-side wait).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ void latch_status(DevCounters* c, unsigned int bit) {
@@ -408,4 +428,8 @@ pic_status sort_by_cell_run(size_t n, const uint32_t* cell, const uint64_t* id, 
                             uint32_t* cell_off, const SortScratch& sc, cudaStream_t s);
 // Host-side count of kernel launches (instrumentation).
 void count_launches(int n);
+// Allocate and fill the FP32 coefficient tables (Qf, and Qfn with a second
+// field) of the mesh's current fields, if not there yet; later field
+// updates keep them current.  Defined in mesh.cu.
+pic_status ensure_fp32_coefficients(pic_mesh_s* m, cudaStream_t st);
 }  // namespace pic

@@ -34,8 +34,8 @@ struct OdeArgs {
 // positions, cells and order are bit for bit those of pic_advect), leaving
 // each stage's (cell, x-hat) behind.
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kernel(MeshView m, StoreView s, df dt,
-                                                                                  StageRec rec,
+__global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s, df dt,
+                                                                                  const __grid_constant__ StageRec rec,
                                                                                   uint32_t* __restrict__ cell_new,
                                                                                   uint32_t* __restrict__ counts,
                                                                                   DevCounters* __restrict__ ctr) {
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128, PIC_ADVECT_MIN_BLOCKS) advect_record_kern
 // A kernel of its own, so that neither it nor the ODE kernel outgrows the
 // instruction cache.
 template <int D>
-__global__ void __launch_bounds__(128, 4) props_grad_kernel(MeshView m, StageRec rec, int S,
+__global__ void __launch_bounds__(128, 4) props_grad_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StageRec rec, int S,
                                                            const uint32_t* __restrict__ cell_new,
                                                            const DevCounters* __restrict__ ctr,
                                                            float2* __restrict__ Gs) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(128, 4) props_grad_kernel(MeshView m, StageRec
 #endif
 
 template <int D, int RK>
-__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(StoreView s, df dt, OdeArgs o,
+__global__ void __launch_bounds__(128, PIC_PROPS_MIN_BLOCKS) props_ode_kernel(const __grid_constant__ StoreView s, df dt, OdeArgs o,
                                                                               const float2* __restrict__ Gs,
                                                                               const uint32_t* __restrict__ cell_new,
                                                                               const DevCounters* __restrict__ ctr) {

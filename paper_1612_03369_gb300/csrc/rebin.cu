@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) rank_by_id_kernel(const uint32_t* __restr
 }
 
 // Copy every field from the old slot perm[j] to the new slot j.
-__global__ void __launch_bounds__(256) gather_kernel(StoreView src, StoreView dst, const uint32_t* __restrict__ perm, int dim,
+__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ StoreView src, const __grid_constant__ StoreView dst, const uint32_t* __restrict__ perm, int dim,
                                                      DevCounters* __restrict__ ctr) {
   gather_phase(src, dst, perm, dim, ctr->n_alive, &ctr->status, blockIdx.x * blockDim.x + threadIdx.x,
                gridDim.x * blockDim.x);

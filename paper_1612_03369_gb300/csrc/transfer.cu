@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) vertex_partial_kernel(const uint32_t* __r
 // Phase 2, thread per vertex: the partial sums of the cells around the
 // vertex, added in increasing cell index.
 template <int D>
-__global__ void __launch_bounds__(256) vertex_gather_kernel(MeshView m, const double* __restrict__ part,
+__global__ void __launch_bounds__(256) vertex_gather_kernel(const __grid_constant__ MeshView m, const double* __restrict__ part,
                                                             double empty_fill, double* __restrict__ avg,
                                                             double* __restrict__ weight) {
   constexpr int NC = 1 << D;

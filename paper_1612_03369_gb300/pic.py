@@ -60,6 +60,7 @@ SIGNATURES = {
     "pic_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pic_cell_offsets": (_I, [_P, _P, _P]),
     "pic_timing_enable": (_I, [_P, _I]),
+    "pic_set_advect_staging": (_I, [_P, _I]),
     "pic_timing_read": (_I, [_P, _P, _P, _P]),
     "pic_kernel_launches": (_U64, []),
     "pic_ensemble_create": (_I, [_I, _P, _P, _P, _P, _I, _P, _P]),
@@ -303,7 +304,8 @@ def pic_get_stats(parts: int):
     return dict(zip(("particle_steps", "walks", "global_searches", "newton_iterations"), [int(a.value) for a in v]))
 
 
-COUNTER_NAMES = ("particle_steps", "walks", "global_searches", "newton_iterations", "lost", "fallback64", "walk64")
+COUNTER_NAMES = ("particle_steps", "walks", "global_searches", "newton_iterations", "lost", "fallback64", "walk64",
+                 "deferred")
 
 
 def pic_get_counters(parts: int) -> dict:
@@ -315,6 +317,10 @@ def pic_get_counters(parts: int) -> dict:
 def pic_export(parts: int, x=None, xhat=None, id=None, cell=None, props=None, stream=None):
     _check(_lib.pic_export(parts, _ptr(x), _ptr(xhat), _ptr(id), _ptr(cell), _ptr(props), _stream(stream)),
            "pic_export")
+
+
+def pic_set_advect_staging(parts: int, on: bool):
+    _check(_lib.pic_set_advect_staging(parts, 1 if on else 0), "pic_set_advect_staging")
 
 
 def pic_cell_offsets(parts: int, off, stream=None):
