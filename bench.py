@@ -1,29 +1,32 @@
 """Benchmark of the particle hot path: RK4 particle-steps/s for
 advect + locate + rebin on a 3D Q2 mesh, with its HBM roofline fraction.
 
-Workload (default): 3D unit cube, 64^3 hexes with interior vertices jittered
-by up to 0.1 h, Q2 velocity = curl of 8 random-phase sinusoidal vector
-potentials (zero wall-normal flow), 20 particles per cell (5,242,880), three
-FP64 properties, RK4 at CFL 0.5.  One benchmark step = one time step of every
-particle (advect with located stages, final locate, rebin into the
-(cell, id)-sorted store).  The particle state (~440 MB) is larger than L2,
-so no L2 flush is needed between steps.
+Workload (default, c3): 3D unit cube, 128^3 hexes with interior vertices
+jittered by up to 0.1 h, Q2 velocity = curl of 8 random-phase sinusoidal
+vector potentials (zero wall-normal flow), 20 particles per cell
+(41,943,040), three FP64 properties, RK4 at CFL 0.5.  One benchmark step =
+one time step of every particle (advect with located stages, final locate,
+rebin into the (cell, id)-sorted store).  The particle state (~3.5 GB) is
+far larger than L2, so no L2 flush is needed between steps.  `value` is the
+FP64 form (double-float arithmetic, FP64 storage); the same line carries the
+FP32-basis form's rate on the same workload and its position and cell-average
+error against the FP64 form over the configuration's 20 steps, measured on
+every particle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config c2|c1|c3|c4|c5]
+                  [--config c3|c2|c1|c4|c5|c2p|next]
 
-c3 is the precision form (FP32 basis) at 128^3; c4 times the adjoint
-(recorded forward + reverse sweep) at 32^3 x 32 per cell over 20 steps; c5
-times the 64-problem ensemble (10 steps per persistent graph launch); c2p
-times c2 with the damage and deformation-gradient ODEs; next times the rows
-after the hot path (time interpolation, property ODEs, transfers,
-generation) on the c2 workload.  The default is c2.
+c2 is the 64^3 FP64 workload; c4 times the adjoint (recorded forward +
+reverse sweep) at 32^3 x 32 per cell over 20 steps; c5 times the 64-problem
+ensemble (10 steps per persistent graph launch); c2p times c2 with the damage
+and deformation-gradient ODEs; next times the rows after the hot path (time
+interpolation, property ODEs, transfers, generation) on the c2 workload.
 
 Under torchrun (N > 1) every rank advances its own replica of c1-c3
 (independent problems, no data-path collective: weak scaling), and the 64
 members of c5 are dealt out to the ranks by particle count (strong
-scaling); the time is the maximum over ranks.  --impl reference times the CPU oracle on the host
-cores on a bounded sample of the same workload.
+scaling); the time is the maximum over ranks.  --impl reference times the CPU
+oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -44,32 +47,40 @@ sys.path.insert(0, ROOT)
 from paper_1612_03369_gb300 import workloads as W  # noqa: E402
 from paper_1612_03369_gb300 import shard  # noqa: E402
 
-# Algorithmic bytes per particle-step of the whole step and of the advect
-# kernel (FP64 form, 3D, P properties, u64 ids): each particle's state is
-# read and written once, cell data (8 unique Q2 nodes x 3 x 8 B + one vertex
-# x 3 x 8 B + a u32 offset) amortised over the particles per cell.
-def step_bytes(dim: int, n_props: int, ppc: float, xhat_bytes: int = 8) -> float:
+# Algorithmic bytes per particle-step (the method's data movement): each
+# particle's state (x, x-hat, u64 id, P properties) read once and written
+# once, the new-cell key written and read, and the cell data (8 unique Q2
+# nodes x 3 components + one vertex, and a u32 offset) amortised over the
+# particles per cell.  The FP32-basis form counts x-hat and the DOFs as FP32.
+def step_bytes(dim: int, n_props: int, ppc: float, xhat_bytes: int = 8, dof_bytes: int = 8) -> float:
     state = dim * 8 + dim * xhat_bytes + 8 + n_props * 8
-    cell_data = ((2 ** dim) * dim * 8 + dim * 8 + 4) / ppc
+    cell_data = ((2 ** dim) * dim * dof_bytes + dim * 8 + 4) / ppc
     return 2 * state + 8 + cell_data
 
 
-def advect_bytes(dim: int, ppc: float, n_props: int, xhat_bytes: int = 8) -> float:
-    # reads x, x-hat, cell; writes x, x-hat, new cell; cell data amortised;
-    # the step also carries the id and properties into the new order (the
-    # previous step's rebin order is applied on the way)
-    return 2 * (dim * 8 + dim * xhat_bytes + 4 + 8 + n_props * 8) + ((2 ** dim) * dim * 8 + dim * 8) / ppc
+# The advect kernel's share: it reads x, x-hat, cell, id and the properties and
+# writes them in the new order with the new cell; cell data amortised.
+def advect_bytes(dim: int, ppc: float, n_props: int, xhat_bytes: int = 8, dof_bytes: int = 8) -> float:
+    return 2 * (dim * 8 + dim * xhat_bytes + 4 + 8 + n_props * 8) + ((2 ** dim) * dim * dof_bytes + dim * 8) / ppc
 
 
-# From the ncu capture summarised in profiles/advect_kernel_c2_64cubed.md
-# (current advect kernel, 64^3 workload, RK4, FP64 form, steady field): FP32
-# flops executed per particle-step (FFMA counted as 2) and DRAM bytes per
-# particle per launch.  They describe that kernel on that workload only.
-ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP = 9074.6
-ADVECT_C2_DRAM_BYTES_PER_PARTICLE = 1566.81e6 / 5242880
-# FP32 peak derived from unit counts and the maximum SM clock: 152 SMs x 128
-# FP32 lanes x 2 flops (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per particle of one launch of the advect kernel,
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# current kernel on the 64^3 x 20 workload, RK4, in the middle of a
+# multi-step call; traffic grows with the particle count, so a launch at
+# another size is scaled by its particles.  Keyed by precision (0 FP64
+# form, 1 FP32-basis form).
+ADVECT_DRAM_BYTES_PER_PARTICLE = {0: 1181.538e6 / 5242880, 1: 1023.133e6 / 5242880}
+# Warp instructions per 32 particle-steps and pipe utilisation of the same
+# captures: the advect kernel is bound by instruction issue (double-float
+# arithmetic on the FP32 pipe) in the FP64 form, and by issue and load
+# latency in the FP32-basis form, not by HBM.
+ADVECT_ISSUE = {
+    0: {"warp_instructions_per_32_particle_steps": 10888, "issue_active_pct": 74.0, "fma_pipe_active_pct": 58.9,
+        "top_stall": "not_selected 2.36 per issue (issue-bound)"},
+    1: {"warp_instructions_per_32_particle_steps": 4520, "issue_active_pct": 63.2, "fma_pipe_active_pct": 39.2,
+        "top_stall": "long_scoreboard 3.85 per issue"},
+}
 
 
 def load_peaks():
@@ -87,7 +98,9 @@ def workload(name: str, n: int | None = None):
     if name == "c1":
         return W.c1() if n is None else W.c1(n=n)
     if name == "c3":
-        return W.c3() if n is None else W.c3(n=n)
+        wl = W.c3() if n is None else W.c3(n=n)
+        wl.name = "c3_3d_curl_%d^3" % wl.n[0]
+        return wl
     return W.c2() if n is None else W.c2(n=n)
 
 
@@ -140,6 +153,82 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _seed(P, mesh, wl):
+    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
+    st = parts.export()
+    for q in range(min(wl.n_props, wl.dim)):
+        parts.set_property(q, st["x"][q].contiguous())  # property q = initial coordinate q
+    del st
+    return parts
+
+
+def _timed_advect(P, parts, wl, precision, steps, warmup, stream, barrier, clocks=None):
+    """warmup untimed steps, then `steps` steps between CUDA events on the
+    stream, with the library's per-step advect / rebin events on.  Returns
+    (ms, advect ms per step, rebin ms per step, particle-steps, counter
+    deltas, clock record or None)."""
+    import torch
+
+    parts.advect(wl.dt, wl.integrator, warmup, precision)
+    torch.cuda.synchronize()
+    c0 = parts.stats()
+    P.pic_timing_enable(parts.h, True)
+    if clocks is not None:
+        clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    parts.advect(wl.dt, wl.integrator, steps, precision)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks is not None else None
+    P.pic_timing_enable(parts.h, False)
+    adv, reb, nsteps = P.pic_timing_read(parts.h)
+    c1 = parts.stats()
+    d = {k: c1[k] - c0[k] for k in c1}
+    return e0.elapsed_time(e1), adv / max(nsteps, 1), reb / max(nsteps, 1), d["particle_steps"], d, clk
+
+
+def _accuracy_fp32_basis(P, mesh, wl):
+    """Both forms from the same seeded store over the configuration's steps;
+    every particle compared by id, and the per-cell averages of property 0.
+    The FP64 form is the reference here: it matches the CPU oracle to 1e-12
+    in positions and cell averages (the parity tests), far below the FP32
+    basis's error."""
+    import torch
+
+    out = {}
+    runs = []
+    for prec in (P.PIC_FP64, P.PIC_FP32_BASIS):
+        parts = _seed(P, mesh, wl)
+        parts.advect(wl.dt, wl.integrator, wl.n_steps, prec)
+        e = parts.export()
+        avg, cnt = parts.average(0)
+        runs.append((e["x"], e["id"], avg, cnt))
+        del e
+        parts.close()
+    (x64, id64, a64, c64), (x32, id32, a32, c32) = runs
+    N0 = wl.n_particles
+    pos = torch.full((N0,), -1, dtype=torch.int64, device=x64.device)
+    pos[id32 - wl.first_id] = torch.arange(id32.numel(), device=x64.device)
+    p32 = pos[id64 - wl.first_id]
+    both = p32 >= 0
+    dx = (x64[:, both] - x32[:, p32[both]]).abs().amax(dim=0)
+    diff_cells = (a64 != a32) | (c64 != c32)
+    out.update({
+        "reference": "the FP64 form on the GPU (itself within 1e-12 of the CPU oracle in the parity tests)",
+        "steps": wl.n_steps, "particles_compared": int(both.sum()),
+        "lost_fp64_form": int(N0 - id64.numel()), "lost_fp32_basis_form": int(N0 - id32.numel()),
+        "max_position_error": float(dx.max()), "rms_position_error": float(dx.pow(2).mean().sqrt()),
+        "cells_with_different_average": int(diff_cells.sum()),
+        "max_cell_average_error": float((a64 - a32).abs().max()),
+        "cells_with_different_count": int((c64 != c32).sum()),
+    })
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1612_03369_gb300 import pic as P
@@ -147,13 +236,9 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     wl = workload(args.config, args.mesh)
-    precision = P.PIC_FP32_BASIS if args.config == "c3" else P.PIC_FP64
+    precision = P.PIC_FP64
     mesh = P.Mesh(wl.n, wl.X, wl.U)
-    parts = P.Particles(mesh, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
-    st = parts.export()
-    for q in range(min(wl.n_props, wl.dim)):
-        parts.set_property(q, st["x"][q].contiguous())
-    del st
+    parts = _seed(P, mesh, wl)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -162,36 +247,18 @@ def run_ours(args, rank, world, local_rank):
 
             dist.barrier()
 
-    # warm-up
-    parts.advect(wl.dt, wl.integrator, args.warmup, precision)
-    torch.cuda.synchronize()
-    n0, _, _ = parts.state()
-    stats0 = parts.stats()
     launches0 = P.pic_kernel_launches()
-    P.pic_timing_enable(parts.h, True)
-    clocks = ClockSampler(local_rank)
-    clocks.start()
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    parts.advect(wl.dt, wl.integrator, args.steps, precision)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clk = clocks.stop()
-    P.pic_timing_enable(parts.h, False)
+    ms, adv_avg_ms, reb_avg_ms, psteps, cdelta, clk = _timed_advect(
+        P, parts, wl, precision, args.steps, args.warmup, stream, barrier, ClockSampler(local_rank))
     launches = P.pic_kernel_launches() - launches0
-    ms = e0.elapsed_time(e1)
-    adv_ms, reb_ms, nsteps = P.pic_timing_read(parts.h)
-    stats1 = parts.stats()
-    psteps = stats1["particle_steps"] - stats0["particle_steps"]
     n1, nlost, status = parts.state()
 
     # ---- the other particle -> field transfers (Sec. 2.7), timed on their
-    # own after the step loop: shape-function-weighted vertex averages (iv)
-    # and the per-cell linear least squares (v) of property 0
+    # own after the step loop: the cell averages (ii), shape-function-weighted
+    # vertex averages (iv) and the per-cell linear least squares (v) of
+    # property 0
     xfer = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, fn in (("cell_average_ms", lambda: parts.average(0)),
                      ("vertex_average_ms", lambda: parts.vertex_average(0)),
                      ("project_linear_ms", lambda: parts.project_linear(0))):
@@ -266,17 +333,36 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     assert len(checks) == e2e_steps
 
+    # ---- the FP32-basis form (precision form) on the same workload, its own
+    # store; and its error against the FP64 form over the configuration's steps
+    # (after the end-to-end steps: from its first use on, every field update
+    # also builds the FP32 coefficient table)
+    fp32 = None
+    if args.config == "c3":
+        p32 = _seed(P, mesh, wl)
+        ms32, adv32, reb32, ps32, cd32, _ = _timed_advect(P, p32, wl, P.PIC_FP32_BASIS, args.steps, args.warmup,
+                                                         stream, barrier)
+        p32.close()
+        fp32 = {"value": ps32 / (ms32 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms32 / args.steps,
+                "advect_ms_per_step": adv32, "rebin_ms_per_step": reb32,
+                "algorithmic_bytes_per_particle_step": step_bytes(wl.dim, wl.n_props, wl.ppc, 4, 4),
+                "newton_iterations_per_particle_step": cd32["newton_iterations"] / max(ps32, 1),
+                "full_path_particle_steps": cd32["deferred"]}
+        hbm, _ = load_peaks()
+        fp32["step_fraction_of_hbm_roofline"] = (fp32["value"] * fp32["algorithmic_bytes_per_particle_step"] / 1e9
+                                                 / hbm)
+        ab32 = advect_bytes(wl.dim, wl.ppc, wl.n_props, 4, 4)
+        fp32["roofline"] = roofline_object(1, adv32, ps32 / args.steps, ab32, hbm)
+        if not args.no_accuracy:
+            fp32["accuracy"] = _accuracy_fp32_basis(P, mesh, wl)
+
     (tmax, e2e_s, e2e_serial_s), (psteps_all, e2e_all, e2e_serial_all) = shard.reduce_timing(
         [ms, e2e_s, e2e_serial_s], [psteps, e2e_psteps, e2e_serial_psteps], device=dev if world > 1 else None)
 
     hbm, peak_kind = load_peaks()
-    ppc = float(wl.ppc)
     value = psteps_all / (tmax / 1e3)
-    adv_bytes = advect_bytes(wl.dim, ppc, wl.n_props)
-    adv_avg_ms = adv_ms / max(nsteps, 1)
-    per_launch_particles = psteps / max(nsteps, 1)
-    achieved = adv_bytes * per_launch_particles / (adv_avg_ms / 1e3) / 1e9
-    sbytes = step_bytes(wl.dim, wl.n_props, ppc)
+    sbytes = step_bytes(wl.dim, wl.n_props, wl.ppc)
+    ab = advect_bytes(wl.dim, wl.ppc, wl.n_props)
     res = {
         "metric": "RK4 particle-steps/s (advect+locate+rebin), 3D Q2 mesh; % of HBM roofline",
         "value": value,
@@ -288,17 +374,17 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if precision == 0 else "f64+f32basis",
+        "dtype": "f64 storage / df64 arithmetic (double-float on the FP32 pipe, ~2^-48)",
         "data": "synthetic (seeded jittered mesh, curl-of-potential Q2 field, local-coordinate seeding)",
         "config": {"workload": wl.name, "mesh": "x".join(str(v) for v in wl.n), "particles": wl.n_particles,
                    "particles_per_cell": wl.ppc, "n_props": wl.n_props, "integrator": "RK4" if wl.integrator == 4 else
-                   ("RK2" if wl.integrator == 2 else "Euler"), "dt": wl.dt, "cfl": 0.5,
+                   ("RK2" if wl.integrator == 2 else "Euler"), "dt": wl.dt, "cfl": 0.5, "form": "FP64",
                    "l2": "state ~%.0f MB > 129 MB L2, no flush" % (wl.n_particles * sbytes / 2 / 1e6),
                    "parallelism": "replicas x%d" % world if world > 1 else "single GPU"},
         "step_fraction_of_hbm_roofline": (value * sbytes / 1e9) / hbm,
         "step_algorithmic_bytes_per_particle_step": sbytes,
-        "roofline": roofline_object(args, adv_avg_ms, per_launch_particles, adv_bytes, achieved, hbm, peak_kind,
-                                    reb_ms / max(nsteps, 1)),
+        "roofline": roofline_object(0, adv_avg_ms, psteps / args.steps, ab, hbm, peak_kind, reb_avg_ms),
+        "fp32_basis_form": fp32,
         "transfers_one_property": xfer,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -312,12 +398,11 @@ def run_ours(args, rank, world, local_rank):
                 "serial_value": e2e_serial_all / e2e_serial_s,
                 "serial_what": "the same with the upload issued on the compute stream before each step"},
         "state": {"alive": n1, "lost_total": nlost, "status_word": status,
-                  "walks": stats1["walks"] - stats0["walks"],
-                  "global_searches": stats1["global_searches"] - stats0["global_searches"],
-                  "fp64_fallback_particle_steps": stats1["fallback64"] - stats0["fallback64"],
-                  "fp64_walk_particle_steps": stats1["walk64"] - stats0["walk64"],
-                  "newton_iterations_per_particle_step": (stats1["newton_iterations"] - stats0["newton_iterations"])
-                  / max(psteps, 1)},
+                  "walks": cdelta["walks"], "global_searches": cdelta["global_searches"],
+                  "fp64_fallback_particle_steps": cdelta["fallback64"],
+                  "fp64_walk_particle_steps": cdelta["walk64"],
+                  "full_path_particle_steps": cdelta["deferred"],
+                  "newton_iterations_per_particle_step": cdelta["newton_iterations"] / max(psteps, 1)},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
@@ -327,8 +412,13 @@ def run_ours(args, rank, world, local_rank):
     return res
 
 
+# FP32 peak derived from unit counts and the maximum SM clock: 152 SMs x 128
+# FP32 lanes x 2 flops (FMA) x 2.07 GHz (the ALU bound of the double-float
+# kernels below).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
 # FP32 flops (FADD + FMUL + 2 FFMA) per reverse step of the 32^3 x 32 adjoint
-# (1,048,576 particles, RK4), counted by ncu (profiles/adjoint_c4_32cubed.md):
+# (1,048,576 particles, RK4), counted by an ncu capture of these kernels:
 # reverse_lambda_kernel (G and lambda at 4.19M stage points, double-float)
 # and cell_partial_kernel (the per-cell sums, double-float).
 ADJOINT_C4_FP32_FLOPS_PER_REVERSE_STEP = 1.572e10 + 6.538e9
@@ -532,11 +622,11 @@ def run_props(args):
 # FP32 flops (FADD + FMUL + 2 FFMA) per particle-step of the property-ODE
 # work beyond the plain step: the stage-gradient kernel (13,768) and the ODE
 # kernel (4,480), both in double-float, counted by ncu on the 64^3 x 20
-# workload (profiles/next_rows_c2_64cubed.md).
+# workload (an ncu capture of these kernels).
 PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 18248.0
 
 # FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
-# counted by ncu on the 64^3 x 20 workload; profiles/next_rows_c2_64cubed.md).
+# counted by an ncu capture on the 64^3 x 20 workload).
 FP64_FLOPS = {
     "vertex_partial_kernel<3>": 42.00,     # per particle
     "lsq_linear_kernel<3>": 40.75,         # per particle
@@ -699,24 +789,37 @@ def run_next(args):
             "config": {"workload": "c2_3d_curl_64^3", "particles": N}, "rows": rows}
 
 
-def roofline_object(args, adv_avg_ms, particles, adv_bytes, hbm_achieved, hbm, peak_kind, rebin_ms):
-    """The advect kernel's roofline.  It is bound by FP32 issue (double-float
-    arithmetic), so its roofline is the FP32 ALU peak; its HBM fraction is
-    reported beside it.  The flop and traffic figures come from the ncu
-    capture of this kernel on the 64^3 workload and are null elsewhere."""
-    hbm_part = {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "peak_kind": peak_kind,
-                "frac": hbm_achieved / hbm, "algorithmic_bytes_per_particle": adv_bytes}
-    if args.config == "c2":
-        tflops = ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP * particles / (adv_avg_ms / 1e3) / 1e12
-        return {"kernel": "advect_kernel<3,RK4>", "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS,
-                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
-                "traffic": ADVECT_C2_DRAM_BYTES_PER_PARTICLE * particles,
-                "fp32_flops_per_particle_step": ADVECT_C2_FP32_FLOPS_PER_PARTICLE_STEP,
-                "avg_launch_ms": adv_avg_ms, "rebin_ms_per_step": rebin_ms, "hbm": hbm_part}
-    return {"kernel": "advect_kernel<3,RK4>", "bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": None, "traffic": None, "avg_launch_ms": adv_avg_ms,
-            "rebin_ms_per_step": rebin_ms, "hbm": hbm_part}
+def roofline_object(precision, adv_avg_ms, particles, adv_bytes, hbm, peak_kind="measured", rebin_ms=None):
+    """The advect kernel's HBM roofline: algorithmic bytes per particle-step x
+    particles per launch / the launch's mean CUDA-event time, against the
+    measured HBM copy bandwidth.  Beside it, the DRAM traffic of one launch
+    (from an ncu capture of the kernel, scaled to this launch's particles) and
+    the issue view of the same capture."""
+    achieved = adv_bytes * particles / (adv_avg_ms / 1e3) / 1e9
+    dram = ADVECT_DRAM_BYTES_PER_PARTICLE.get(precision)
+    issue = ADVECT_ISSUE.get(precision)
+    form = "FP64 form" if precision == 0 else "FP32-basis form"
+    return {"kernel": "advect_kernel<3,RK4> (%s)" % form, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_kind": "%s HBM copy bandwidth" % peak_kind,
+            "algorithmic_bytes_per_particle_step": adv_bytes, "particles_per_launch": particles,
+            "avg_launch_ms": adv_avg_ms, "rebin_ms_per_step": rebin_ms,
+            "traffic": dram * particles if dram else None,
+            "traffic_source": "ncu dram__bytes_read+write of this kernel on the 64^3 x 20 workload, per particle, "
+                              "x particles per launch" if dram else None,
+            "issue_view": issue}
+
+
+def _sample_particles(O, om, wl, ids):
+    """Particles `ids` of the uniform-count seeding, rebuilt from the
+    published generator (SplitMix64 output g*dim + j gives x-hat_j of particle
+    g) and the oracle's map, without seeding the whole store in the oracle."""
+    d = wl.dim
+    xh = np.array([[(O.splitmix64(wl.pseed, int(g) * d + j) >> 11) * 2.0 ** -53 for j in range(d)] for g in ids])
+    cell = (np.asarray(ids) // wl.ppc).astype(np.int64)
+    x = np.array([om.phi(int(K), t) for K, t in zip(cell, xh)])
+    props = np.zeros((len(ids), wl.n_props))
+    props[:, : min(wl.n_props, d)] = x[:, : min(wl.n_props, d)]
+    return O.Particles(x, xh, cell, (wl.first_id + np.asarray(ids)).astype(np.uint64), props)
 
 
 def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
@@ -725,11 +828,10 @@ def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
     import oracle as O
 
     om = O.Mesh(wl.n, wl.X, wl.U)
-    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
     rng = np.random.default_rng(0)
     n = sample or 2000
-    pick = np.sort(rng.choice(op.n, min(n, op.n), replace=False))
-    sub = op.subset(pick)
+    pick = np.sort(rng.choice(wl.n_particles, min(n, wl.n_particles), replace=False))
+    sub = _sample_particles(O, om, wl, pick)
     done = 0
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds:
@@ -745,15 +847,17 @@ def cpu_baseline(wl, seconds: float = 15.0, sample: int | None = None):
 # The oracle on all host cores: the sample split into one chunk per core, each
 # advanced in its own process (spawned, so nothing of the GPU context is
 # inherited).  The oracle is unchanged; only the particles are divided, which
-# is exact because they move independently.
+# is exact because they move independently.  The field goes to the workers
+# through a memory-mapped file.
 _ORC_WORKER = None
 
 
-def _orc_worker_init(n, X, U, dt, integrator):
+def _orc_worker_init(n, X, U_path, dt, integrator):
     global _ORC_WORKER
     import oracle as O
 
-    _ORC_WORKER = (O, O.Mesh(n, X, U), dt, integrator)
+    U = np.load(U_path, mmap_mode="r")
+    _ORC_WORKER = (O, O.Mesh(n, X, np.ascontiguousarray(U)), dt, integrator)
 
 
 def _orc_worker_run(task):
@@ -776,18 +880,22 @@ def cpu_baseline_all_cores(wl, seconds: float = 10.0, per_core: int = 2000):
 
     cores = os.cpu_count() or 1
     om = O.Mesh(wl.n, wl.X, wl.U)
-    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
     rng = np.random.default_rng(0)
-    pick = np.sort(rng.choice(op.n, min(per_core * cores, op.n), replace=False))
-    sub = op.subset(pick)
+    pick = np.sort(rng.choice(wl.n_particles, min(per_core * cores, wl.n_particles), replace=False))
+    sub = _sample_particles(O, om, wl, pick)
     chunks = np.array_split(np.arange(sub.n), cores)
     tasks = [(sub.x[c], sub.xhat[c], sub.cell[c], sub.id[c], sub.props[c], seconds) for c in chunks]
     ctx = mp.get_context("spawn")
+    fd, U_path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
     try:
-        with ctx.Pool(cores, initializer=_orc_worker_init, initargs=(wl.n, wl.X, wl.U, wl.dt, wl.integrator)) as pool:
-            res = pool.map_async(_orc_worker_run, tasks, chunksize=1).get(timeout=seconds + 180)
+        np.save(U_path, wl.U)
+        with ctx.Pool(cores, initializer=_orc_worker_init, initargs=(wl.n, wl.X, U_path, wl.dt, wl.integrator)) as pool:
+            res = pool.map_async(_orc_worker_run, tasks, chunksize=1).get(timeout=seconds + 300)
     except Exception as e:  # a worker that cannot start must not hold the benchmark
         return {"unavailable": "%s: %s" % (type(e).__name__, e), "cores": cores, "kind": "oracle"}
+    finally:
+        os.unlink(U_path)
     done = sum(r[0] for r in res)
     el = max(r[1] for r in res)
     return {"value": done / el, "unit": "particle-steps/s", "cores": cores, "kind": "oracle",
@@ -798,15 +906,14 @@ def cpu_baseline_all_cores(wl, seconds: float = 10.0, per_core: int = 2000):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    wl = workload(args.config)
+    wl = workload(args.config if args.config in ("c1", "c2", "c3") else "c3")
     import oracle as O
 
     om = O.Mesh(wl.n, wl.X, wl.U)
-    op = O.seed_particles(om, uniform_count=wl.ppc, seed=wl.pseed, n_props=wl.n_props)
     rng = np.random.default_rng(1)
     sample = 300
-    pick = np.sort(rng.choice(op.n, sample, replace=False))
-    sub = op.subset(pick)
+    pick = np.sort(rng.choice(wl.n_particles, sample, replace=False))
+    sub = _sample_particles(O, om, wl, pick)
     for _ in range(args.warmup):
         sub = O.advect(om, sub, wl.dt, wl.integrator, 1)
     done = 0
@@ -832,12 +939,13 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "c2p", "next"])
+    ap.add_argument("--config", default="c3", choices=["c1", "c2", "c3", "c4", "c5", "c2p", "next"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-basis form's error measurement")
     ap.add_argument("--mesh", type=int, default=None,
                     help="cells per axis instead of the configuration's (profiling only: not that configuration)")
     args = ap.parse_args()

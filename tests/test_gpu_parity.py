@@ -156,6 +156,55 @@ def test_c2_full_size_sampled(P, oracle_mod):
     lost_ids = set(int(i) for i in sub.id) - set(int(i) for i in so.id)
     for i in lost_ids:
         assert i not in pos
+    # cell averages (Sec. 2.7 (ii)) of sampled cells at full size: every
+    # particle the GPU holds in the cell is followed by the oracle, must end
+    # in that cell, and the oracle's left fold of their property over them
+    # (store order) is the GPU's average
+    ga, gc = parts.average(1)
+    ga, gc = ga.cpu().numpy(), gc.cpu().numpy()
+    for K in rng.choice(wl.ncells, 12, replace=False):
+        members = np.nonzero(g["cell"] == K)[0]
+        assert gc[K] == len(members)
+        idx = np.searchsorted(op.id, g["id"][members])  # ids index the oracle's seeded store
+        so = oracle_mod.advect(om, op.subset(idx), wl.dt, wl.integrator, wl.n_steps)
+        np.testing.assert_array_equal(so.cell, np.full(len(members), K))
+        np.testing.assert_array_equal(so.id, g["id"][members])
+        oa, oc = oracle_mod.cell_average(wl.ncells, so.cell, so.props[:, 1])
+        assert oc[K] == gc[K]
+        assert abs(oa[K] - ga[K]) <= H.TOL_AVG, (K, oa[K], ga[K])
+
+
+def test_c3_fp64_form_full_size_sampled(P, oracle_mod):
+    """The benchmark's headline configuration in the FP64 form: 128^3
+    jittered hexes, 20 per cell (41.9M particles), RK4, 20 steps.  Sampled
+    particles follow the oracle one by one: same owner cell, positions within
+    1e-12.  The whole store keeps the sorted-by-(cell, id) invariant and
+    conservation."""
+    wl = W.c3()
+    mesh, parts = H.gpu_seed(wl, n_props=0)
+    N0 = wl.n_particles
+    parts.advect(wl.dt, wl.integrator, wl.n_steps, P.PIC_FP64)
+    n_alive, n_lost, status = parts.state()
+    assert n_alive + n_lost == N0
+    assert status == 0
+    e = parts.export()
+    ids = e["id"].cpu().numpy().astype(np.int64)
+    cells = e["cell"].cpu().numpy().view(np.uint32).astype(np.int64)
+    key = cells * (2**40) + ids
+    assert (np.diff(key) > 0).all()
+    rng = np.random.default_rng(2)
+    pick = np.sort(rng.choice(N0, 200, replace=False))
+    om = oracle_mod.Mesh(wl.n, wl.X, wl.U)
+    sub = _sample_from_generator(oracle_mod, om, wl, pick)
+    so = oracle_mod.advect(om, sub, wl.dt, wl.integrator, wl.n_steps)
+    pos = {int(i): k for k, i in enumerate(ids)}
+    x = e["x"].cpu().numpy()
+    for i, c, xo in zip(so.id, so.cell, so.x):
+        k = pos[int(i)]
+        assert cells[k] == c
+        assert np.abs(x[:, k] - xo).max() <= H.TOL_X
+    for i in set(int(i) for i in sub.id) - set(int(i) for i in so.id):
+        assert i not in pos
 
 
 def _sample_from_generator(O, om, wl, ids):
