@@ -381,7 +381,7 @@ pic_status pic_sort_by_cell(size_t n, const uint32_t *cell, const uint64_t *id, 
  * results are those of pic_sort_by_cell.
  *   Limits: n <= 524288 items and n_cells <= 131072 cells; larger requests
  *   return PIC_ERR_ARG with a message and enqueue nothing.
- *   Scratch: a fixed device array of 7,340,544 bytes inside the library
+ *   Scratch: a fixed device array of 7,340,800 bytes inside the library
  *   (the scratch of one sort at both limits).  Under CUDA's lazy module
  *   loading (the default) a device receives the array on this entry point's
  *   first call there, which looks up its address (cudaGetSymbolAddress): make

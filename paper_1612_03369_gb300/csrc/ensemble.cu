@@ -381,7 +381,7 @@ extern "C" pic_status pic_ensemble_create(int n_problems, const pic_mesh* meshes
       cudaMalloc(&e->bar, sizeof(GridBarrier)) != cudaSuccess ||
       cudaMalloc(&counts, sizeof(uint32_t) * C) != cudaSuccess ||
       cudaMalloc(&off, sizeof(uint32_t) * ((size_t)C + 1)) != cudaSuccess ||
-      cudaMalloc(&sums, sizeof(uint32_t) * (nb + 1)) != cudaSuccess ||
+      cudaMalloc(&sums, scan_scratch_bytes(C)) != cudaSuccess ||
       cudaMalloc(&total, sizeof(uint32_t) * 2) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(counts);

@@ -397,7 +397,7 @@ extern "C" pic_status pic_import_particles(pic_mesh mesh, size_t n, const double
   bool ok = cudaMalloc(&cell, sizeof(uint32_t) * nn) == cudaSuccess &&
             cudaMalloc(&flag, sizeof(uint32_t) * nn) == cudaSuccess &&
             cudaMalloc(&rank, sizeof(uint32_t) * (nn + 1)) == cudaSuccess &&
-            cudaMalloc(&sums, sizeof(uint32_t) * (nb + 1)) == cudaSuccess &&
+            cudaMalloc(&sums, scan_scratch_bytes((uint32_t)nn)) == cudaSuccess &&
             cudaMalloc(&total, sizeof(uint32_t) * 2) == cudaSuccess &&
             cudaMalloc(&perm, sizeof(uint32_t) * nn) == cudaSuccess &&
             cudaMalloc(&off, sizeof(uint32_t) * (C + 1)) == cudaSuccess &&

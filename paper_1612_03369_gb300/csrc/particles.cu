@@ -83,7 +83,7 @@ pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, 
   ok = ok && cudaMalloc(&p->cell_new, sizeof(uint32_t) * cap) == cudaSuccess;
   ok = ok && cudaMalloc(&p->counts, sizeof(uint32_t) * C) == cudaSuccess;
   ok = ok && cudaMalloc(&p->cursor, sizeof(uint32_t) * C) == cudaSuccess;
-  ok = ok && cudaMalloc(&p->block_sums, sizeof(uint32_t) * (nb + 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&p->block_sums, scan_scratch_bytes(C)) == cudaSuccess;
   ok = ok && cudaMalloc(&p->key_id, sizeof(uint64_t) * cap) == cudaSuccess;
   ok = ok && cudaMalloc(&p->key_src, sizeof(uint32_t) * cap) == cudaSuccess;
   ok = ok && cudaMalloc(&p->perm, sizeof(uint32_t) * cap) == cudaSuccess;
@@ -114,7 +114,7 @@ pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t unifor
   uint32_t *counts = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
   const uint32_t nb = scan_block_count(C);
   if (cudaMalloc(&counts, sizeof(uint32_t) * C) != cudaSuccess || cudaMalloc(&off, sizeof(uint32_t) * (C + 1)) != cudaSuccess ||
-      cudaMalloc(&sums, sizeof(uint32_t) * (nb + 1)) != cudaSuccess || cudaMalloc(&total, sizeof(uint32_t) * 2) != cudaSuccess) {
+      cudaMalloc(&sums, scan_scratch_bytes(C)) != cudaSuccess || cudaMalloc(&total, sizeof(uint32_t) * 2) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(counts);
     cudaFree(off);

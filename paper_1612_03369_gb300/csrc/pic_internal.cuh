@@ -103,7 +103,7 @@ struct pic_particles_s {
   uint32_t* cell_new;     // [capacity]
   uint32_t* counts;       // [C]
   uint32_t* cursor;       // [C]
-  uint32_t* block_sums;   // [scan blocks]
+  uint32_t* block_sums;   // scan scratch (scan_scratch_bytes(C))
   uint64_t* key_id;       // [capacity]
   uint32_t* key_src;      // [capacity]
   uint32_t* perm;         // [capacity]
@@ -391,9 +391,11 @@ pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s);
 pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,
                         cudaStream_t st, const char* who, pic_particles_s** out, size_t* n_out);
 // Exclusive scan of n u32 values into out[0..n] (out[n] = total); total also
-// written to *total_dev when non-null.  Defined in rebin.cu.
-pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,
-                    uint32_t* cursor_init, cudaStream_t s);
+// written to *total_dev when non-null; cursor_init, when non-null, receives
+// out[0..n) too.  scratch: scan_scratch_bytes(n) bytes (cleared by the
+// call).  Defined in rebin.cu.
+pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* scratch, uint32_t* total_dev,
+                    uint32_t* cursor_init, cudaStream_t s, unsigned int* status = nullptr);
 uint32_t scan_block_count(uint32_t n);
 int num_sms();
 // Allocate a store (particles.cu); takes ownership of cell_off.
@@ -408,18 +410,19 @@ struct SortScratch {
   uint64_t* key_id;
   uint32_t* key_src;
 };
-// Cells per tile of the offset scan (scan_u32): its tile-sum array holds
-// scan_block_count(C) entries.
+// Items per tile of the single-pass scan (scan_u32), and the bytes of its
+// scratch: one 64-bit state word per tile and the tile counter.
 constexpr uint32_t kScanTileCells = 4096;
-constexpr uint32_t scan_tiles(uint32_t n) { return (n + kScanTileCells - 1) / kScanTileCells; }
+__host__ __device__ constexpr uint32_t scan_tiles(uint32_t n) { return (n + kScanTileCells - 1) / kScanTileCells; }
+constexpr size_t scan_scratch_bytes(uint32_t n) { return sizeof(uint64_t) * ((size_t)scan_tiles(n) + 1); }
 // Bytes of the stateless sort's scratch for n items and C cells, in the order
 // sort_scratch_layout carves them (each piece rounded up to 256 B): status
-// words, counts[C], cursor[C], tile sums, key_id[n] u64, key_src[n] u32.
+// words, counts[C], cursor[C], scan scratch, key_id[n] u64, key_src[n] u32.
 constexpr size_t sort_scratch_up(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t sort_scratch_bytes(size_t n, uint32_t C) {
   return sort_scratch_up(sizeof(uint32_t) * 4) + 2 * sort_scratch_up(sizeof(uint32_t) * (size_t)C) +
-         sort_scratch_up(sizeof(uint32_t) * ((size_t)scan_tiles(C) + 1)) +
-         sort_scratch_up(sizeof(uint64_t) * (n ? n : 1)) + sort_scratch_up(sizeof(uint32_t) * (n ? n : 1));
+         sort_scratch_up(scan_scratch_bytes(C)) + sort_scratch_up(sizeof(uint64_t) * (n ? n : 1)) +
+         sort_scratch_up(sizeof(uint32_t) * (n ? n : 1));
 }
 SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C);
 pic_status sort_by_cell_check(size_t n, const uint32_t* cell, const uint64_t* id, uint32_t C, const uint32_t* perm,

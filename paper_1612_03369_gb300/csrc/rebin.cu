@@ -23,31 +23,101 @@ static_assert(kScanTile == kScanTileCells, "scan tile size and the scratch layou
 
 uint32_t scan_block_count(uint32_t n) { return scan_tiles(n); }
 
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, uint32_t n,
-                                                                   uint32_t* __restrict__ block_sums) {
-  scan_phase_reduce(in, n, block_sums, blockIdx.x, gridDim.x);
+// Single-pass exclusive scan (decoupled look-back, after Merrill & Garland,
+// "Single-pass parallel prefix scan with decoupled look-back", NVIDIA 2016).
+// A block takes its tile in arrival order from a counter, so every tile it
+// waits on belongs to a block that has already started.  It sums its tile
+// (warp shuffles, then one warp over the warp sums), publishes the sum
+// (flag A), then thread 0 walks back over the predecessors: a predecessor's
+// inclusive prefix (flag P) ends the walk, its sum (flag A) is added and the
+// walk goes on.  The block then publishes its own inclusive prefix (flag P)
+// and writes its tile.  Each state word holds the flag in its top two bits
+// and the value below.  The wait for a predecessor that has not published is
+// bounded by the global timer; if it runs out the block latches
+// PIC_STATUS_TIMEOUT (its offsets are then wrong, which the rebin's bounds
+// checks catch and flag).
+constexpr uint64_t kScanFlagA = 1ull << 62, kScanFlagP = 2ull << 62, kScanValue = (1ull << 62) - 1;
+constexpr unsigned long long kScanWaitNs = 1000000000ull;
+
+__global__ void __launch_bounds__(kScanThreads) scan_single_pass_kernel(const uint32_t* __restrict__ in, uint32_t n,
+                                                                        uint64_t* __restrict__ state,
+                                                                        uint32_t* __restrict__ out,
+                                                                        uint32_t* __restrict__ cursor,
+                                                                        uint32_t* __restrict__ total_dev,
+                                                                        unsigned int* __restrict__ status) {
+  __shared__ uint32_t s_tile, s_prefix, s_total;
+  const uint32_t ntiles = scan_tiles(n);
+  if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int*>(state + ntiles), 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  if (t >= ntiles) return;  // block-uniform
+  const uint32_t base = t * kScanTileCells + threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = (base + q < n) ? in[base + q] : 0u;
+    sum += v[q];
+  }
+  const uint32_t ex = block_excl_scan(sum, &s_total);  // ends with a block barrier
+  if (threadIdx.x == 0) {
+    const uint32_t total = s_total;
+    volatile uint64_t* vs = state;
+    uint64_t prefix = 0;
+    if (t == 0) {
+      __threadfence();
+      atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kScanFlagP | total));
+    } else {
+      __threadfence();
+      atomicExch(reinterpret_cast<unsigned long long*>(state + t), (unsigned long long)(kScanFlagA | total));
+      int64_t p = (int64_t)t - 1;
+      const unsigned long long t0 = global_ns();
+      while (p >= 0) {
+        const uint64_t w = vs[p];
+        const uint64_t flag = w & ~kScanValue;
+        if (flag == 0) {
+          if (global_ns() - t0 > kScanWaitNs) {
+            atomicOr(status, PIC_STATUS_TIMEOUT);
+            break;
+          }
+          continue;
+        }
+        prefix += w & kScanValue;
+        if (flag == kScanFlagP) break;
+        --p;
+      }
+      __threadfence();
+      atomicExch(reinterpret_cast<unsigned long long*>(state + t), (unsigned long long)(kScanFlagP | (prefix + total)));
+    }
+    s_prefix = (uint32_t)prefix;
+  }
+  __syncthreads();
+  uint32_t run = s_prefix + ex;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    const uint32_t i = base + q;
+    if (i < n) {
+      out[i] = run;
+      if (cursor) cursor[i] = run;
+    }
+    run += v[q];
+    if (i + 1 == n) {
+      out[n] = run;
+      if (total_dev) *total_dev = run;
+    }
+  }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t* __restrict__ sums, uint32_t nb) {
-  scan_phase_sums(sums, nb);
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const uint32_t* __restrict__ in, uint32_t n,
-                                                                  const uint32_t* __restrict__ block_sums,
-                                                                  uint32_t* __restrict__ out,
-                                                                  uint32_t* __restrict__ cursor,
-                                                                  uint32_t* __restrict__ total_dev) {
-  scan_phase_apply(in, n, block_sums, out, cursor, total_dev, blockIdx.x, gridDim.x);
-}
-
-pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* block_sums, uint32_t* total_dev,
-                    uint32_t* cursor_init, cudaStream_t s) {
-  const uint32_t nb = scan_block_count(n);
+// The scan's status word: the store's counters where there is one, else a
+// word of the scratch past the tile states (cleared with them).
+pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* scratch, uint32_t* total_dev,
+                    uint32_t* cursor_init, cudaStream_t s, unsigned int* status) {
   if (n == 0) return PIC_OK;
-  scan_reduce_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums);
-  scan_sums_kernel<<<1, kScanThreads, 0, s>>>(block_sums, nb);
-  scan_apply_kernel<<<nb, kScanThreads, 0, s>>>(in, n, block_sums, out, cursor_init, total_dev);
-  count_launches(3);
+  const uint32_t nt = scan_tiles(n);
+  uint64_t* state = reinterpret_cast<uint64_t*>(scratch);
+  PIC_CUDA(cudaMemsetAsync(state, 0, sizeof(uint64_t) * (nt + 1), s));
+  unsigned int* st = status ? status : reinterpret_cast<unsigned int*>(state + nt) + 1;
+  scan_single_pass_kernel<<<nt, kScanThreads, 0, s>>>(in, n, state, out, cursor_init, total_dev, st);
+  count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;
 }
@@ -103,7 +173,7 @@ static int grid_cap(size_t n, int block, int per_sm) {
 // old slot) and the sorted cells written into the other buffer; n_alive
 // becomes the survivors' count.  The particles have not moved yet.
 pic_status rebin_order_from_counts(pic_particles_s* p, cudaStream_t s) {
-  pic_status r = scan_u32(p->counts, p->cell_off, p->C, p->block_sums, &p->ctr->n_next, p->cursor, s);
+  pic_status r = scan_u32(p->counts, p->cell_off, p->C, p->block_sums, &p->ctr->n_next, p->cursor, s, &p->ctr->status);
   if (r != PIC_OK) return r;
   const StoreView a = store_view(p, p->cur), b = store_view(p, 1 - p->cur);
   scatter_keys_kernel<<<grid_cap(p->capacity, 256, 16), 256, 0, s>>>(p->cell_new, a.id, p->cursor, p->key_id, p->key_src,
@@ -167,7 +237,6 @@ __global__ void count_cells_kernel(const uint32_t* __restrict__ cell, uint32_t n
 
 SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C) {
   // the pieces and their order are those counted by sort_scratch_bytes
-  const size_t nb = scan_block_count(C) + 1;
   auto up = sort_scratch_up;
   char* p = (char*)base;
   SortScratch sc;
@@ -178,7 +247,7 @@ SortScratch sort_scratch_layout(void* base, size_t n, uint32_t C) {
   sc.cursor = (uint32_t*)p;
   p += up(sizeof(uint32_t) * (size_t)C);
   sc.block_sums = (uint32_t*)p;
-  p += up(sizeof(uint32_t) * nb);
+  p += up(scan_scratch_bytes(C));
   sc.key_id = (uint64_t*)p;
   p += up(sizeof(uint64_t) * (n ? n : 1));
   sc.key_src = (uint32_t*)p;
@@ -198,7 +267,7 @@ pic_status sort_by_cell_run(size_t n, const uint32_t* cell, const uint64_t* id, 
   PIC_CUDA(cudaMemsetAsync(sc.counts, 0, sizeof(uint32_t) * C, s));
   sort_init_kernel<<<1, 1, 0, s>>>(sc.misc, (uint32_t)n);
   if (n) count_cells_kernel<<<grid_cap(n, 256, 16), 256, 0, s>>>(cell, (uint32_t)n, C, sc.counts, sc.misc + 1);
-  pic_status r = scan_u32(sc.counts, cell_off, C, sc.block_sums, sc.misc + 2, sc.cursor, s);
+  pic_status r = scan_u32(sc.counts, cell_off, C, sc.block_sums, sc.misc + 2, sc.cursor, s, sc.misc + 1);
   if (r != PIC_OK) return r;
   if (n) {
     scatter_keys_kernel<<<grid_cap(n, 256, 16), 256, 0, s>>>(cell, id, sc.cursor, sc.key_id, sc.key_src, C, n, sc.misc,

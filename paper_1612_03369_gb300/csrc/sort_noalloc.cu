@@ -10,7 +10,7 @@
 // that is part of the library's device image instead.
 //
 // The array is a file-scope __device__ variable of kNoAllocScratchBytes
-// (7,340,544 B: exactly the scratch of a sort at both limits below).  Under
+// (7,340,800 B: exactly the scratch of a sort at both limits below).  Under
 // CUDA's lazy module loading (the default) a device gets the array when the
 // library first asks for its address there, which this entry point does on
 // its first call on that device: make that first call (n = 0 is enough)
@@ -35,7 +35,7 @@ namespace pic {
 constexpr size_t kNoAllocMaxItems = 524288;   // 2^19 items
 constexpr uint32_t kNoAllocMaxCells = 131072;  // 2^17 cells
 constexpr size_t kNoAllocScratchBytes = sort_scratch_bytes(kNoAllocMaxItems, kNoAllocMaxCells);
-static_assert(kNoAllocScratchBytes == 7340544, "scratch layout changed: update the documented size");
+static_assert(kNoAllocScratchBytes == 7340800, "scratch layout changed: update the documented size");
 
 static __device__ __align__(256) unsigned char g_sort_scratch[kNoAllocScratchBytes];
 
