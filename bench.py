@@ -22,10 +22,12 @@ ensemble (10 steps per persistent graph launch); c2p times c2 with the damage
 and deformation-gradient ODEs; next times the rows after the hot path (time
 interpolation, property ODEs, transfers, generation) on the c2 workload.
 
-Under torchrun (N > 1) every rank advances its own replica of c1-c3
-(independent problems, no data-path collective: weak scaling), and the 64
-members of c5 are dealt out to the ranks by particle count (strong
-scaling); the time is the maximum over ranks.  --impl reference times the CPU
+Under torchrun (N > 1) the c2 and c3 mesh is split over the ranks in slabs
+of cell layers: each rank advances the particles of its layers and hands
+those that leave to its neighbours (NCCL point-to-point; strong scaling);
+--partition replicas runs N independent copies instead (weak scaling).  The
+64 members of c5 are dealt out to the ranks by particle count (strong
+scaling).  The time is the maximum over ranks.  --impl reference times the CPU
 oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -117,12 +119,21 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Start sampling every 50 ms and return once the first sample is in
+        (nvidia-smi takes a moment to start), so that the samples cover the
+        timed region that follows."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 10.0 and self.proc.poll() is None:
+                if os.path.getsize(self.path) > 0:
+                    break
+                time.sleep(0.02)
+            self.skip = sum(1 for _ in open(self.path))  # samples from before the timed region
         except Exception:
             self.proc = None
 
@@ -136,7 +147,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in list(open(self.path))[getattr(self, "skip", 0):]:
             f = [v.strip() for v in line.split(",")]
             if len(f) < 9:
                 continue
@@ -407,6 +418,117 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
         res["cpu_baseline"]["all_cores"] = cpu_baseline_all_cores(wl, seconds=min(args.cpu_seconds, 10.0))
+    parts.close()
+    mesh.close()
+    return res
+
+
+def run_slab(args, rank, world, local_rank):
+    """One mesh split over the ranks in slabs of cell layers (parallel
+    transport, Sec. 2.4): every rank seeds and advances the particles of its
+    own layers on a sub-mesh with two halo layers, then hands the particles
+    that left its layers to its neighbours (NCCL point-to-point, counts then
+    payload) and merges what it receives.  The total work is fixed: strong
+    scaling.  A rank's particles are seeded with its own generator stream
+    (first id = the rank's global offset), the same distribution as the
+    single store's."""
+    import torch
+    import torch.distributed as dist
+    from paper_1612_03369_gb300 import pic as P
+    from paper_1612_03369_gb300 import slab
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    wl = workload(args.config, args.mesh)
+    s = slab.make_slab(wl.n, rank, world, halo=2)
+    mesh = P.Mesh(s.local_n, slab.slice_vertices(wl.X, s), slab.slice_nodes(wl.U, s))
+    own = wl.ppc * s.owned_cells
+    parts = P.Particles(mesh, per_cell=slab.owned_per_cell(s, wl.ppc), seed=wl.pseed + rank,
+                        first_id=slab.first_id(s, wl.ppc), n_props=wl.n_props, capacity=int(own * 1.25) + 4096)
+    st = parts.export()
+    for q in range(min(wl.n_props, wl.dim)):
+        parts.set_property(q, st["x"][q].contiguous())
+    del st
+    stream = torch.cuda.current_stream()
+    moved = [0, 0]
+
+    def step():
+        parts.advect(wl.dt, wl.integrator, 1)
+        d, u = slab.exchange_step(parts, s, dev)
+        moved[0] += d
+        moved[1] += u
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    c0 = parts.stats()
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    moved[:] = [0, 0]
+    launches0 = P.pic_kernel_launches()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = P.pic_kernel_launches() - launches0
+    psteps = parts.stats()["particle_steps"] - c0["particle_steps"]
+
+    # end to end: every step uploads the rank's slice of the field from
+    # pinned host memory, steps, exchanges, and reads the averages of its own
+    # cells back
+    Uh = torch.from_numpy(slab.slice_nodes(wl.U, s)).pin_memory()
+    avg_h = torch.empty(s.owned_cells, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    ce = parts.stats()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.pic_set_velocity_dofs(mesh.h, Uh)
+        step()
+        a, _ = parts.average(0)
+        avg_h.copy_(a[s.own_lo: s.own_hi])
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_psteps = parts.stats()["particle_steps"] - ce["particle_steps"]
+    (tmax, e2e_s), (psteps_all, e2e_all, mv_d, mv_u) = shard.reduce_timing(
+        [ms, e2e_s], [psteps, e2e_psteps, moved[0], moved[1]], device=dev if world > 1 else None)
+    hbm, peak_kind = load_peaks()
+    value = psteps_all / (tmax / 1e3)
+    sbytes = step_bytes(wl.dim, wl.n_props, wl.ppc)
+    res = {
+        "metric": "RK4 particle-steps/s (advect+locate+rebin), 3D Q2 mesh; % of HBM roofline",
+        "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64 storage / df64 arithmetic (double-float on the FP32 pipe, ~2^-48)",
+        "data": "synthetic (seeded jittered mesh, curl-of-potential Q2 field, local-coordinate seeding per rank)",
+        "config": {"workload": wl.name, "mesh": "x".join(str(v) for v in wl.n), "particles": wl.n_particles,
+                   "particles_per_cell": wl.ppc, "n_props": wl.n_props, "integrator": "RK4", "dt": wl.dt, "cfl": 0.5,
+                   "form": "FP64", "parallelism": "slab x%d (cell layers along z, 2 halo layers, NCCL exchange of "
+                                                   "the particles that leave a slab, with their cells)" % world,
+                   "l2": "state > 129 MB L2 per rank, no flush"},
+        "step_fraction_of_hbm_roofline": (value / world * sbytes / 1e9) / hbm,
+        "exchanged_particles_per_step": (mv_d + mv_u) / args.steps,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": e2e_all / e2e_s, "unit": "particle-steps/s",
+                "h2d_bytes_per_step": int(Uh.numel() * 8) * world, "d2h_bytes_per_step": int(wl.ncells * 8),
+                "steps": e2e_steps,
+                "what": "per step and rank: the rank's field slice H2D from pinned memory, one step with the "
+                        "exchange, the averages of its own cells D2H"},
+    }
     parts.close()
     mesh.close()
     return res
@@ -946,6 +1068,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the FP32-basis form's error measurement")
+    ap.add_argument("--partition", default=None, choices=["slab", "replicas"],
+                    help="one mesh split in slabs with particle exchange (the default with N > 1 GPUs; explicit at "
+                         "N = 1: one slab) or N independent replicas")
     ap.add_argument("--mesh", type=int, default=None,
                     help="cells per axis instead of the configuration's (profiling only: not that configuration)")
     args = ap.parse_args()
@@ -971,6 +1096,8 @@ def main():
         dist.init_process_group("nccl")
     if args.config == "c5":
         res = run_ensemble(args, rank, world, local_rank)
+    elif args.config in ("c2", "c3") and (args.partition == "slab" or (world > 1 and args.partition is None)):
+        res = run_slab(args, rank, world, local_rank)
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0:

@@ -467,6 +467,36 @@ pic_status pic_get_counters(pic_particles parts, uint64_t *values, int n_values)
 pic_status pic_export(pic_particles parts, double *x, double *xhat, uint64_t *id, uint32_t *cell, double *props,
                       void *stream);
 
+/* Particles leaving a process's part of the mesh (Sec. 2.4, parallel
+ * transport: a particle that left a process's cells is sent to the owner of
+ * its new cell together with that cell, so that the receiver does not search
+ * for it).  With the mesh split into slabs of whole cell layers, the sorted
+ * store holds the particles that moved below its own layers at its start and
+ * those that moved above at its end, each a contiguous range.
+ *
+ * pic_export_range copies `count` particles of the sorted store from slot
+ * `first` on:  x, xhat [dim][count] FP64 (xhat device memory; the store's
+ * double-float pair converted exactly);  id [count] u64;  cell [count] u32,
+ * each the store's cell + cell_shift (for example into a global numbering;
+ * a nonzero shift needs device memory);  props [n_props][count] FP64.  Any
+ * pointer may be NULL; x, id, props device or host.  Synchronises `stream`
+ * (reads the particle count).
+ * Errors: PIC_ERR_ARG (range past the store, host xhat), PIC_ERR_CUDA. */
+pic_status pic_export_range(pic_particles parts, size_t first, size_t count, long long cell_shift, double *x,
+                            double *xhat, uint64_t *id, uint32_t *cell, double *props, void *stream);
+
+/* Keep the store's particles whose cell lies in [keep_lo, keep_hi), add n_in
+ * particles with known cells (cell_in[i] + cell_shift in this store's mesh;
+ * out of range: dropped, PIC_STATUS_BOUNDS), then sort the store by
+ * (cell, id).  Inputs in device memory, laid out as pic_export_range writes
+ * them (props_in may be NULL: zeros).  Dropped particles are not counted as
+ * lost (they were handed to another store).  Synchronises `stream`.
+ * Errors: PIC_ERR_ARG, PIC_ERR_CAPACITY (kept + received > capacity),
+ * PIC_ERR_CUDA. */
+pic_status pic_merge_particles(pic_particles parts, uint32_t keep_lo, uint32_t keep_hi, size_t n_in, const double *x_in,
+                               const double *xhat_in, const uint64_t *id_in, const uint32_t *cell_in,
+                               long long cell_shift, const double *props_in, void *stream);
+
 /* Cell offsets of the sorted store: off[K]..off[K+1] are the particles of
  * cell K.  off is [n_cells + 1] u32, device or host. */
 pic_status pic_cell_offsets(pic_particles parts, uint32_t *off, void *stream);

@@ -59,6 +59,8 @@ SIGNATURES = {
     "pic_get_counters": (_I, [_P, _P, _I]),
     "pic_export": (_I, [_P, _P, _P, _P, _P, _P, _P]),
     "pic_cell_offsets": (_I, [_P, _P, _P]),
+    "pic_export_range": (_I, [_P, _SZ, _SZ, C.c_longlong, _P, _P, _P, _P, _P, _P]),
+    "pic_merge_particles": (_I, [_P, _U32, _U32, _SZ, _P, _P, _P, _P, C.c_longlong, _P, _P]),
     "pic_timing_enable": (_I, [_P, _I]),
     "pic_set_advect_staging": (_I, [_P, _I]),
     "pic_timing_read": (_I, [_P, _P, _P, _P]),
@@ -319,6 +321,22 @@ def pic_export(parts: int, x=None, xhat=None, id=None, cell=None, props=None, st
            "pic_export")
 
 
+def pic_export_range(parts: int, first: int, count: int, x=None, xhat=None, id=None, cell=None, props=None,
+                     cell_shift: int = 0, stream=None):
+    _check(_lib.pic_export_range(parts, int(first), int(count), int(cell_shift), _ptr(x), _ptr(xhat), _ptr(id),
+                                 _ptr(cell), _ptr(props), _stream(stream)), "pic_export_range")
+
+
+def pic_merge_particles(parts: int, keep_lo: int, keep_hi: int, x_in, xhat_in, id_in, cell_in, cell_shift: int = 0,
+                        props_in=None, stream=None):
+    n = int(id_in.shape[0]) if id_in is not None else 0
+    _check(_lib.pic_merge_particles(parts, int(keep_lo), int(keep_hi), n, _ptr(x_in) if n else None,
+                                    _ptr(xhat_in) if n else None, _ptr(id_in) if n else None,
+                                    _ptr(cell_in) if n else None, int(cell_shift),
+                                    _ptr(props_in) if (n and props_in is not None) else None, _stream(stream)),
+           "pic_merge_particles")
+
+
 def pic_set_advect_staging(parts: int, on: bool):
     _check(_lib.pic_set_advect_staging(parts, 1 if on else 0), "pic_set_advect_staging")
 
@@ -516,6 +534,30 @@ class Particles:
         props = torch.empty((max(self.n_props, 1), n), dtype=torch.float64, device="cuda")
         pic_export(self.h, x, xh, ids, cell, props if self.n_props else None, stream)
         return {"x": x, "xhat": xh, "id": ids, "cell": cell, "props": props[: self.n_props]}
+
+    def export_range(self, first: int, count: int, cell_shift: int = 0, stream=None):
+        """Particles [first, first + count) of the sorted store as torch device
+        tensors, cells shifted by cell_shift."""
+        import torch
+
+        x = torch.empty((self.dim, count), dtype=torch.float64, device="cuda")
+        xh = torch.empty((self.dim, count), dtype=torch.float64, device="cuda")
+        ids = torch.empty(count, dtype=torch.int64, device="cuda")
+        cell = torch.empty(count, dtype=torch.int32, device="cuda")
+        props = torch.empty((max(self.n_props, 1), count), dtype=torch.float64, device="cuda")
+        if count:
+            pic_export_range(self.h, first, count, x, xh, ids, cell, props if self.n_props else None, cell_shift, stream)
+        return {"x": x, "xhat": xh, "id": ids, "cell": cell, "props": props[: self.n_props]}
+
+    def merge(self, keep_lo: int, keep_hi: int, incoming=None, cell_shift: int = 0, stream=None):
+        """Keep the particles of cells [keep_lo, keep_hi), add `incoming` (as
+        export_range returns it) at cell + cell_shift, re-sort."""
+        if incoming is None or incoming["id"].shape[0] == 0:
+            pic_merge_particles(self.h, keep_lo, keep_hi, None, None, None, None, 0, None, stream)
+            return
+        pic_merge_particles(self.h, keep_lo, keep_hi, incoming["x"].contiguous(), incoming["xhat"].contiguous(),
+                            incoming["id"].contiguous(), incoming["cell"].contiguous(), cell_shift,
+                            incoming["props"].contiguous() if self.n_props else None, stream)
 
     def cell_offsets(self, stream=None):
         import torch
