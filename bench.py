@@ -138,8 +138,16 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        """Samples from the last one before the timed region to the first
+        one after it (a region shorter than the sampling period still gets
+        the two that bracket it)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        t0 = time.time()
+        while time.time() - t0 < 1.0 and self.proc.poll() is None:
+            if sum(1 for _ in open(self.path)) > getattr(self, "skip", 0):
+                break
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -147,7 +155,7 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in list(open(self.path))[getattr(self, "skip", 0):]:
+        for line in list(open(self.path))[max(getattr(self, "skip", 0) - 1, 0):]:
             f = [v.strip() for v in line.split(",")]
             if len(f) < 9:
                 continue

@@ -204,8 +204,14 @@ pic_status pic_set_properties(pic_particles parts, int prop, const double *value
  *   PIC_EULER x + dt u(x);  PIC_RK2 midpoint x + dt u(x + dt/2 u(x));
  *   PIC_RK4 x + (k1 + 2 k2 + 2 k3 + k4)/6, k1 = dt u(x), k2 = dt u(x + k1/2),
  *   k3 = dt u(x + k2/2), k4 = dt u(x + k3).
- *   precision  PIC_FP64, or PIC_FP32_BASIS (Q2 basis and contraction in FP32;
- *              positions and the inverse-map residual stay FP64)
+ *   precision  PIC_FP64: FP64 storage, arithmetic in double-float on the FP32
+ *              pipe (~2^-48 relative; within 1e-12 of the FP64 oracle);
+ *              PIC_FP32_BASIS: the Q2 basis and contraction in FP32 on
+ *              reference coordinates; positions accumulate in double-float
+ *              and are stored in FP64; the new position of each step is
+ *              located with the double-float residual and convergence test
+ *              (its stored x-hat good to ~1e-14), the stage points with the
+ *              FP32 Newton alone (x-hat to ~1e-7, all an FP32 basis can use)
  * Errors: PIC_ERR_ARG (mesh/store mismatch, dt not finite, n_steps < 0,
  * velocity not set), PIC_ERR_CUDA. */
 pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,
@@ -307,6 +313,8 @@ pic_status pic_ensemble_set_dt(pic_ensemble ens, const double *dts, void *stream
  *   mode 1: one persistent cooperative kernel for all n_steps; phases are
  *           separated by a grid barrier whose waits give up after a time
  *           limit (then PIC_ERR_TIMEOUT); synchronises to read that status
+ *   In both modes the advect's warps take tiles of particles (32 unless the
+ *   autotuner chose another size) from a work counter.
  *   use_graph: capture the launches once (per n_steps, mode, integrator and
  *           buffer parity) into a CUDA graph and replay it
  * Errors: PIC_ERR_ARG, PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
@@ -314,9 +322,11 @@ pic_status pic_ensemble_run(pic_ensemble ens, pic_integrator integrator, int n_s
                             void *stream);
 
 /* Autotuner of the persistent kernel: times one step for every (blocks per
- * SM, tile of particles claimed at a time) candidate on a snapshot of the
- * store, keeps the fastest for later runs and restores the store.
- * Synchronises.  Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
+ * SM from 1 to the occupancy limit, tile of 32, 128 or 512 particles claimed
+ * by a warp at a time) candidate on a snapshot of the store, keeps the
+ * fastest for later runs of both modes (the per-step mode takes the tile
+ * size) and restores the store.  Any out pointer may be NULL.  Synchronises.
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PIC_ERR_CUDA. */
 pic_status pic_ensemble_tune(pic_ensemble ens, pic_integrator integrator, int *blocks_per_sm, int *tile,
                              double *best_ms, void *stream);
 

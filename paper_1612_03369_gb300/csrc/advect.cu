@@ -53,23 +53,6 @@ struct StageLayout {
   static constexpr size_t bytes() { return (size_t)kAdvectWarps * 2 * BUF * sizeof(float4); }
 };
 
-// The full step of one particle (every rare path of the locate available),
-// out of line.
-struct FullStep {
-  uint32_t K;
-  int iters;
-  unsigned flags;
-};
-template <int D, int RK, bool F32B, bool TWO>
-__device__ __noinline__ FullStep advect_particle_full(const MeshView& m, const StoreView& s, uint32_t i,
-                                                      const StoreView& d, uint32_t j, uint32_t K, df dt) {
-  FullStep o;
-  o.iters = 0;
-  o.flags = 0;
-  o.K = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, o.iters, o.flags);
-  return o;
-}
-
 // One particle of a tile: slot j of d, from particle perm[j] of s when perm
 // is given (the previous step's order applied on the way: its cell is in
 // d.cell[j], its id and properties are carried over), else slot j of s in

@@ -243,4 +243,23 @@ __device__ __forceinline__ uint32_t advect_particle(const MeshView& m, const Sto
   return advect_particle_to<D, RK, F32B, TWO>(m, s, i, s, i, K, dt, iters, flags, static_cast<Hook&&>(hook));
 }
 
+// The full step of one particle (every rare path of the locate available),
+// out of line: the fallback of a fast-path step that returned kDefer.  It
+// re-reads the particle from s, so nothing of the abandoned fast step is
+// kept.
+struct FullStep {
+  uint32_t K;
+  int iters;
+  unsigned flags;
+};
+template <int D, int RK, bool F32B, bool TWO>
+__device__ __noinline__ FullStep advect_particle_full(const MeshView& m, const StoreView& s, uint32_t i,
+                                                      const StoreView& d, uint32_t j, uint32_t K, df dt) {
+  FullStep o;
+  o.iters = 0;
+  o.flags = 0;
+  o.K = advect_particle_to<D, RK, F32B, TWO>(m, s, i, d, j, K, dt, o.iters, o.flags);
+  return o;
+}
+
 }  // namespace pic

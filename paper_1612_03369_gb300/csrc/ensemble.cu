@@ -31,6 +31,7 @@ namespace pic {
 
 constexpr int kMaxEnsemble = 128;
 constexpr int kEnsBlock = 128;
+constexpr int kMaxBlocksPerSm = 32;  // the hardware's limit of resident blocks
 
 struct GridBarrier {
   unsigned int count;
@@ -110,65 +111,102 @@ __device__ __forceinline__ void load_ensemble(EnsShared& sh, const MeshView* vie
 }
 
 // One particle of the ensemble: its problem from the global cell, then the
-// single-mesh step, then back to a global cell.  With perm == nullptr slot j
-// of s advances in place (d is s); otherwise slot j of d takes particle
-// perm[j] of s, whose global cell the previous rebin left in d.cell[j], with
-// its id and properties (the previous step's order applied on the way).
-// Returns the new global cell (PIC_LOST if none), which the caller counts.
+// single-mesh step (the fast path, and the full step where the fast path
+// defers, as in pic_advect), then back to a global cell.  With perm ==
+// nullptr slot j of s advances in place (d is s); otherwise slot j of d takes
+// particle perm[j] of s, whose global cell the previous rebin left in
+// d.cell[j], with its id and properties (the previous step's order applied on
+// the way).  Returns the new global cell (PIC_LOST if none); *full is set
+// when the full step ran.
 template <int D, int RK>
 __device__ __forceinline__ uint32_t ensemble_particle(const EnsShared& sh, int P, const StoreView& s,
                                                       const StoreView& d, const uint32_t* __restrict__ perm, uint32_t j,
-                                                      uint32_t* __restrict__ cell_new, int& iters, unsigned& flags,
-                                                      unsigned& lost) {
+                                                      int& iters, unsigned& flags, uint32_t& full) {
   uint32_t i = j, g;
   if (perm) {
     i = perm[j];
     g = d.cell[j];
     if (i >= s.cap) {
       flags |= kFlagBounds;
-      g = PIC_LOST;
-      i = 0;
-    } else {
-      d.id[j] = s.id[i];
-      for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
+      return PIC_LOST;
     }
+    d.id[j] = s.id[i];
+    for (int q = 0; q < s.n_props; ++q) d.props[(size_t)q * d.cap + j] = s.props[(size_t)q * s.cap + i];
   } else {
     g = s.cell[j];
   }
-  uint32_t out = PIC_LOST;
-  if (g < sh.base[P]) {
-    const int p = problem_of(sh.base, P, g);
-    const uint32_t Kn =
-        advect_particle_to<D, RK, false>(sh.views[p], s, i, d, j, g - sh.base[p], sh.dt[p], iters, flags);
-    if (Kn != PIC_LOST) out = sh.base[p] + Kn;
-  } else {
+  if (g >= sh.base[P]) {
     flags |= kFlagBounds;
+    return PIC_LOST;
   }
-  cell_new[j] = out;
-  if (out == PIC_LOST) lost = 1;
-  return out;
+  const int p = problem_of(sh.base, P, g);
+  const MeshView& m = sh.views[p];
+  const uint32_t K = g - sh.base[p];
+  uint32_t Kn = advect_particle_cells<D, RK, false, false, NoHook, true>(GlobalCells<D, false>{m}, m, s, i, d, j, K,
+                                                                         sh.dt[p], iters, flags);
+  if (Kn == kDefer) {
+    const FullStep f = advect_particle_full<D, RK, false, false>(m, s, i, d, j, K, sh.dt[p]);
+    Kn = f.K;
+    iters = f.iters;
+    flags = f.flags;
+    full = 1;
+  }
+  return Kn == PIC_LOST ? PIC_LOST : sh.base[p] + Kn;
 }
 
+// One step's advect: every warp takes tiles of `tile` particles (a multiple
+// of 32) from *tile_ctr, the next one while it works on the current one,
+// and advances them 32 at a time, one particle per lane; each new cell is
+// counted (warp-aggregated) and written to cell_new.  Warps that finish
+// early take more tiles, so the grid ends together.
+template <int D, int RK>
+__device__ __forceinline__ void ensemble_advect_tiles(const EnsShared& sh, int P, const StoreView& s,
+                                                      const StoreView& d, const uint32_t* __restrict__ perm,
+                                                      uint32_t n, uint32_t tile, uint32_t* tile_ctr,
+                                                      uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts,
+                                                      DevCounters* __restrict__ ctr) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t ntiles = (n + tile - 1) / tile;
+  auto grab = [&]() -> uint32_t {
+    uint32_t t = 0;
+    if (lane == 0) t = atomicAdd(tile_ctr, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+  };
+  uint32_t t = grab();
+  while (t < ntiles) {
+    const uint32_t tn = grab();
+    const uint32_t end = (t + 1) * tile < n ? (t + 1) * tile : n;
+    for (uint32_t j0 = t * tile; j0 < end; j0 += 32u) {
+      const uint32_t j = j0 + lane;
+      int iters = 0;
+      unsigned flags = 0, lost = 0, steps = 0;
+      uint32_t Kc = PIC_LOST, full = 0;
+      if (j < end) {
+        steps = 1;
+        Kc = ensemble_particle<D, RK>(sh, P, s, d, perm, j, iters, flags, full);
+        cell_new[j] = Kc;
+        lost = Kc == PIC_LOST ? 1u : 0u;
+      }
+      const unsigned dc = __reduce_add_sync(0xffffffffu, full);
+      if (dc && lane == 0) atomicAdd(&ctr->deferred, (unsigned long long)dc);
+      (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
+      flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u,
+                     flags);
+    }
+    t = tn;
+  }
+}
+
+// Per-step mode: one step's advect over the whole ensemble (tiles from the
+// store's work counter, cleared before the launch).
 template <int D, int RK>
 __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_advect_kernel(
     const MeshView* __restrict__ views, const uint32_t* __restrict__ base, const df* __restrict__ dts, int P,
-    const __grid_constant__ StoreView s, const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm, uint32_t* __restrict__ cell_new,
-    uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
+    const __grid_constant__ StoreView s, const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm,
+    uint32_t tile, uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
   __shared__ EnsShared sh;
   load_ensemble(sh, views, base, dts, P);
-  const uint32_t n = ctr->n_alive;
-  for (uint32_t b0 = blockIdx.x * blockDim.x; b0 < n; b0 += gridDim.x * blockDim.x) {
-    const uint32_t i = b0 + threadIdx.x;
-    int iters = 0;
-    unsigned flags = 0, lost = 0, steps = 0;
-    uint32_t Kc = PIC_LOST;
-    if (i < n) {
-      steps = 1;
-      Kc = ensemble_particle<D, RK>(sh, P, s, d, perm, i, cell_new, iters, flags, lost);
-    }
-    (void)aggregated_increment(counts, Kc, Kc != PIC_LOST);
-    flush_counters(ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u, flags);
-  }
+  ensemble_advect_tiles<D, RK>(sh, P, s, d, perm, ctr->n_alive, tile, &ctr->tile_next, cell_new, counts, ctr);
 }
 
 struct PersistArgs {
@@ -178,7 +216,7 @@ struct PersistArgs {
   int P;
   StoreView sv[2];
   int start;  // buffer holding the store at the first step
-  uint32_t *cell_new, *counts, *cursor, *cell_off, *tile_sums, *key_src, *perm, *tile_ctr;
+  uint32_t *cell_new, *counts, *cursor, *cell_off, *chunk_sums, *key_src, *perm, *tile_ctr;
   uint64_t* key_id;
   DevCounters* ctr;
   GridBarrier* bar;
@@ -188,76 +226,48 @@ struct PersistArgs {
   unsigned long long timeout_ns;
 };
 
-// All n_steps of the ensemble in one launch (see the file comment).
+// All n_steps of the ensemble in one launch (see the file comment).  A step
+// is five phases, each ended by a grid barrier: advect (warp tiles); the sums
+// of the blocks' chunks of the per-cell counts; each chunk's offsets; the
+// scatter, which also clears the counts for the next step (the offsets are
+// built, nothing reads them again); the rank.  counts and the tile counters
+// are cleared before the launch.
 template <int D, int RK>
 __global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_persistent_kernel(PersistArgs A) {
   __shared__ EnsShared sh;
-  __shared__ uint32_t s_tile;
   load_ensemble(sh, A.views, A.base, A.dts, A.P);
   const uint32_t nb = gridDim.x, bid = blockIdx.x;
   const uint32_t gtid = bid * blockDim.x + threadIdx.x, gthreads = nb * blockDim.x;
-  volatile uint32_t* n_alive = &A.ctr->n_alive;
-  volatile uint32_t* n_next = &A.ctr->n_next;
   // The particles of buffer curb stand in the order of the previous rebin
   // (pending) or in the store's order; each step's advect applies the
   // pending order on the way (reading curb, writing the other buffer), and
   // one gather after the last step applies the last order.
   int curb = A.start;
   bool pending = false;
-  uint32_t nn = 0;
+  uint32_t n = *(volatile uint32_t*)&A.ctr->n_alive;
   for (int step = 0; step < A.n_steps; ++step) {
-    for (uint32_t c = gtid; c < A.C; c += gthreads) A.counts[c] = 0u;
-    if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    const uint32_t n = *n_alive;
-    const StoreView& src = A.sv[curb];
-    const StoreView& dst = A.sv[pending ? 1 - curb : curb];
-    const uint32_t* perm = pending ? A.perm : nullptr;
-    // advect: tiles of A.tile particles claimed dynamically
-    for (;;) {
-      if (threadIdx.x == 0) s_tile = atomicAdd(A.tile_ctr + step, 1u);
-      __syncthreads();
-      const uint32_t t0 = s_tile * (uint32_t)A.tile;
-      __syncthreads();
-      if (t0 >= n) break;
-      const uint32_t t1 = (t0 + A.tile < n) ? t0 + A.tile : n;
-      for (uint32_t b0 = t0; b0 < t1; b0 += blockDim.x) {
-        const uint32_t i = b0 + threadIdx.x;
-        int iters = 0;
-        unsigned flags = 0, lost = 0, steps = 0;
-        uint32_t Kc = PIC_LOST;
-        if (i < t1) {
-          steps = 1;
-          Kc = ensemble_particle<D, RK>(sh, A.P, src, dst, perm, i, A.cell_new, iters, flags, lost);
-        }
-        (void)aggregated_increment(A.counts, Kc, Kc != PIC_LOST);
-        flush_counters(A.ctr, steps, iters, lost, (flags & kFlagWalk) ? 1u : 0u, (flags & kFlagGlobal) ? 1u : 0u,
-                       flags);
-      }
-    }
+    ensemble_advect_tiles<D, RK>(sh, A.P, A.sv[curb], A.sv[pending ? 1 - curb : curb], pending ? A.perm : nullptr, n,
+                                 (uint32_t)A.tile, A.tile_ctr + step, A.cell_new, A.counts, A.ctr);
     if (pending) curb = 1 - curb;
     const StoreView& cur = A.sv[curb];
     const StoreView& nxt = A.sv[1 - curb];
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    scan_phase_reduce(A.counts, A.C, A.tile_sums, bid, nb);
+    scan_phase_chunk_sums(A.counts, A.C, A.chunk_sums, bid, nb);
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    if (bid == 0) scan_phase_sums(A.tile_sums, (A.C + scan_tile_size() - 1) / scan_tile_size());
+    scan_phase_chunk_apply(A.counts, A.C, A.chunk_sums, A.cell_off, A.cursor, &A.ctr->n_next, bid, nb);
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    scan_phase_apply(A.counts, A.C, A.tile_sums, A.cell_off, A.cursor, &A.ctr->n_next, bid, nb);
-    if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
+    const uint32_t nn = *(volatile uint32_t*)&A.ctr->n_next;
+    for (uint32_t c = gtid; c < A.C; c += gthreads) A.counts[c] = 0u;
+    if (gtid == 0) A.ctr->n_alive = nn;
     scatter_phase(A.cell_new, cur.id, A.cursor, A.key_id, A.key_src, A.C, A.cap, n, &A.ctr->status, gtid, gthreads);
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
     rank_phase(A.cell_off, A.key_id, A.key_src, A.perm, nxt.cell, A.C, A.cap, &A.ctr->status, gtid >> 5,
                gthreads >> 5);
-    nn = *n_next;
     if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-    if (gtid == 0) *n_alive = nn;
-    __threadfence();
+    n = nn;
     pending = true;
   }
-  if (pending) {
-    gather_phase(A.sv[curb], A.sv[1 - curb], A.perm, A.dim, nn, &A.ctr->status, gtid, gthreads);
-    if (!grid_sync(A.bar, nb, A.timeout_ns)) return;
-  }
+  if (pending) gather_phase(A.sv[curb], A.sv[1 - curb], A.perm, A.dim, n, &A.ctr->status, gtid, gthreads);
 }
 
 // Barrier self-test: the barrier expects one block more than the launch has,
@@ -294,7 +304,7 @@ struct pic_ensemble_s {
   int has_dt;
   pic_particles_s* store;
   GridBarrier* bar;
-  uint32_t* tile_sums;
+  uint32_t* chunk_sums;  // one per block of the persistent grid
   uint32_t* tile_ctr;
   int tile_ctr_cap;
   int blocks_per_sm, tile;
@@ -320,7 +330,7 @@ extern "C" pic_status pic_ensemble_destroy(pic_ensemble e) {
   cudaFree(e->base_dev);
   cudaFree(e->dt_dev);
   cudaFree(e->bar);
-  cudaFree(e->tile_sums);
+  cudaFree(e->chunk_sums);
   cudaFree(e->tile_ctr);
   pic_destroy_particles(e->store);
   delete e;
@@ -355,7 +365,7 @@ extern "C" pic_status pic_ensemble_create(int n_problems, const pic_mesh* meshes
   e->base_host.resize(n_problems + 1);
   e->timeout_s = 4.0;
   e->blocks_per_sm = 0;
-  e->tile = 1024;
+  e->tile = 32;
   uint64_t Ct = 0;
   for (int p = 0; p < n_problems; ++p) {
     e->base_host[p] = (uint32_t)Ct;
@@ -374,7 +384,6 @@ extern "C" pic_status pic_ensemble_create(int n_problems, const pic_mesh* meshes
     return s;
   };
   uint32_t *counts = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
-  const uint32_t nb = scan_block_count(C);
   if (cudaMalloc(&e->views_dev, sizeof(MeshView) * n_problems) != cudaSuccess ||
       cudaMalloc(&e->base_dev, sizeof(uint32_t) * (n_problems + 1)) != cudaSuccess ||
       cudaMalloc(&e->dt_dev, sizeof(df) * n_problems) != cudaSuccess ||
@@ -473,6 +482,28 @@ static int ensemble_max_blocks_per_sm(int dim, int rk) {
   return b > 0 ? b : 1;
 }
 
+// Resident blocks per SM of the per-step advect kernel (its grid: one
+// resident wave; the warps take tiles from the work counter).
+static int ensemble_advect_blocks_per_sm(int dim, int rk) {
+  static int cache[2][5] = {};
+  int& b = cache[dim == 3][rk];
+  if (b > 0) return b;
+  cudaError_t r;
+  if (dim == 2)
+    r = rk == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<2, 1>, kEnsBlock, 0)
+        : rk == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<2, 2>, kEnsBlock, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<2, 4>, kEnsBlock, 0);
+  else
+    r = rk == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<3, 1>, kEnsBlock, 0)
+        : rk == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<3, 2>, kEnsBlock, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ensemble_advect_kernel<3, 4>, kEnsBlock, 0);
+  if (r != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
 template <int D, int RK>
 static cudaError_t launch_persistent(const PersistArgs& A, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -492,24 +523,24 @@ static pic_status enqueue_run(pic_ensemble_s* e, int integrator, int n_steps, in
   pic_particles_s* s = e->store;
   const int rk = integrator;
   if (mode == 0) {
+    const int grid = ensemble_advect_blocks_per_sm(e->dim, rk) * num_sms();
+    const uint32_t tile = (uint32_t)e->tile;
     for (int step = 0; step < n_steps; ++step) {
       PIC_CUDA(cudaMemsetAsync(s->counts, 0, sizeof(uint32_t) * s->C, st));
-      const int grid = (int)((s->capacity + kEnsBlock - 1) / kEnsBlock < (size_t)num_sms() * 16
-                                 ? (s->capacity + kEnsBlock - 1) / kEnsBlock
-                                 : (size_t)num_sms() * 16);
+      PIC_CUDA(cudaMemsetAsync(&s->ctr->tile_next, 0, sizeof(uint32_t), st));
       // as in pic_advect: each step applies the previous step's order on the
       // way, and the last step's order is applied by one gather
       const bool fused = step > 0;
       const StoreView sv = store_view(s, s->cur), dv = fused ? store_view(s, 1 - s->cur) : sv;
       const uint32_t* pm = fused ? s->perm : nullptr;
       if (e->dim == 2) {
-        if (rk == 1) ensemble_advect_kernel<2, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
-        else if (rk == 2) ensemble_advect_kernel<2, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
-        else ensemble_advect_kernel<2, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        if (rk == 1) ensemble_advect_kernel<2, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
+        else if (rk == 2) ensemble_advect_kernel<2, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
+        else ensemble_advect_kernel<2, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
       } else {
-        if (rk == 1) ensemble_advect_kernel<3, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
-        else if (rk == 2) ensemble_advect_kernel<3, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
-        else ensemble_advect_kernel<3, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, s->cell_new, s->counts, s->ctr);
+        if (rk == 1) ensemble_advect_kernel<3, 1><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
+        else if (rk == 2) ensemble_advect_kernel<3, 2><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
+        else ensemble_advect_kernel<3, 4><<<grid, kEnsBlock, 0, st>>>(e->views_dev, e->base_dev, e->dt_dev, e->P, sv, dv, pm, tile, s->cell_new, s->counts, s->ctr);
       }
       count_launches(1);
       PIC_CUDA(cudaGetLastError());
@@ -526,9 +557,10 @@ static pic_status enqueue_run(pic_ensemble_s* e, int integrator, int n_steps, in
   // persistent (scratch allocated beforehand by prepare_persistent)
   const int bps = e->blocks_per_sm > 0 ? e->blocks_per_sm : ensemble_max_blocks_per_sm(e->dim, rk);
   const int grid = bps * num_sms();
-  if (!e->tile_sums || e->tile_ctr_cap < n_steps)
+  if (!e->chunk_sums || e->tile_ctr_cap < n_steps || grid > num_sms() * kMaxBlocksPerSm)
     return (set_error("pic_ensemble_run: persistent scratch missing"), PIC_ERR_STATE);
   PIC_CUDA(cudaMemsetAsync(e->tile_ctr, 0, sizeof(uint32_t) * n_steps, st));
+  PIC_CUDA(cudaMemsetAsync(s->counts, 0, sizeof(uint32_t) * s->C, st));
   PIC_CUDA(cudaMemsetAsync(e->bar, 0, sizeof(GridBarrier), st));
   PersistArgs A;
   A.views = e->views_dev;
@@ -542,7 +574,7 @@ static pic_status enqueue_run(pic_ensemble_s* e, int integrator, int n_steps, in
   A.counts = s->counts;
   A.cursor = s->cursor;
   A.cell_off = s->cell_off;
-  A.tile_sums = e->tile_sums;
+  A.chunk_sums = e->chunk_sums;
   A.key_src = s->key_src;
   A.perm = s->perm;
   A.tile_ctr = e->tile_ctr;
@@ -566,12 +598,10 @@ static pic_status enqueue_run(pic_ensemble_s* e, int integrator, int n_steps, in
   return PIC_OK;
 }
 
-// Scratch of the persistent kernel (tile sums of the scan, per-step tile
-// counters); allocated outside any stream capture.
+// Scratch of the persistent kernel (the scan's chunk sums, one per block;
+// per-step tile counters); allocated outside any stream capture.
 static pic_status prepare_persistent(pic_ensemble_s* e, int n_steps) {
-  const uint32_t T = kEnsBlock * kScanItems;
-  const uint32_t ntiles = (e->store->C + T - 1) / T;
-  if (!e->tile_sums) PIC_CUDA(cudaMalloc(&e->tile_sums, sizeof(uint32_t) * (ntiles + 1)));
+  if (!e->chunk_sums) PIC_CUDA(cudaMalloc(&e->chunk_sums, sizeof(uint32_t) * num_sms() * kMaxBlocksPerSm));
   if (e->tile_ctr_cap < n_steps) {
     cudaFree(e->tile_ctr);
     e->tile_ctr = nullptr;
@@ -726,12 +756,12 @@ extern "C" pic_status pic_ensemble_tune(pic_ensemble e, pic_integrator integrato
       return pr;
     }
   }
-  const int tiles[3] = {256, 1024, 4096};
+  const int tiles[3] = {32, 128, 512};
   cudaEvent_t ev0, ev1;
   cudaEventCreate(&ev0);
   cudaEventCreate(&ev1);
   double best = 1e300;
-  int bb = maxb, bt = 1024;
+  int bb = maxb, bt = 32;
   const int save_b = e->blocks_per_sm, save_t = e->tile;
   pic_status result = PIC_OK;
   for (int b = 1; b <= maxb && result == PIC_OK; ++b)

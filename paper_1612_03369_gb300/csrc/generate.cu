@@ -393,7 +393,6 @@ extern "C" pic_status pic_import_particles(pic_mesh mesh, size_t n, const double
            *off = nullptr;
   double* xh = nullptr;
   uint64_t* id = nullptr;
-  const uint32_t nb = scan_block_count((uint32_t)nn);
   bool ok = cudaMalloc(&cell, sizeof(uint32_t) * nn) == cudaSuccess &&
             cudaMalloc(&flag, sizeof(uint32_t) * nn) == cudaSuccess &&
             cudaMalloc(&rank, sizeof(uint32_t) * (nn + 1)) == cudaSuccess &&

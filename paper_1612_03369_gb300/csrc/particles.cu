@@ -71,7 +71,6 @@ pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, 
   p->capacity = capacity > 0 ? capacity : 1;
   p->cell_off = cell_off;
   const size_t cap = p->capacity, d = (size_t)dim;
-  const uint32_t nb = scan_block_count(C);
   bool ok = true;
   for (int b = 0; b < 2 && ok; ++b) {
     ok = ok && cudaMalloc(&p->x[b], sizeof(double) * d * cap) == cudaSuccess;
@@ -112,7 +111,6 @@ pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t unifor
   if (n_props < 0 || n_props > kMaxProps) return (set_error("%s: n_props must be in [0, %d]", who, kMaxProps), PIC_ERR_ARG);
   const uint32_t C = mesh->C;
   uint32_t *counts = nullptr, *off = nullptr, *sums = nullptr, *total = nullptr;
-  const uint32_t nb = scan_block_count(C);
   if (cudaMalloc(&counts, sizeof(uint32_t) * C) != cudaSuccess || cudaMalloc(&off, sizeof(uint32_t) * (C + 1)) != cudaSuccess ||
       cudaMalloc(&sums, scan_scratch_bytes(C)) != cudaSuccess || cudaMalloc(&total, sizeof(uint32_t) * 2) != cudaSuccess) {
     cudaGetLastError();

@@ -396,7 +396,6 @@ pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t unifor
 // call).  Defined in rebin.cu.
 pic_status scan_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* scratch, uint32_t* total_dev,
                     uint32_t* cursor_init, cudaStream_t s, unsigned int* status = nullptr);
-uint32_t scan_block_count(uint32_t n);
 int num_sms();
 // Allocate a store (particles.cu); takes ownership of cell_off.
 pic_particles_s* store_alloc(int dim, int n_props, uint32_t C, size_t capacity, uint32_t* cell_off);

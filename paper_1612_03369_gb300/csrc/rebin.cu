@@ -21,16 +21,15 @@ constexpr int kScanThreads = 1024;
 constexpr uint32_t kScanTile = kScanThreads * kScanItems;
 static_assert(kScanTile == kScanTileCells, "scan tile size and the scratch layout disagree");
 
-uint32_t scan_block_count(uint32_t n) { return scan_tiles(n); }
-
 // Single-pass exclusive scan (decoupled look-back, after Merrill & Garland,
 // "Single-pass parallel prefix scan with decoupled look-back", NVIDIA 2016).
 // A block takes its tile in arrival order from a counter, so every tile it
 // waits on belongs to a block that has already started.  It sums its tile
 // (warp shuffles, then one warp over the warp sums), publishes the sum
-// (flag A), then thread 0 walks back over the predecessors: a predecessor's
-// inclusive prefix (flag P) ends the walk, its sum (flag A) is added and the
-// walk goes on.  The block then publishes its own inclusive prefix (flag P)
+// (flag A), then its first warp walks back over the predecessors 32 at a
+// time: the nearest inclusive prefix (flag P) in the window ends the walk
+// with the sums (flag A) after it added, a window of sums only is added and
+// the walk goes on.  The block then publishes its own inclusive prefix (flag P)
 // and writes its tile.  Each state word holds the flag in its top two bits
 // and the value below.  The wait for a predecessor that has not published is
 // bounded by the global timer; if it runs out the block latches
@@ -59,36 +58,52 @@ __global__ void __launch_bounds__(kScanThreads) scan_single_pass_kernel(const ui
     sum += v[q];
   }
   const uint32_t ex = block_excl_scan(sum, &s_total);  // ends with a block barrier
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    const uint32_t lane = threadIdx.x;
     const uint32_t total = s_total;
-    volatile uint64_t* vs = state;
     uint64_t prefix = 0;
     if (t == 0) {
-      __threadfence();
-      atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kScanFlagP | total));
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(reinterpret_cast<unsigned long long*>(state), (unsigned long long)(kScanFlagP | total));
+      }
     } else {
-      __threadfence();
-      atomicExch(reinterpret_cast<unsigned long long*>(state + t), (unsigned long long)(kScanFlagA | total));
-      int64_t p = (int64_t)t - 1;
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(reinterpret_cast<unsigned long long*>(state + t), (unsigned long long)(kScanFlagA | total));
+      }
+      // warp 0 reads the 32 predecessors [p_end - 31, p_end] at once (lane
+      // 31 the nearest; before tile 0 an inclusive prefix of 0): once all
+      // have published, the nearest inclusive prefix and the sums after it
+      // end the walk, else their 32 sums are added and the window moves on
+      volatile uint64_t* vs = state;
+      int64_t p_end = (int64_t)t - 1;
       const unsigned long long t0 = global_ns();
-      while (p >= 0) {
-        const uint64_t w = vs[p];
+      for (;;) {
+        const int64_t p = p_end - (31 - (int64_t)lane);
+        uint64_t w = kScanFlagP;
+        if (p >= 0) w = vs[p];
         const uint64_t flag = w & ~kScanValue;
-        if (flag == 0) {
-          if (global_ns() - t0 > kScanWaitNs) {
-            atomicOr(status, PIC_STATUS_TIMEOUT);
+        if (__any_sync(0xffffffffu, flag == 0)) {
+          if (__any_sync(0xffffffffu, global_ns() - t0 > kScanWaitNs)) {
+            if (lane == 0) atomicOr(status, PIC_STATUS_TIMEOUT);
             break;
           }
           continue;
         }
-        prefix += w & kScanValue;
-        if (flag == kScanFlagP) break;
-        --p;
+        const unsigned pm = __ballot_sync(0xffffffffu, flag == kScanFlagP);
+        const int hp = pm ? 31 - __clz((int)pm) : -1;
+        prefix += __reduce_add_sync(0xffffffffu, (int)lane >= hp ? (uint32_t)(w & kScanValue) : 0u);
+        if (pm) break;
+        p_end -= 32;
       }
-      __threadfence();
-      atomicExch(reinterpret_cast<unsigned long long*>(state + t), (unsigned long long)(kScanFlagP | (prefix + total)));
+      if (lane == 0) {
+        __threadfence();
+        atomicExch(reinterpret_cast<unsigned long long*>(state + t),
+                   (unsigned long long)(kScanFlagP | (prefix + total)));
+      }
     }
-    s_prefix = (uint32_t)prefix;
+    if (lane == 0) s_prefix = (uint32_t)prefix;
   }
   __syncthreads();
   uint32_t run = s_prefix + ex;

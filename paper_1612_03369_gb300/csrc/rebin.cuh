@@ -3,9 +3,10 @@
 // (block index bid of nb blocks), so that the stand-alone kernels of
 // rebin.cu and the persistent ensemble kernel run the same code.
 //
-//   scan   exclusive prefix sum of per-cell counts in tiles of
-//          blockDim.x * kScanItems cells: tile sums, one block scans them,
-//          then every tile applies its offset
+//   scan   exclusive prefix sum of per-cell counts: each block of the grid
+//          sums a contiguous chunk, then offsets its chunk by the sums of
+//          the chunks before it (the stand-alone rebin uses the single-pass
+//          kernel of rebin.cu instead)
 //   scatter (id, old slot) of each particle to a free slot of its new cell
 //   rank   new slot = segment start + rank of the id among the cell's ids
 //   gather every field copied from its old slot to its new slot
@@ -48,73 +49,64 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
   return r;
 }
 
-__device__ __forceinline__ uint32_t scan_tile_size() { return blockDim.x * kScanItems; }
-
-// Tile sums of in[0..n) for tiles bid, bid + nb, ...
-__device__ __forceinline__ void scan_phase_reduce(const uint32_t* __restrict__ in, uint32_t n,
-                                                  uint32_t* __restrict__ tile_sums, uint32_t bid, uint32_t nb) {
-  __shared__ uint32_t tot;
-  const uint32_t T = scan_tile_size(), ntiles = (n + T - 1) / T;
-  for (uint32_t t = bid; t < ntiles; t += nb) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int q = 0; q < kScanItems; ++q) {
-      const uint32_t i = t * T + q * blockDim.x + threadIdx.x;
-      if (i < n) s += in[i];
-    }
-    (void)block_excl_scan(s, &tot);
-    if (threadIdx.x == 0) tile_sums[t] = tot;
-    __syncthreads();
-  }
+// The exclusive scan of a co-resident grid (the persistent ensemble kernel),
+// in two phases with a grid barrier between them.  Block bid of nb owns the
+// contiguous chunk [bid n / nb, (bid + 1) n / nb) of the n values.
+__device__ __forceinline__ void scan_chunk(uint32_t n, uint32_t bid, uint32_t nb, uint32_t& lo, uint32_t& hi) {
+  lo = (uint32_t)((uint64_t)bid * n / nb);
+  hi = (uint32_t)((uint64_t)(bid + 1) * n / nb);
 }
 
-// One block: exclusive scan of the tile sums in place.
-__device__ __forceinline__ void scan_phase_sums(uint32_t* __restrict__ sums, uint32_t ntiles) {
-  __shared__ uint32_t carry_s, tot;
-  if (threadIdx.x == 0) carry_s = 0;
+// Phase 1: sums[bid] = the sum of block bid's chunk.
+__device__ __forceinline__ void scan_phase_chunk_sums(const uint32_t* __restrict__ in, uint32_t n,
+                                                      uint32_t* __restrict__ sums, uint32_t bid, uint32_t nb) {
+  __shared__ uint32_t tot;
+  uint32_t lo, hi, s = 0;
+  scan_chunk(n, bid, nb, lo, hi);
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
+  (void)block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) sums[bid] = tot;
   __syncthreads();
-  for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < ntiles ? sums[i] : 0u;
-    const uint32_t ex = block_excl_scan(v, &tot);
-    const uint32_t carry = carry_s;
-    if (i < ntiles) sums[i] = carry + ex;
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s = carry + tot;
-    __syncthreads();
-  }
 }
 
-// out[i] = exclusive prefix of in (and cursor[i] when given); out[n] and
-// *total_dev get the total.
-__device__ __forceinline__ void scan_phase_apply(const uint32_t* __restrict__ in, uint32_t n,
-                                                 const uint32_t* __restrict__ tile_sums, uint32_t* __restrict__ out,
-                                                 uint32_t* __restrict__ cursor, uint32_t* __restrict__ total_dev,
-                                                 uint32_t bid, uint32_t nb) {
+// Phase 2: block bid adds up sums[0..bid) and writes the exclusive prefix of
+// its chunk to out (and cursor when given), kScanItems consecutive values
+// per thread and pass; the last block writes the total to out[n] and
+// *total_dev.
+__device__ __forceinline__ void scan_phase_chunk_apply(const uint32_t* __restrict__ in, uint32_t n,
+                                                       const uint32_t* __restrict__ sums, uint32_t* __restrict__ out,
+                                                       uint32_t* __restrict__ cursor, uint32_t* __restrict__ total_dev,
+                                                       uint32_t bid, uint32_t nb) {
   __shared__ uint32_t tot;
-  const uint32_t T = scan_tile_size(), ntiles = (n + T - 1) / T;
-  for (uint32_t t = bid; t < ntiles; t += nb) {
-    const uint32_t base = t * T + threadIdx.x * kScanItems;
+  uint32_t lo, hi, before = 0;
+  scan_chunk(n, bid, nb, lo, hi);
+  for (uint32_t k = threadIdx.x; k < bid; k += blockDim.x) before += sums[k];
+  (void)block_excl_scan(before, &tot);
+  uint32_t carry = tot;
+  const uint32_t T = blockDim.x * kScanItems;
+  for (uint32_t base0 = lo; base0 < hi; base0 += T) {
+    const uint32_t base = base0 + threadIdx.x * kScanItems;
     uint32_t v[kScanItems], s = 0;
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
-      v[q] = (base + q < n) ? in[base + q] : 0u;
+      v[q] = (base + q < hi) ? in[base + q] : 0u;
       s += v[q];
     }
-    uint32_t ex = block_excl_scan(s, &tot) + tile_sums[t];
+    uint32_t ex = carry + block_excl_scan(s, &tot);
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
-      const uint32_t i = base + q;
-      if (i < n) {
-        out[i] = ex;
-        if (cursor) cursor[i] = ex;
+      if (base + q < hi) {
+        out[base + q] = ex;
+        if (cursor) cursor[base + q] = ex;
       }
       ex += v[q];
-      if (i + 1 == n) {
-        out[n] = ex;
-        if (total_dev) *total_dev = ex;
-      }
     }
+    carry += tot;
+    __syncthreads();  // tot is rewritten by the next pass
+  }
+  if (bid + 1 == nb && threadIdx.x == 0) {
+    out[n] = carry;
+    if (total_dev) *total_dev = carry;
   }
 }
 
@@ -136,18 +128,20 @@ __device__ __forceinline__ uint32_t aggregated_increment(uint32_t* __restrict__ 
 
 // (id, old slot) of every located particle i < n into a free slot of its new
 // cell.  first - lane and stride must be multiples of 32 (whole warps), so
-// that every lane of a warp takes part in the aggregated increments.
+// that every lane of a warp takes part in the aggregated increments.  Each
+// thread takes U particles per pass and issues their loads, then the U
+// warp-aggregated atomics, before it waits on any of them (memory-level
+// parallelism when the grid is small, as in a persistent kernel).
 __device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_new, const uint64_t* __restrict__ id,
                                               uint32_t* __restrict__ cursor, uint64_t* __restrict__ key_id,
                                               uint32_t* __restrict__ key_src, uint32_t C, size_t cap, uint32_t n,
                                               unsigned int* __restrict__ status, uint32_t first, uint32_t stride) {
-  // four particles per thread and pass, their cells loaded before the first
-  // increment (memory-level parallelism when the grid is small, as in a
-  // persistent kernel)
   constexpr int U = 4;
   const uint32_t lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
   for (size_t base = (size_t)first - lane; base < n; base += (size_t)U * stride) {
     uint32_t K[U];
+    uint64_t iv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const size_t i = base + (size_t)u * stride + lane;
@@ -155,17 +149,29 @@ __device__ __forceinline__ void scatter_phase(const uint32_t* __restrict__ cell_
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint32_t i = (uint32_t)(base + (size_t)u * stride + lane);
+      const size_t i = base + (size_t)u * stride + lane;
+      iv[u] = K[u] < C ? id[i] : 0ull;
+    }
+    unsigned peers[U];
+    uint32_t old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
       if (K[u] != PIC_LOST && K[u] >= C) atomicOr(status, PIC_STATUS_BOUNDS);
       const bool take = K[u] < C;
-      const uint32_t slot = aggregated_increment(cursor, K[u], take);
-      if (!take) continue;
+      peers[u] = __match_any_sync(0xffffffffu, take ? K[u] : 0xFFFFFFFFu);
+      old[u] = 0;
+      if (take && (int)lane == __ffs(peers[u]) - 1) old[u] = atomicAdd(cursor + K[u], (uint32_t)__popc(peers[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t slot = __shfl_sync(0xffffffffu, old[u], __ffs(peers[u]) - 1) + (uint32_t)__popc(peers[u] & below);
+      if (K[u] >= C) continue;
       if (slot >= cap) {
         atomicOr(status, PIC_STATUS_BOUNDS);
         continue;
       }
-      key_id[slot] = id[i];
-      key_src[slot] = i;
+      key_id[slot] = iv[u];
+      key_src[slot] = (uint32_t)(base + (size_t)u * stride + lane);
     }
   }
 }
@@ -187,10 +193,20 @@ __device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off
   const uint32_t per_warp = C / (nw ? nw : 1u);
   uint32_t G = 1;
   while (G < 32u && 2u * G <= per_warp) G *= 2u;
+  // the segment starts of group K0 (lanes >= nc: the group's end); the next
+  // group's are loaded while this one is ranked
+  auto starts = [&](uint32_t K0, int& nc, uint32_t& st, uint32_t& end_all) {
+    nc = K0 < C ? ((C - K0) < G ? (int)(C - K0) : (int)G) : 0;
+    st = K0 < C ? cell_off[K0 + (uint32_t)(lane < nc ? lane : nc)] : 0u;
+    end_all = K0 < C ? cell_off[K0 + (uint32_t)nc] : 0u;
+  };
+  int nc_n;
+  uint32_t st_n, end_n;
+  starts(w * G, nc_n, st_n, end_n);
   for (uint32_t K0 = w * G; K0 < C; K0 += nw * G) {
-    const int nc = (C - K0) < G ? (int)(C - K0) : (int)G;  // cells in this group
-    const uint32_t start = cell_off[K0 + (uint32_t)(lane < nc ? lane : nc)];  // lanes >= nc: the group's end
-    const uint32_t end_all = cell_off[K0 + (uint32_t)nc];
+    const int nc = nc_n;  // cells in this group
+    const uint32_t start = st_n, end_all = end_n;
+    starts(K0 + nw * G, nc_n, st_n, end_n);
     const uint32_t beg_all = __shfl_sync(0xffffffffu, start, 0);
     // segment starts must be non-decreasing and inside the store
     const uint32_t prev = __shfl_up_sync(0xffffffffu, start, 1);
@@ -199,8 +215,21 @@ __device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off
       if (lane == 0) atomicOr(status, PIC_STATUS_BOUNDS);
       continue;
     }
+    // each chunk's key and source are loaded one chunk ahead
+    uint64_t my_n = 0;
+    uint32_t src_n = 0;
+    if (beg_all + lane < end_all) {
+      my_n = key_id[beg_all + lane];
+      src_n = key_src[beg_all + lane];
+    }
     for (uint32_t j0 = beg_all; j0 < end_all; j0 += 32u) {
       const uint32_t j = j0 + lane;
+      const uint64_t my = my_n;
+      const uint32_t src = src_n;
+      if (j + 32u < end_all) {
+        my_n = key_id[j + 32u];
+        src_n = key_src[j + 32u];
+      }
       // c = the last of the nc cells whose segment starts at or before j
       int c = 0;
 #pragma unroll
@@ -212,11 +241,10 @@ __device__ __forceinline__ void rank_phase(const uint32_t* __restrict__ cell_off
       const uint32_t nxt = __shfl_sync(0xffffffffu, start, (c + 1) & 31);
       const uint32_t end = c + 1 < nc ? nxt : end_all;
       if (j < end_all) {
-        const uint64_t my = key_id[j];
         uint32_t rank = 0;
 #pragma unroll 4
         for (uint32_t f = beg; f < end; ++f) rank += (key_id[f] < my) ? 1u : 0u;
-        perm[beg + rank] = key_src[j];
+        perm[beg + rank] = src;
         if (cell_out) cell_out[beg + rank] = K0 + (uint32_t)c;
       }
     }
