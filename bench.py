@@ -320,11 +320,15 @@ def run_ours(args, rank, world, local_rank):
     e2e_serial_s = time.perf_counter() - t0
     e2e_serial_psteps = parts.stats()["particle_steps"] - stats_e0["particle_steps"]
     # pipelined: the next step's field is staged on a copy stream while the
-    # current step runs, then committed (one upload per step either way), and
-    # the host reads step n's averages (double-buffered) while step n + 1 runs
-    copy_stream = torch.cuda.Stream()
+    # current step runs, then committed (one upload per step either way); the
+    # averages go to one of two device buffers and are read back on a second
+    # copy stream while the next step runs, into one of two pinned host
+    # buffers, which the host reads one step later
+    copy_stream, d2h_stream = torch.cuda.Stream(), torch.cuda.Stream()
+    avg_db = [avg_d, torch.empty_like(avg_d)]
     avg_hb = [avg_h, torch.empty_like(avg_h).pin_memory()]
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    ready = [torch.cuda.Event(), torch.cuda.Event()]  # averages of step n computed (compute stream)
+    done = [torch.cuda.Event(), torch.cuda.Event()]  # averages of step n on the host (copy stream)
     checks = []
     stats_e0 = parts.stats()
     torch.cuda.synchronize()
@@ -333,17 +337,23 @@ def run_ours(args, rank, world, local_rank):
     P.pic_stage_velocity_dofs(mesh.h, Uh, copy_stream)
     P.pic_commit_velocity_dofs(mesh.h, stream)
     for n in range(e2e_steps):
+        b = n % 2
         P.pic_advect(parts.h, mesh.h, wl.dt, wl.integrator, precision, 1)
+        if n >= 2:
+            stream.wait_event(done[b])  # step n - 2's read-back of this buffer has finished
         for q in range(wl.n_props):
-            P.pic_interpolate_to_cells(parts.h, mesh.h, q, avg_d[q], cnt_d if q == 0 else None)
-        avg_hb[n % 2].copy_(avg_d, non_blocking=True)
-        done[n % 2].record(stream)
+            P.pic_interpolate_to_cells(parts.h, mesh.h, q, avg_db[b][q], cnt_d if q == 0 else None)
+        ready[b].record(stream)
+        d2h_stream.wait_event(ready[b])
+        with torch.cuda.stream(d2h_stream):
+            avg_hb[b].copy_(avg_db[b], non_blocking=True)
+        done[b].record(d2h_stream)
         if n + 1 < e2e_steps:
             P.pic_stage_velocity_dofs(mesh.h, Uh, copy_stream)
             P.pic_commit_velocity_dofs(mesh.h, stream)
         if n >= 1:
-            done[(n - 1) % 2].synchronize()  # step n - 1's averages are on the host
-            checks.append(float(avg_hb[(n - 1) % 2][0, 0]))
+            done[1 - b].synchronize()  # step n - 1's averages are on the host
+            checks.append(float(avg_hb[1 - b][0, 0]))
     done[(e2e_steps - 1) % 2].synchronize()
     checks.append(float(avg_hb[(e2e_steps - 1) % 2][0, 0]))
     barrier()
@@ -412,8 +422,8 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": int(wl.n_props * wl.ncells * 8), "steps": e2e_steps,
                 "what": "per step: velocity DOFs H2D from pinned host memory (staged on a copy stream during the "
                         "previous step, then committed) + pic_advect 1 step + per-cell averages of all properties "
-                        "+ D2H of the averages into one of two pinned buffers; the host reads step n's averages "
-                        "while step n+1 runs, and the last step's before the clock stops",
+                        "+ D2H of the averages on a second copy stream into one of two pinned buffers; the host "
+                        "reads step n's averages while step n+1 runs, and the last step's before the clock stops",
                 "serial_value": e2e_serial_all / e2e_serial_s,
                 "serial_what": "the same with the upload issued on the compute stream before each step"},
         "state": {"alive": n1, "lost_total": nlost, "status_word": status,

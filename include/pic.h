@@ -200,6 +200,13 @@ pic_status pic_set_properties(pic_particles parts, int prop, const double *value
  *     search; the lowest cell index owns points on shared faces)
  *   - a particle with a stage point or new position in no cell is lost
  *   - the store is rebuilt sorted by (cell, id) with lost particles removed
+ * The particle data move to their sorted slots inside the next step's
+ * advect.  After the last step of a call the new order is computed but left
+ * pending: the next pic_advect applies it inside its first advect, and
+ * pic_interpolate_to_cells reads through it; every other call on the store
+ * applies it first (one gather on that call's stream).  Every call thus sees
+ * the store sorted by (cell, id); pic_get_state and pic_cell_offsets already
+ * describe the new order.
  * Integrators (classical forms, reading of the garbled printed formulas):
  *   PIC_EULER x + dt u(x);  PIC_RK2 midpoint x + dt u(x + dt/2 u(x));
  *   PIC_RK4 x + (k1 + 2 k2 + 2 k3 + k4)/6, k1 = dt u(x), k2 = dt u(x + k1/2),

@@ -421,6 +421,10 @@ extern "C" pic_status pic_advect_record_tape(pic_particles parts, pic_mesh mesh,
   if (mesh->has_next)
     return (set_error("pic_advect_record: the adjoint supports a steady field only (no U_next)"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(parts, st);
+    if (r0 != PIC_OK) return r0;
+  }
   pic_tape_s* tp = (pic_tape_s*)calloc(1, sizeof(pic_tape_s));
   tp->parts = parts;
   tp->mesh = mesh;

@@ -365,9 +365,10 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
   const MeshView m = mesh_view(mesh);
   // Each step's rebin computes the new order (perm, sorted cells); the
   // particles themselves move with the next step's advect, which reads them
-  // through perm, and after the last step with one gather.  Every step thus
-  // reads and writes the particle state once instead of twice.
-  bool pending = false;
+  // through perm.  Every step thus reads and writes the particle state once
+  // instead of twice.  The last step's order stays pending for the next
+  // call (see settle_order).
+  bool pending = parts->pending_order != 0;
   for (int step = 0; step < n_steps; ++step) {
     PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
     PIC_CUDA(cudaMemsetAsync(&parts->ctr->tile_next, 0, sizeof(unsigned int), st));
@@ -387,14 +388,11 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
     }
     PIC_CUDA(cudaGetLastError());
     if (ev) PIC_CUDA(cudaEventRecord(ev[1], st));
+    parts->pending_order = 0;  // consumed by this step's advect
     pic_status r = rebin_order_from_counts(parts, st);
     if (r != PIC_OK) return r;
     pending = true;
-    if (step + 1 == n_steps) {
-      r = rebin_apply_order(parts, st);
-      if (r != PIC_OK) return r;
-      pending = false;
-    }
+    parts->pending_order = 1;
     if (ev) PIC_CUDA(cudaEventRecord(ev[2], st));
   }
   return PIC_OK;
@@ -404,6 +402,10 @@ extern "C" pic_status pic_locate(pic_particles parts, pic_mesh mesh, void* strea
   if (!parts || !mesh) return (set_error("pic_locate: null handle"), PIC_ERR_ARG);
   if (parts->mesh != mesh) return (set_error("pic_locate: mesh mismatch"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(parts, st);
+    if (r0 != PIC_OK) return r0;
+  }
   const MeshView m = mesh_view(mesh);
   PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
   if (mesh->dim == 2)

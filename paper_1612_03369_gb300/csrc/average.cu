@@ -12,9 +12,12 @@ namespace pic {
 //   0 arithmetic  sum v / n
 //   1 geometric   exp(sum log v / n)   (NaN if the cell holds a v <= 0)
 //   2 harmonic    n / sum (1 / v)      (NaN if the cell holds a v <= 0)
-template <int KIND>
+// PERM (an order left pending by pic_advect): slot i's value is
+// prop[perm[i]], the same values in the same order as after the gather.
+template <int KIND, bool PERM>
 __global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __restrict__ cell_off,
-                                                           const double* __restrict__ prop, uint32_t C, size_t cap,
+                                                           const double* __restrict__ prop,
+                                                           const uint32_t* __restrict__ perm, uint32_t C, size_t cap,
                                                            double empty_fill, double* __restrict__ avg,
                                                            uint32_t* __restrict__ count, DevCounters* __restrict__ ctr) {
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < C; K += gridDim.x * blockDim.x) {
@@ -26,7 +29,16 @@ __global__ void __launch_bounds__(256) cell_average_kernel(const uint32_t* __res
     double s = 0.0;
     bool bad = false;
     for (uint32_t i = beg; i < end; ++i) {
-      const double v = prop[i];
+      uint32_t src = i;
+      if constexpr (PERM) {
+        src = perm[i];
+        if (src >= cap) {
+          bad = true;
+          latch_status(ctr, PIC_STATUS_BOUNDS);
+          continue;
+        }
+      }
+      const double v = prop[src];
       if constexpr (KIND == 0) {
         s += v;
       } else {
@@ -67,12 +79,25 @@ extern "C" pic_status pic_interpolate_to_cells(pic_particles p, pic_mesh mesh, i
   if (grid > cap) grid = cap;
   const int g = (int)(grid ? grid : 1);
   const double* pv = p->props[p->cur] + (size_t)prop * p->capacity;
-  if (kind == PIC_AVG_ARITHMETIC)
-    cell_average_kernel<0><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
-  else if (kind == PIC_AVG_GEOMETRIC)
-    cell_average_kernel<1><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
-  else
-    cell_average_kernel<2><<<g, 256, 0, st>>>(p->cell_off, pv, p->C, p->capacity, empty_fill, avg, count, p->ctr);
+  // read through a pending order, do not apply it
+  const uint32_t* pm = p->perm;
+  const uint32_t C = p->C;
+  const size_t cp = p->capacity;
+  if (p->pending_order) {
+    if (kind == PIC_AVG_ARITHMETIC)
+      cell_average_kernel<0, true><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+    else if (kind == PIC_AVG_GEOMETRIC)
+      cell_average_kernel<1, true><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+    else
+      cell_average_kernel<2, true><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+  } else {
+    if (kind == PIC_AVG_ARITHMETIC)
+      cell_average_kernel<0, false><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+    else if (kind == PIC_AVG_GEOMETRIC)
+      cell_average_kernel<1, false><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+    else
+      cell_average_kernel<2, false><<<g, 256, 0, st>>>(p->cell_off, pv, pm, C, cp, empty_fill, avg, count, p->ctr);
+  }
   count_launches(1);
   PIC_CUDA(cudaGetLastError());
   return PIC_OK;

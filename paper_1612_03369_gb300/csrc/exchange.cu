@@ -81,6 +81,10 @@ extern "C" pic_status pic_export_range(pic_particles p, size_t first, size_t cou
                                        double* xhat, uint64_t* id, uint32_t* cell, double* props, void* stream) {
   if (!p) return (set_error("pic_export_range: null handle"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   unsigned int n_alive = 0;
   PIC_CUDA(cudaMemcpyAsync(&n_alive, &p->ctr->n_alive, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   PIC_CUDA(cudaStreamSynchronize(st));
@@ -131,6 +135,10 @@ extern "C" pic_status pic_merge_particles(pic_particles p, uint32_t keep_lo, uin
   if (keep_lo > keep_hi || keep_hi > p->C)
     return (set_error("pic_merge_particles: kept cells [%u, %u) outside [0, %u)", keep_lo, keep_hi, p->C), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   unsigned int n_old = 0;
   PIC_CUDA(cudaMemcpyAsync(&n_old, &p->ctr->n_alive, sizeof(unsigned int), cudaMemcpyDeviceToHost, st));
   PIC_CUDA(cudaStreamSynchronize(st));

@@ -218,6 +218,10 @@ extern "C" pic_status pic_set_properties(pic_particles p, int prop, const double
   if (!p || !values) return (set_error("pic_set_properties: null argument"), PIC_ERR_ARG);
   if (prop < 0 || prop >= p->n_props) return (set_error("pic_set_properties: property %d out of range", prop), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   set_prop_kernel<<<1024, 256, 0, st>>>(p->props[p->cur] + (size_t)prop * p->capacity, values, p->ctr);
   count_launches(1);
   PIC_CUDA(cudaGetLastError());
@@ -269,6 +273,10 @@ extern "C" pic_status pic_export(pic_particles p, double* x, double* xhat, uint6
                                  void* stream) {
   if (!p) return (set_error("pic_export: null handle"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   DevCounters h;
   pic_status r = read_counters(p, &h);
   if (r != PIC_OK) return r;

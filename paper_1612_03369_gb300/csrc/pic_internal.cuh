@@ -97,6 +97,7 @@ struct pic_particles_s {
   uint32_t* cell[2];
   double* props[2];
   int cur;                // which buffer holds the sorted store
+  int pending_order;      // pic_advect left the last rebin's order unapplied (perm; sorted cells in the other buffer)
   int stage_cells;        // pic_advect stages the cells' blocks in shared memory (pic_set_advect_staging)
   uint32_t* cell_off;     // [C+1]
   // scratch for the rebin
@@ -386,6 +387,12 @@ struct StageRec {
 void launch_advect_record(pic_particles_s* p, const MeshView& m, double dt, int rk, const StageRec& rec,
                           cudaStream_t st);
 pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s);
+// pic_advect leaves its last rebin's order pending (the next pic_advect
+// applies it inside its advect, pic_interpolate_to_cells reads through it);
+// every other call that reads or writes the particle arrays in slot order
+// applies it first with this (a gather on stream s; nothing when none is
+// pending).  Defined in rebin.cu.
+pic_status settle_order(pic_particles_s* p, cudaStream_t s);
 // Counting, cell offsets and store allocation shared by the generators
 // (particles.cu); the store's buffer 0 is then filled by the caller.
 pic_status seed_prepare(pic_mesh mesh, const uint32_t* per_cell, uint32_t uniform_count, int n_props, size_t capacity,

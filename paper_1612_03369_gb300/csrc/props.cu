@@ -277,6 +277,10 @@ extern "C" pic_status pic_advect_properties(pic_particles parts, pic_mesh mesh, 
   };
   const OdeArgs o = {odes->damage, odes->deformation, split(odes->alpha), split(odes->beta)};
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(parts, st);
+    if (r0 != PIC_OK) return r0;
+  }
   const MeshView m = mesh_view(mesh);
   if (!parts->stage_rec) {
     const size_t bytes = (size_t)4 * parts->capacity * (sizeof(uint32_t) + sizeof(float2) * d + sizeof(float2) * d * d);

@@ -211,6 +211,12 @@ pic_status rebin_apply_order(pic_particles_s* p, cudaStream_t s) {
   return PIC_OK;
 }
 
+pic_status settle_order(pic_particles_s* p, cudaStream_t s) {
+  if (!p->pending_order) return PIC_OK;
+  p->pending_order = 0;
+  return rebin_apply_order(p, s);
+}
+
 pic_status rebin_from_counts(pic_particles_s* p, cudaStream_t s) {
   pic_status r = rebin_order_from_counts(p, s);
   if (r != PIC_OK) return r;
@@ -324,6 +330,10 @@ extern "C" pic_status pic_sort_by_cell(size_t n, const uint32_t* cell, const uin
 extern "C" pic_status pic_rebin(pic_particles parts, void* stream) {
   if (!parts) return (set_error("pic_rebin: null handle"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(parts, st);
+    if (r0 != PIC_OK) return r0;
+  }
   PIC_CUDA(cudaMemsetAsync(parts->counts, 0, sizeof(uint32_t) * parts->C, st));
   identity_cells_kernel<<<grid_cap(parts->capacity, 256, 16), 256, 0, st>>>(parts->cell[parts->cur], parts->cell_new,
                                                                           parts->counts, parts->C, parts->ctr);

@@ -213,6 +213,10 @@ extern "C" pic_status pic_interpolate_to_vertices(pic_particles p, pic_mesh mesh
   if (prop < 0 || prop >= p->n_props)
     return (set_error("pic_interpolate_to_vertices: property %d out of range", prop), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   const MeshView m = mesh_view(mesh);
   if (!p->xfer) {
     const size_t bytes = sizeof(double) * 2 * ((size_t)1 << mesh->dim) * (size_t)p->C;
@@ -245,6 +249,10 @@ extern "C" pic_status pic_project_linear(pic_particles p, pic_mesh mesh, int pro
   if (prop < 0 || prop >= p->n_props)
     return (set_error("pic_project_linear: property %d out of range", prop), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const pic_status r0 = settle_order(p, st);
+    if (r0 != PIC_OK) return r0;
+  }
   const double* pv = p->props[p->cur] + (size_t)prop * p->capacity;
   const int g = transfer_grid(p->C, 128);
   if (mesh->dim == 2)
