@@ -36,7 +36,8 @@ namespace pic {
 
 // FP32 phase ends when max|update| <= kSettle32: the iterate is then within
 // ~C*kSettle32^2 + 1e-7 of the root (C ~ 1 for cells jittered by 10%), and
-// the double-float step takes that to ~C*(2e-7)^2 + 6e-8*2e-7 ~ 1e-14.
+// the double-float step takes that to ~C*(2e-7)^2 + 3e-7*2e-7 ~ 1e-13 (the
+// FP32 Jacobian and the approximate reciprocal of solve32 scale the update).
 constexpr float kSettle32 = 2e-4f;
 constexpr int kMaxIt32 = 8;
 
@@ -185,11 +186,17 @@ __device__ __forceinline__ bool solve32(const float J[D][D], const float r[D], f
   // that every kernel inlining this (the advect kernel's template instances,
   // the stage-recording kernel, the adjoint's stage kernel) computes the same
   // iterates bit for bit, whatever the compiler would contract on its own.
+  // The determinant's reciprocal is the hardware approximation (one
+  // instruction, within 2 ulp; the IEEE division took a dozen): it scales a
+  // Newton update whose last, double-float-residual step is ~1e-7, so it
+  // moves the root by ~3e-14, the size of the FP32 Jacobian's own error.  A
+  // zero or non-finite determinant fails here; one so small that its
+  // reciprocal overflows gives an update the caller rejects (|d| > 1e3).
   auto det2 = [](float a, float b, float c, float e) { return __fmaf_rn(a, b, -__fmul_rn(c, e)); };  // a b - c e
   if constexpr (D == 2) {
     const float det = det2(J[0][0], J[1][1], J[0][1], J[1][0]);
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float inv = __fdiv_rn(1.0f, det);
+    const float inv = __fdividef(1.0f, det);
     d[0] = __fmul_rn(det2(J[1][1], r[0], J[0][1], r[1]), inv);
     d[1] = __fmul_rn(det2(J[0][0], r[1], J[1][0], r[0]), inv);
     return true;
@@ -199,7 +206,7 @@ __device__ __forceinline__ bool solve32(const float J[D][D], const float r[D], f
     const float c02 = det2(J[1][0], J[2][1], J[1][1], J[2][0]);
     const float det = __fmaf_rn(J[0][2], c02, __fmaf_rn(J[0][1], c01, __fmul_rn(J[0][0], c00)));
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return false;
-    const float inv = __fdiv_rn(1.0f, det);
+    const float inv = __fdividef(1.0f, det);
     const float c10 = det2(J[0][2], J[2][1], J[0][1], J[2][2]);
     const float c11 = det2(J[0][0], J[2][2], J[0][2], J[2][0]);
     const float c12 = det2(J[0][1], J[2][0], J[0][0], J[2][1]);
