@@ -768,8 +768,6 @@ PROPS_ODE_FP32_FLOPS_PER_PARTICLE_STEP = 18248.0
 # FP64 operations per unit of the FP64-bound kernels (dadd + dmul + 2 dfma,
 # counted by an ncu capture on the 64^3 x 20 workload).
 FP64_FLOPS = {
-    "vertex_partial_kernel<3>": 42.00,     # per particle
-    "lsq_linear_kernel<3>": 40.75,         # per particle
     "mh_seed_kernel<3>": 238.96,           # per chain step
     "cell_weights_kernel<3>": 1815.0,      # per cell
 }
@@ -785,6 +783,24 @@ def _fp64_roof(kernel, units, ms):
     ach = f * units / (ms / 1e3) / 1e12
     return {"kernel": kernel, "bound": "fp64", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_PEAK_TFLOPS, "fp64_flops_per_unit": f, "peak_kind": "derived (nominal FP64 rate)"}
+
+
+# The transfers fold each particle's x-hat (three double-float pairs) and its
+# property once, in double-float arithmetic on the FP32 pipe; per particle
+# 24 + 8 B, plus the per-cell outputs amortised over 20 particles per cell:
+# 2^3 corner numerators and denominators as double-float pairs (vertex
+# averages), 4 coefficients and a count (least squares).
+TRANSFER_BYTES_PER_PARTICLE = {"vertex_partial_kernel<3>": 32.0 + 16 * 8 / 20.0,
+                               "lsq_linear_kernel<3>": 32.0 + (4 * 8 + 4) / 20.0}
+
+
+def _transfer_roof(kernel, units, ms):
+    hbm, kind = load_peaks()
+    b = TRANSFER_BYTES_PER_PARTICLE[kernel]
+    ach = b * units / (ms / 1e3) / 1e9
+    return {"kernel": kernel, "bound": "fp32 issue (double-float arithmetic)", "view": "hbm",
+            "algorithmic_bytes_per_particle": b, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "peak_kind": kind}
 
 
 def run_next(args):
@@ -870,9 +886,9 @@ def run_next(args):
     rows["f3_transfers"] = {
         "particles": N, "cell_average_ms": ms_a, "vertex_average_ms": ms_v, "project_linear_ms": ms_l,
         "vertex_average": {"value": N / (ms_v / 1e3), "unit": "particles/s",
-                           "roofline": _fp64_roof("vertex_partial_kernel<3>", N, ms_v)},
+                           "roofline": _transfer_roof("vertex_partial_kernel<3>", N, ms_v)},
         "project_linear": {"value": N / (ms_l / 1e3), "unit": "particles/s",
-                           "roofline": _fp64_roof("lsq_linear_kernel<3>", N, ms_l)},
+                           "roofline": _transfer_roof("lsq_linear_kernel<3>", N, ms_l)},
         "cpu_baseline": {
             "vertex_average": cpu(lambda: O.vertex_average(om, full.cell, full.xhat, v0), N, "all %d particles" % N),
             "project_linear": cpu(lambda: O.cell_lsq_linear(om, full.cell, full.xhat, v0), N, "all %d particles" % N)}}

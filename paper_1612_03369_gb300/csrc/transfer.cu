@@ -11,62 +11,82 @@
 // the cells' partial sums then added in increasing cell index, which rounds
 // differently from one left fold over the support (the definition) by a few
 // ulps of the sum.
+#include "df.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
 
-__device__ __forceinline__ double xhat64(const float2* __restrict__ xh, size_t idx) {
-  const float2 v = xh[idx];
-  return (double)v.x + (double)v.y;
+// The arithmetic per particle is double-float on the FP32 pipe (the stored
+// x-hat already is a double-float pair; the property is split once): GB300's
+// FP64 pipe runs about 1/80 of the FP32 rate, and the FP64 form of these
+// kernels was bound by it.  Every product keeps ~2^-47 of its value and the
+// sums are compensated (acc_mad, acc_add), so the per-cell sums carry a
+// relative error of a few 2^-47 against the FP64 definition.
+__device__ __forceinline__ df one_minus(df t) {  // 1 - t
+  const df d = two_sum(1.0f, -t.hi);
+  return fast_two_sum(d.hi, __fsub_rn(d.lo, t.lo));
 }
+__device__ __forceinline__ df minus_half(df t) {  // t - 1/2
+  const df d = two_sum(t.hi, -0.5f);
+  return fast_two_sum(d.hi, __fadd_rn(d.lo, t.lo));
+}
+__device__ __forceinline__ double df_to_f64(df a) { return (double)a.hi + (double)a.lo; }
 
 // Two phases, both deterministic.
 // Phase 1, thread per cell: each particle of the cell is read once and its
 // 2^D corner weights (the tensor product of (1 - t_a, t_a), multiplied in
 // axis order) are folded, in store order, into the cell's partial sums
 //   num[c][K] = sum w_c(x-hat_i) p_i,   den[c][K] = sum w_c(x-hat_i)
-// stored corner-major ([c][C]) so that the phase-2 reads of a warp coalesce.
+// stored as double-float pairs, corner-major ([c][C]) so that the phase-2
+// reads of a warp coalesce.
 template <int D>
 __global__ void __launch_bounds__(128) vertex_partial_kernel(const uint32_t* __restrict__ cell_off,
                                                              const float2* __restrict__ xh, const double* __restrict__ prop,
-                                                             uint32_t C, size_t cap, double* __restrict__ part,
+                                                             uint32_t C, size_t cap, float2* __restrict__ part,
                                                              DevCounters* __restrict__ ctr) {
   constexpr int NC = 1 << D;
   for (uint32_t K = blockIdx.x * blockDim.x + threadIdx.x; K < C; K += gridDim.x * blockDim.x) {
     const uint32_t beg = cell_off[K], end = cell_off[K + 1];
-    double num[NC], den[NC];
+    df_acc num[NC], den[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) num[c] = den[c] = 0.0;
+    for (int c = 0; c < NC; ++c) num[c] = den[c] = acc_zero();
     if (end > cap || beg > end) {
       latch_status(ctr, PIC_STATUS_BOUNDS);
     } else {
       for (uint32_t i = beg; i < end; ++i) {
-        double t[D];
+        df f[D][2];  // f[a][0] = 1 - t_a, f[a][1] = t_a
 #pragma unroll
-        for (int a = 0; a < D; ++a) t[a] = xhat64(xh, a * cap + i);
-        const double p = prop[i];
+        for (int a = 0; a < D; ++a) {
+          const float2 v = xh[a * cap + i];
+          f[a][1] = df_make(v.x, v.y);
+          f[a][0] = one_minus(f[a][1]);
+        }
+        const df p = df_from_double(prop[i]);
+        df w01[4];  // the first two axes' products, corner bits 0 and 1
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w01[c] = df_mul(f[0][c & 1], f[1][(c >> 1) & 1]);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          double w = 1.0;
-#pragma unroll
-          for (int a = 0; a < D; ++a) w *= ((c >> a) & 1) ? t[a] : 1.0 - t[a];
-          num[c] += w * p;
-          den[c] += w;
+          const df w = D == 3 ? df_mul(w01[c & 3], f[D - 1][(c >> 2) & 1]) : w01[c];
+          acc_mad(num[c], w, p);
+          acc_add(den[c], w);
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-      part[(size_t)c * C + K] = num[c];
-      part[(size_t)(NC + c) * C + K] = den[c];
+      const df a = acc_result(num[c]), b = acc_result(den[c]);
+      part[(size_t)c * C + K] = make_float2(a.hi, a.lo);
+      part[(size_t)(NC + c) * C + K] = make_float2(b.hi, b.lo);
     }
   }
 }
 
 // Phase 2, thread per vertex: the partial sums of the cells around the
-// vertex, added in increasing cell index.
+// vertex, added in increasing cell index (double-float), then one FP64
+// division.
 template <int D>
-__global__ void __launch_bounds__(256) vertex_gather_kernel(const __grid_constant__ MeshView m, const double* __restrict__ part,
+__global__ void __launch_bounds__(256) vertex_gather_kernel(const __grid_constant__ MeshView m, const float2* __restrict__ part,
                                                             double empty_fill, double* __restrict__ avg,
                                                             double* __restrict__ weight) {
   constexpr int NC = 1 << D;
@@ -77,7 +97,7 @@ __global__ void __launch_bounds__(256) vertex_gather_kernel(const __grid_constan
     const uint32_t r = v / (uint32_t)m.nv[0];
     vc[1] = D == 3 ? (int)(r % (uint32_t)m.nv[1]) : (int)r;
     vc[2] = D == 3 ? (int)(r / (uint32_t)m.nv[1]) : 0;
-    double num = 0.0, den = 0.0;
+    df_acc num = acc_zero(), den = acc_zero();
 #pragma unroll
     for (int o = 0; o < NC; ++o) {
       // bit a of o is the offset along axis a (x fastest, the last axis
@@ -92,11 +112,13 @@ __global__ void __launch_bounds__(256) vertex_gather_kernel(const __grid_constan
       }
       if (!ok) continue;
       const uint32_t K = cell_index<D>(m, c[0], c[1], c[2]);
-      num += part[(size_t)corner * C + K];
-      den += part[(size_t)(NC + corner) * C + K];
+      const float2 a = part[(size_t)corner * C + K], b = part[(size_t)(NC + corner) * C + K];
+      acc_add(num, df_make(a.x, a.y));
+      acc_add(den, df_make(b.x, b.y));
     }
-    avg[v] = den > 0.0 ? num / den : empty_fill;
-    if (weight) weight[v] = den;
+    const double dn = df_to_f64(acc_result(den));
+    avg[v] = dn > 0.0 ? df_to_f64(acc_result(num)) / dn : empty_fill;
+    if (weight) weight[v] = dn;
   }
 }
 
@@ -117,25 +139,44 @@ __global__ void __launch_bounds__(128) lsq_linear_kernel(const uint32_t* __restr
       latch_status(ctr, PIC_STATUS_BOUNDS);
       continue;
     }
-    double M[NB][NB + 1], sum = 0.0;
+    // the upper triangle of A^T A, A^T p and sum p, accumulated in
+    // double-float (row a = (1, x-hat - 1/2)), then converted once
+    df_acc Ma[NB][NB + 1], sa = acc_zero();
 #pragma unroll
     for (int r = 0; r < NB; ++r)
 #pragma unroll
-      for (int q = 0; q <= NB; ++q) M[r][q] = 0.0;
+      for (int q = 0; q <= NB; ++q) Ma[r][q] = acc_zero();
     for (uint32_t i = beg; i < end; ++i) {
-      double a[NB];
-      a[0] = 1.0;
+      df a[NB];
+      a[0] = df_make(1.0f, 0.f);
 #pragma unroll
-      for (int j = 0; j < D; ++j) a[j + 1] = xhat64(xh, j * cap + i) - 0.5;
-      const double p = prop[i];
+      for (int j = 0; j < D; ++j) {
+        const float2 v = xh[j * cap + i];
+        a[j + 1] = minus_half(df_make(v.x, v.y));
+      }
+      const df p = df_from_double(prop[i]);
 #pragma unroll
       for (int r = 0; r < NB; ++r) {
 #pragma unroll
-        for (int q = r; q < NB; ++q) M[r][q] += a[r] * a[q];  // upper triangle; a[r] a[q] = a[q] a[r]
-        M[r][NB] += a[r] * p;
+        for (int q = r; q < NB; ++q) {
+          if (r == 0)
+            acc_add(Ma[r][q], a[q]);  // a[0] = 1
+          else
+            acc_mad(Ma[r][q], a[r], a[q]);
+        }
+        if (r == 0)
+          acc_add(Ma[r][NB], p);
+        else
+          acc_mad(Ma[r][NB], a[r], p);
       }
-      sum += p;
+      acc_add(sa, p);
     }
+    double M[NB][NB + 1];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+      for (int q = r; q <= NB; ++q) M[r][q] = df_to_f64(acc_result(Ma[r][q]));
+    const double sum = df_to_f64(acc_result(sa));
 #pragma unroll
     for (int r = 1; r < NB; ++r)
 #pragma unroll
@@ -148,31 +189,42 @@ __global__ void __launch_bounds__(128) lsq_linear_kernel(const uint32_t* __restr
       c[0] = empty_fill;
     } else {
       bool ok = n > (uint32_t)D;
-      double dmax = 0.0;
+      double dmax = 0.0, invd[NB];
 #pragma unroll
       for (int r = 0; r < NB; ++r) dmax = M[r][r] > dmax ? M[r][r] : dmax;
 #pragma unroll
       for (int col = 0; col < NB; ++col) {
         if (!ok) break;
         int piv = col;
+        double best = fabs(M[col][col]);
 #pragma unroll
         for (int r = col + 1; r < NB; ++r)
-          if (fabs(M[r][col]) > fabs(M[piv][col])) piv = r;
-        if (!(fabs(M[piv][col]) > 1e-12 * dmax)) {
+          if (fabs(M[r][col]) > best) {
+            best = fabs(M[r][col]);
+            piv = r;
+          }
+        if (!(best > 1e-12 * dmax)) {
           ok = false;
           break;
         }
-        if (piv != col) {
+        // the swap with compile-time row indices keeps M in registers
 #pragma unroll
-          for (int q = 0; q <= NB; ++q) {
-            const double t = M[col][q];
-            M[col][q] = M[piv][q];
-            M[piv][q] = t;
+        for (int r = col + 1; r < NB; ++r)
+          if (r == piv) {
+#pragma unroll
+            for (int q = 0; q <= NB; ++q) {
+              const double t = M[col][q];
+              M[col][q] = M[r][q];
+              M[r][q] = t;
+            }
           }
-        }
+        // one reciprocal per pivot (FP64 divisions are sequences on the FP64
+        // pipe; the solve's rounding is covered by the kappa-scaled bound)
+        const double inv = 1.0 / M[col][col];
+        invd[col] = inv;
 #pragma unroll
         for (int r = col + 1; r < NB; ++r) {
-          const double f = M[r][col] / M[col][col];
+          const double f = M[r][col] * inv;
 #pragma unroll
           for (int q = col; q <= NB; ++q) M[r][q] -= f * M[col][q];
         }
@@ -183,7 +235,7 @@ __global__ void __launch_bounds__(128) lsq_linear_kernel(const uint32_t* __restr
           double s = M[r][NB];
 #pragma unroll
           for (int q = r + 1; q < NB; ++q) s -= M[r][q] * c[q];
-          c[r] = s / M[r][r];
+          c[r] = s * invd[r];
         }
       } else {
         c[0] = sum / (double)n;
@@ -228,14 +280,13 @@ extern "C" pic_status pic_interpolate_to_vertices(pic_particles p, pic_mesh mesh
   }
   const double* pv = p->props[p->cur] + (size_t)prop * p->capacity;
   const int g1 = transfer_grid(p->C, 128), g2 = transfer_grid((size_t)m.nverts, 256);
+  float2* part = reinterpret_cast<float2*>(p->xfer);  // [2 * 2^dim][C] double-float pairs
   if (mesh->dim == 2) {
-    vertex_partial_kernel<2><<<g1, 128, 0, st>>>(p->cell_off, p->xhat[p->cur], pv, p->C, p->capacity, p->xfer,
-                                                 p->ctr);
-    vertex_gather_kernel<2><<<g2, 256, 0, st>>>(m, p->xfer, empty_fill, avg, weight);
+    vertex_partial_kernel<2><<<g1, 128, 0, st>>>(p->cell_off, p->xhat[p->cur], pv, p->C, p->capacity, part, p->ctr);
+    vertex_gather_kernel<2><<<g2, 256, 0, st>>>(m, part, empty_fill, avg, weight);
   } else {
-    vertex_partial_kernel<3><<<g1, 128, 0, st>>>(p->cell_off, p->xhat[p->cur], pv, p->C, p->capacity, p->xfer,
-                                                 p->ctr);
-    vertex_gather_kernel<3><<<g2, 256, 0, st>>>(m, p->xfer, empty_fill, avg, weight);
+    vertex_partial_kernel<3><<<g1, 128, 0, st>>>(p->cell_off, p->xhat[p->cur], pv, p->C, p->capacity, part, p->ctr);
+    vertex_gather_kernel<3><<<g2, 256, 0, st>>>(m, part, empty_fill, avg, weight);
   }
   count_launches(2);
   PIC_CUDA(cudaGetLastError());
