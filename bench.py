@@ -216,17 +216,18 @@ def _timed_advect(P, parts, wl, precision, steps, warmup, stream, barrier, clock
     return e0.elapsed_time(e1), adv / max(nsteps, 1), reb / max(nsteps, 1), d["particle_steps"], d, clk
 
 
-def _accuracy_fp32_basis(P, mesh, wl):
+def _accuracy_fp32_basis(P, mesh, wl, form=None):
     """Both forms from the same seeded store over the configuration's steps;
     every particle compared by id, and the per-cell averages of property 0.
     The FP64 form is the reference here: it matches the CPU oracle to 1e-12
     in positions and cell averages (the parity tests), far below the FP32
-    basis's error."""
+    basis's error.  form: PIC_FP32_BASIS (default) or
+    PIC_FP32_BASIS_STAGE_DF."""
     import torch
 
     out = {}
     runs = []
-    for prec in (P.PIC_FP64, P.PIC_FP32_BASIS):
+    for prec in (P.PIC_FP64, P.PIC_FP32_BASIS if form is None else form):
         parts = _seed(P, mesh, wl)
         parts.advect(wl.dt, wl.integrator, wl.n_steps, prec)
         e = parts.export()
@@ -390,6 +391,25 @@ def run_ours(args, rank, world, local_rank):
         fp32["roofline"] = roofline_object(1, adv32, ps32 / args.steps, ab32, hbm)
         if not args.no_accuracy:
             fp32["accuracy"] = _accuracy_fp32_basis(P, mesh, wl)
+        # the strict reading: the double-float Newton residual step at the
+        # stage points too (PIC_FP32_BASIS_STAGE_DF)
+        p32 = _seed(P, mesh, wl)
+        msd, advd, rebd, psd, cdd, _ = _timed_advect(P, p32, wl, P.PIC_FP32_BASIS_STAGE_DF, args.steps,
+                                                      args.warmup, stream, barrier)
+        p32.close()
+        roof_d = roofline_object(1, advd, psd / args.steps, ab32, hbm)
+        roof_d.update({"kernel": "advect_kernel<3,RK4> (FP32-basis form, double-float stage residuals)",
+                       "traffic": None, "traffic_source": "not captured for this variant"})
+        roof_d.pop("issue_view", None)
+        fp32["stage_residuals_double_float"] = {
+            "value": psd / (msd / 1e3), "unit": "particle-steps/s", "ms_per_step": msd / args.steps,
+            "advect_ms_per_step": advd, "roofline": roof_d,
+            "newton_iterations_per_particle_step": cdd["newton_iterations"] / max(psd, 1),
+            "what": "the FP32-basis form with the double-float Newton residual and convergence test at every "
+                    "stage point, not only at the new position"}
+        if not args.no_accuracy:
+            fp32["stage_residuals_double_float"]["accuracy"] = _accuracy_fp32_basis(
+                P, mesh, wl, P.PIC_FP32_BASIS_STAGE_DF)
 
     (tmax, e2e_s, e2e_serial_s), (psteps_all, e2e_all, e2e_serial_all) = shard.reduce_timing(
         [ms, e2e_s, e2e_serial_s], [psteps, e2e_psteps, e2e_serial_psteps], device=dev if world > 1 else None)

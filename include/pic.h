@@ -66,7 +66,7 @@ typedef enum {
 } pic_status;
 
 typedef enum { PIC_EULER = 1, PIC_RK2 = 2, PIC_RK4 = 4 } pic_integrator;
-typedef enum { PIC_FP64 = 0, PIC_FP32_BASIS = 1 } pic_precision;
+typedef enum { PIC_FP64 = 0, PIC_FP32_BASIS = 1, PIC_FP32_BASIS_STAGE_DF = 2 } pic_precision;
 typedef enum { PIC_AVG_ARITHMETIC = 0, PIC_AVG_GEOMETRIC = 1, PIC_AVG_HARMONIC = 2 } pic_average;
 
 /* Bits of the device status word (pic_get_state). */
@@ -218,7 +218,9 @@ pic_status pic_set_properties(pic_particles parts, int prop, const double *value
  *              and are stored in FP64; the new position of each step is
  *              located with the double-float residual and convergence test
  *              (its stored x-hat good to ~1e-14), the stage points with the
- *              FP32 Newton alone (x-hat to ~1e-7, all an FP32 basis can use)
+ *              FP32 Newton alone (x-hat to ~1e-7, all an FP32 basis can use);
+ *              PIC_FP32_BASIS_STAGE_DF: the same with the double-float
+ *              residual and convergence test at the stage points too
  * Errors: PIC_ERR_ARG (mesh/store mismatch, dt not finite, n_steps < 0,
  * velocity not set), PIC_ERR_CUDA. */
 pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, pic_integrator integrator,

@@ -354,15 +354,16 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
   if (n_steps < 0) return (set_error("pic_advect: n_steps < 0"), PIC_ERR_ARG);
   if (integrator != PIC_EULER && integrator != PIC_RK2 && integrator != PIC_RK4)
     return (set_error("pic_advect: unknown integrator %d", (int)integrator), PIC_ERR_ARG);
-  if (precision != PIC_FP64 && precision != PIC_FP32_BASIS)
+  if (precision != PIC_FP64 && precision != PIC_FP32_BASIS && precision != PIC_FP32_BASIS_STAGE_DF)
     return (set_error("pic_advect: unknown precision %d", (int)precision), PIC_ERR_ARG);
   if (!mesh->has_velocity) return (set_error("pic_advect: velocity not set"), PIC_ERR_ARG);
   cudaStream_t st = (cudaStream_t)stream;
-  if (precision == PIC_FP32_BASIS) {
+  if (precision != PIC_FP64) {
     const pic_status r = ensure_fp32_coefficients(mesh, st);
     if (r != PIC_OK) return r;
   }
-  const MeshView m = mesh_view(mesh);
+  MeshView m = mesh_view(mesh);
+  m.stage_df = precision == PIC_FP32_BASIS_STAGE_DF ? 1 : 0;
   // Each step's rebin computes the new order (perm, sorted cells); the
   // particles themselves move with the next step's advect, which reads them
   // through perm.  Every step thus reads and writes the particle state once
@@ -374,7 +375,7 @@ extern "C" pic_status pic_advect(pic_particles parts, pic_mesh mesh, double dt, 
     PIC_CUDA(cudaMemsetAsync(&parts->ctr->tile_next, 0, sizeof(unsigned int), st));
     cudaEvent_t* ev = parts->timing ? timing_slot(parts) : nullptr;
     if (ev) PIC_CUDA(cudaEventRecord(ev[0], st));
-    const bool f32 = precision == PIC_FP32_BASIS;
+    const bool f32 = precision != PIC_FP64;
     if (mesh->dim == 2) {
       if (f32)
         launch_advect_rk<2, true>(parts, m, dt, (int)integrator, pending, st);

@@ -200,7 +200,8 @@ __device__ __forceinline__ uint32_t advect_particle_cells(const Cells& cs, const
         y[a] = df_add(xd[a], p < TB::S ? df_scale2(k[a], TB::c(p)) : acc[a]);
       }
       // the FP32-basis form needs double-float x-hat only where it is stored
-      Ks = locate_df<D, kFast>(cs, m, y, Ks, hint, ts, iters, flags, !F32B || p == TB::S);
+      // (unless the stage points are asked for it too)
+      Ks = locate_df<D, kFast>(cs, m, y, Ks, hint, ts, iters, flags, !F32B || p == TB::S || m.stage_df);
       if (Ks == PIC_LOST) return PIC_LOST;
       if constexpr (kFast)
         if (Ks == kDefer) return kDefer;

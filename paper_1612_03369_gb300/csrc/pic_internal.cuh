@@ -147,6 +147,7 @@ struct MeshView {
   const float4* Qf;   // their high parts (FP32-basis form; null until that form is first used)
   const float4* Qfn;
   int has_next;
+  int stage_df;  // FP32-basis form: stage points too take the double-float Newton step (set per pic_advect call)
   double dlo[3], dhi[3];
 };
 
@@ -173,6 +174,7 @@ inline MeshView mesh_view(const pic_mesh_s* m) {
   v.Qf = m->Qf;
   v.Qfn = m->Qfn;
   v.has_next = m->has_next;
+  v.stage_df = 0;
   return v;
 }
 

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpic.so")
 PIC_OK, PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CAPACITY, PIC_ERR_CUDA, PIC_ERR_NOT_CONVERGED, PIC_ERR_TIMEOUT, \
     PIC_ERR_STATE = range(8)
 PIC_EULER, PIC_RK2, PIC_RK4 = 1, 2, 4
-PIC_FP64, PIC_FP32_BASIS = 0, 1
+PIC_FP64, PIC_FP32_BASIS, PIC_FP32_BASIS_STAGE_DF = 0, 1, 2
 PIC_AVG_ARITHMETIC, PIC_AVG_GEOMETRIC, PIC_AVG_HARMONIC = 0, 1, 2
 PIC_TAPE_STAGES, PIC_TAPE_CHECKPOINTS = 0, 1
 PIC_STATUS_NEWTON_NONCONV, PIC_STATUS_CAPACITY, PIC_STATUS_GLOBAL_SEARCH, PIC_STATUS_BOUNDS = 1, 2, 4, 8

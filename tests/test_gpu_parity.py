@@ -258,6 +258,28 @@ def test_fp32_basis_error_bound(P, oracle_mod):
     assert err <= 1e-5, err
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fp32_basis_stage_residual_forms(P, oracle_mod, precision):
+    """Both readings of the precision form on the same store: the stage
+    points located by the FP32 Newton alone (1) or with the double-float
+    residual step too (2, PIC_FP32_BASIS_STAGE_DF).  Either stays within the
+    FP32 basis' error of the FP64 oracle, and the two agree with each other
+    to that order (the stage x-hat they feed an FP32 basis differ by ~1e-7)."""
+    wl = W.curl_cube(8, 20, 10, 2)
+    parts, op, _ = _run_both(P, oracle_mod, wl, wl.n_steps, precision=precision)
+    g = H.gpu_state(parts)
+    pos = {int(i): k for k, i in enumerate(g["id"])}
+    err = max(np.abs(g["x"][pos[int(i)]] - x).max() for i, x in zip(op.id, op.x) if int(i) in pos)
+    assert err <= 1e-5, err
+    assert parts.state()[2] == 0
+    if precision == 2:
+        other, _, _ = _run_both(P, oracle_mod, wl, wl.n_steps, precision=1)
+        o = H.gpu_state(other)
+        opos = {int(i): k for k, i in enumerate(o["id"])}
+        d = max(np.abs(g["x"][pos[i]] - o["x"][opos[i]]).max() for i in pos if i in opos)
+        assert d <= 1e-5, d
+
+
 def test_edge_cases(P, oracle_mod):
     import torch
 
