@@ -86,14 +86,21 @@ __device__ __forceinline__ uint32_t tile_particle(const Cells& cs, const MeshVie
   return Kn;
 }
 
-// The FP32-basis instance needs fewer registers and is bound by load latency
-// rather than issue: 8 resident blocks per SM (64 registers) ran its 128^3
-// step in 7.02 ms against 7.32 ms at 6 (5: 7.51, 7: 7.07).
+// Resident blocks per SM of the step kernel, swept on the 128^3 x 20 step
+// (CUDA events, the same GB300 nodes back to back):
+// - FP64 form: 7 blocks (72 registers) 14.47 ms, 6 blocks (80) 14.76 ms,
+//   5 blocks 16.29 ms;
+// - FP32-basis form: 8 blocks (64 registers) 6.81 ms on most nodes but
+//   9.27 ms on others, 7 blocks 6.82 ms, 6 blocks (80 registers, fewest
+//   spills) 7.02 ms on both kinds of node, so it takes 6.
+#ifndef PIC_ADVECT_MIN_BLOCKS_F64
+#define PIC_ADVECT_MIN_BLOCKS_F64 7
+#endif
 #ifndef PIC_ADVECT_MIN_BLOCKS_F32
-#define PIC_ADVECT_MIN_BLOCKS_F32 8
+#define PIC_ADVECT_MIN_BLOCKS_F32 6
 #endif
 template <int D, int RK, bool F32B, bool TWO, bool STAGE>
-__global__ void __launch_bounds__(kAdvectThreads, F32B ? PIC_ADVECT_MIN_BLOCKS_F32 : PIC_ADVECT_MIN_BLOCKS)
+__global__ void __launch_bounds__(kAdvectThreads, F32B ? PIC_ADVECT_MIN_BLOCKS_F32 : PIC_ADVECT_MIN_BLOCKS_F64)
     advect_kernel(const __grid_constant__ MeshView m, const __grid_constant__ StoreView s,
                   const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm, df dt,
                   uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
@@ -287,11 +294,11 @@ static int grid_for(size_t n, int block) {
 // One advect launch.  With `fused` the previous step's reordering (perm,
 // sorted cells in the other buffer) is applied on the way: the step reads
 // buffer cur and writes buffer 1 - cur, which becomes cur.
-// Persistent grid: PIC_ADVECT_MIN_BLOCKS blocks per SM (the register
+// Persistent grid: PIC_ADVECT_MIN_BLOCKS_F64 / _F32 blocks per SM (the register
 // budget's residency), fewer when the store has fewer warp tiles.
 static int advect_grid(size_t n, bool f32b) {
   const size_t blocks = (n + kAdvectThreads - 1) / kAdvectThreads;
-  const size_t cap = (size_t)num_sms() * (f32b ? PIC_ADVECT_MIN_BLOCKS_F32 : PIC_ADVECT_MIN_BLOCKS);
+  const size_t cap = (size_t)num_sms() * (f32b ? PIC_ADVECT_MIN_BLOCKS_F32 : PIC_ADVECT_MIN_BLOCKS_F64);
   const size_t g = blocks < cap ? blocks : cap;
   return (int)(g > 0 ? g : 1);
 }
