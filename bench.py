@@ -72,16 +72,16 @@ def advect_bytes(dim: int, ppc: float, n_props: int, xhat_bytes: int = 8, dof_by
 # multi-step call; traffic grows with the particle count, so a launch at
 # another size is scaled by its particles.  Keyed by precision (0 FP64
 # form, 1 FP32-basis form).
-ADVECT_DRAM_BYTES_PER_PARTICLE = {0: 1165.573e6 / 5242880, 1: 1103.533e6 / 5242880}
+ADVECT_DRAM_BYTES_PER_PARTICLE = {0: 1342.109e6 / 5242880, 1: 1017.072e6 / 5242880}
 # Warp instructions per 32 particle-steps and pipe utilisation of the same
 # captures: the advect kernel is bound by instruction issue (double-float
 # arithmetic on the FP32 pipe) in the FP64 form, and by issue and load
 # latency in the FP32-basis form, not by HBM.
 ADVECT_ISSUE = {
-    0: {"warp_instructions_per_32_particle_steps": 10671, "issue_active_pct": 74.7, "fma_pipe_active_pct": 60.4,
-        "top_stall": "not_selected 2.34 per issue (issue-bound)"},
-    1: {"warp_instructions_per_32_particle_steps": 4527, "issue_active_pct": 69.7, "fma_pipe_active_pct": 42.6,
-        "top_stall": "long_scoreboard 4.65 per issue"},
+    0: {"warp_instructions_per_32_particle_steps": 10758, "issue_active_pct": 76.3, "fma_pipe_active_pct": 61.2,
+        "top_stall": "not_selected 3.12 per issue (issue-bound)"},
+    1: {"warp_instructions_per_32_particle_steps": 4343, "issue_active_pct": 64.5, "fma_pipe_active_pct": 41.1,
+        "top_stall": "long_scoreboard 3.83 per issue"},
 }
 
 
