@@ -130,11 +130,10 @@ struct Tableau<4> {  // classical RK4: y_1 = x + k0/2, y_2 = x + k1/2, y_3 = x +
   __device__ static bool divide6() { return true; }
 };
 
-// Resident blocks per SM requested from the register allocator by the kernels
-// that inline the particle step besides the single-mesh step kernel (the
-// ensemble, stage-recording and replay kernels; tuning knob, swept at build
-// time with -DPIC_ADVECT_MIN_BLOCKS=n).  The step kernel has its own pair of
-// knobs in advect.cu.
+// Resident blocks per SM requested from the register allocator by the
+// stage-recording and replay kernels, which inline the particle step (tuning
+// knob, swept at build time with -DPIC_ADVECT_MIN_BLOCKS=n).  The step kernel
+// and the ensemble kernels have their own knobs (advect.cu, ensemble.cu).
 #ifndef PIC_ADVECT_MIN_BLOCKS
 #define PIC_ADVECT_MIN_BLOCKS 6
 #endif

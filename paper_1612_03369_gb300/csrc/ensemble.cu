@@ -33,6 +33,14 @@ constexpr int kMaxEnsemble = 128;
 constexpr int kEnsBlock = 128;
 constexpr int kMaxBlocksPerSm = 32;  // the hardware's limit of resident blocks
 
+// Resident blocks per SM the ensemble kernels are compiled for (72
+// registers).  On the 64-problem 2D ensemble, 7 against 6: per-step mode
+// 8.48 against 8.65 ms per step, persistent kernel 8.89 against 8.95 ms; 8
+// (64 registers) made the persistent kernel slower (9.19 ms).
+#ifndef PIC_ENSEMBLE_MIN_BLOCKS
+#define PIC_ENSEMBLE_MIN_BLOCKS 7
+#endif
+
 struct GridBarrier {
   unsigned int count;
   unsigned int gen;
@@ -200,7 +208,7 @@ __device__ __forceinline__ void ensemble_advect_tiles(const EnsShared& sh, int P
 // Per-step mode: one step's advect over the whole ensemble (tiles from the
 // store's work counter, cleared before the launch).
 template <int D, int RK>
-__global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_advect_kernel(
+__global__ void __launch_bounds__(kEnsBlock, PIC_ENSEMBLE_MIN_BLOCKS) ensemble_advect_kernel(
     const MeshView* __restrict__ views, const uint32_t* __restrict__ base, const df* __restrict__ dts, int P,
     const __grid_constant__ StoreView s, const __grid_constant__ StoreView d, const uint32_t* __restrict__ perm,
     uint32_t tile, uint32_t* __restrict__ cell_new, uint32_t* __restrict__ counts, DevCounters* __restrict__ ctr) {
@@ -233,7 +241,7 @@ struct PersistArgs {
 // built, nothing reads them again); the rank.  counts and the tile counters
 // are cleared before the launch.
 template <int D, int RK>
-__global__ void __launch_bounds__(kEnsBlock, PIC_ADVECT_MIN_BLOCKS) ensemble_persistent_kernel(PersistArgs A) {
+__global__ void __launch_bounds__(kEnsBlock, PIC_ENSEMBLE_MIN_BLOCKS) ensemble_persistent_kernel(PersistArgs A) {
   __shared__ EnsShared sh;
   load_ensemble(sh, A.views, A.base, A.dts, A.P);
   const uint32_t nb = gridDim.x, bid = blockIdx.x;
