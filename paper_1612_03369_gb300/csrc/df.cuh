@@ -122,8 +122,6 @@ __device__ __forceinline__ void acc_add(df_acc& acc, df a) {
 }
 
 __device__ __forceinline__ df acc_result(const df_acc& acc) { return fast_two_sum(acc.s, acc.e); }
-// The unevaluated pair, for a consumer that only multiplies it (no need to normalise).
-__device__ __forceinline__ df acc_pair(const df_acc& acc) { return df_make(acc.s, acc.e); }
 
 // Split an FP64 value into a double-float (two conversions and one FP64
 // subtraction: these run on the FP64 pipe, so they are kept off inner loops).

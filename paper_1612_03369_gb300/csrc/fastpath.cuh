@@ -220,8 +220,6 @@ __device__ __forceinline__ bool solve32(const float J[D][D], const float r[D], f
   }
 }
 
-__device__ __forceinline__ df neg(df a) { return df_make(-a.hi, -a.lo); }
-
 // Double-float residual r = dloc - sum_k a_k m_k(t) at a single-float point t
 // (the monomials of t are formed exactly with two_prod).
 template <int D>

@@ -21,12 +21,6 @@
 
 namespace pic {
 
-// a + c for a float constant c.
-__device__ __forceinline__ df df_add_f(df a, float c) {
-  const df s = two_sum(a.hi, c);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
-}
-
 // 1 / a: FP32 reciprocal refined by one Newton step in double-float.
 __device__ __forceinline__ df df_recip(df a) {
   const float r = __frcp_rn(a.hi);
