@@ -517,6 +517,7 @@ def run_slab(args, rank, world, local_rank):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     moved[:] = [0, 0]
     launches0 = P.pic_kernel_launches()
+    P.pic_timing_enable(parts.h, True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
@@ -524,6 +525,8 @@ def run_slab(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    P.pic_timing_enable(parts.h, False)
+    adv, reb, nst = P.pic_timing_read(parts.h)
     ms = e0.elapsed_time(e1)
     launches = P.pic_kernel_launches() - launches0
     psteps = parts.stats()["particle_steps"] - c0["particle_steps"]
@@ -565,6 +568,9 @@ def run_slab(args, rank, world, local_rank):
                    "l2": "state > 129 MB L2 per rank, no flush"},
         "step_fraction_of_hbm_roofline": (value / world * sbytes / 1e9) / hbm,
         "exchanged_particles_per_step": (mv_d + mv_u) / args.steps,
+        "roofline": roofline_object(0, adv / max(nst, 1), psteps / args.steps, advect_bytes(wl.dim, wl.ppc, wl.n_props),
+                                    hbm, peak_kind, reb / max(nst, 1)),
+        "roofline_scope": "rank 0's advect kernel on its slab (each rank runs the same kernel on its own slab)",
         "gpu_launches": int(launches),
         "clocks": clk,
         "e2e": {"value": e2e_all / e2e_s, "unit": "particle-steps/s",
