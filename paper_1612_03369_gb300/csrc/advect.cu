@@ -91,8 +91,9 @@ __device__ __forceinline__ uint32_t tile_particle(const Cells& cs, const MeshVie
 // - FP64 form: 7 blocks (72 registers) 14.47 ms, 6 blocks (80) 14.76 ms,
 //   5 blocks 16.29 ms;
 // - FP32-basis form: 8 blocks (64 registers) 6.81 ms on most nodes but
-//   9.27 ms on others, 7 blocks 6.82 ms, 6 blocks (80 registers, fewest
-//   spills) 7.02 ms on both kinds of node, so it takes 6.
+//   9.27 ms on others, 7 blocks 6.82 or 8.18 ms from one run to the next on
+//   one node, 6 blocks (80 registers, fewest spills) 7.01-7.02 ms on every
+//   node and run, so it takes 6.
 #ifndef PIC_ADVECT_MIN_BLOCKS_F64
 #define PIC_ADVECT_MIN_BLOCKS_F64 7
 #endif
